@@ -1,0 +1,91 @@
+"""Pins for the oracle's dense kernels against textbook/library routines (numpy/LAPACK)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import zolo_oracle as zo
+
+
+def rng(seed=0):
+    return np.random.default_rng(seed)
+
+
+@pytest.mark.parametrize("p,n", [(7, 3), (40, 17), (64, 64), (97, 41)])
+def test_householder_qr_matches_lapack(p, n):
+    W = rng(p * n).standard_normal((p, n))
+    refl, R = zo.householder_qr(W)
+    Q = zo.thin_q(refl, p, n)
+    Qn, Rn = np.linalg.qr(W)
+    # unique up to the signs of R's rows
+    d = np.sign(np.diag(R)) * np.sign(np.diag(Rn))
+    assert np.allclose(R, d[:, None] * Rn, atol=1e-12 * np.abs(Rn).max())
+    assert np.allclose(Q, Qn * d, atol=1e-12)
+    assert np.linalg.norm(Q.T @ Q - np.eye(n)) < 1e-13
+    assert np.linalg.norm(Q @ R - W) < 1e-13 * np.linalg.norm(W)
+
+
+def test_householder_vector_zero_tail():
+    v, tau, beta = zo.householder_vector(np.array([3.0, 0.0, 0.0]))
+    assert tau == 0.0 and beta == 3.0 and v[0] == 1.0
+
+
+def test_cholesky_and_solves_match_lapack():
+    X = rng(3).standard_normal((50, 20))
+    Z = X.T @ X + 0.3 * np.eye(20)
+    R = zo.cholesky_upper(Z)
+    assert np.allclose(R, np.linalg.cholesky(Z).T, atol=1e-12)
+    Y = zo.solve_right_upper(X, R)
+    assert np.allclose(Y, np.linalg.solve(R.T, X.T).T, atol=1e-12)
+    W = zo.solve_right_upper_transpose(Y, R)
+    assert np.allclose(W, X @ np.linalg.inv(Z), atol=1e-11)
+
+
+def test_cholesky_breakdown_raises():
+    with pytest.raises(np.linalg.LinAlgError):
+        zo.cholesky_upper(np.array([[1.0, 2.0], [2.0, 1.0]]))
+
+
+@pytest.mark.parametrize("n", [1, 2, 9, 40])
+def test_eigh_matches_lapack(n):
+    g = rng(n)
+    Q, _ = np.linalg.qr(g.standard_normal((n, n)))
+    lam = np.geomspace(1.0, 1e-9, n)
+    H = (Q * lam) @ Q.T
+    H = 0.5 * (H + H.T)
+    got, V = zo.jacobi_eigh(H)
+    order = np.argsort(-got)
+    got, V = got[order], V[:, order]
+    ref, Vn = np.linalg.eigh(H)
+    ref, Vn = ref[::-1], Vn[:, ::-1]
+    assert np.max(np.abs(got - ref)) < 1e-14
+    assert np.linalg.norm(V.T @ V - np.eye(n)) < 1e-13
+    assert np.linalg.norm(H - (V * got) @ V.T) < 1e-14 * n
+    # eigenvectors of well separated eigenvalues agree up to sign
+    assert np.allclose(np.abs(np.sum(V * Vn, axis=0))[lam > 1e-6], 1.0, atol=1e-8)
+
+
+def test_eigh_semidefinite_falls_back_to_shift():
+    Q, _ = np.linalg.qr(rng(5).standard_normal((12, 12)))
+    lam = np.concatenate([np.linspace(1, 0.1, 10), [0.0, -1e-17]])
+    H = (Q * lam) @ Q.T
+    got, V = zo.jacobi_eigh(0.5 * (H + H.T))
+    assert np.max(np.abs(np.sort(got) - np.sort(lam))) < 1e-14
+
+
+@pytest.mark.parametrize("m,n", [(5, 5), (12, 7), (30, 30)])
+def test_one_sided_jacobi_svd_matches_lapack(m, n):
+    A = rng(m + n).standard_normal((m, n))
+    U, S, V = zo.one_sided_jacobi_svd(A)
+    assert np.allclose(S, np.linalg.svd(A, compute_uv=False), atol=1e-13)
+    assert np.linalg.norm(A - (U * S) @ V.T) < 1e-13 * np.linalg.norm(A)
+    assert np.linalg.norm(U.T @ U - np.eye(n)) < 1e-13
+
+
+def test_hestenes_odd_column_count():
+    X = rng(2).standard_normal((9, 7))
+    Y, _ = zo.hestenes_columns(X)
+    G = Y.T @ Y
+    off = G - np.diag(np.diag(G))
+    assert np.abs(off).max() < 1e-13
+    assert np.allclose(np.sort(np.linalg.norm(Y, axis=0)), np.sort(np.linalg.svd(X, compute_uv=False)))
