@@ -1,0 +1,360 @@
+#!/usr/bin/env python
+"""Zolo-SVD / Zolo-PD throughput on GB300 through libzolo's C ABI.
+
+One step = one Zolo-SVD (or Zolo-PD) of the workload's matrix: the whole hot
+path (coefficients, scaling, the QR-form and Cholesky-form iterations, the
+r-way combination, H, and for the SVD the eigendecomposition of H and U = Qp V).
+`value` is whole-job matrices/s with the input resident in HBM; `e2e` is the
+same through the host-buffer entry point with the copies inside the timed
+region.  The matrix (134 MB and up) and the multi-GB workspace exceed the 129 MB
+L2, so no flush is needed between steps.
+
+Multi-GPU: the decomposition of one matrix is not sharded here; under torchrun
+every rank decomposes its own replica (weak scaling, no collective on the path).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload svd4096|pd256|...]
+  python bench.py --impl reference ...   (the CPU oracle on a bounded sample)
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Zolo-PD matrices/s & eff. TFLOP/s, split-prec vs FP64, at bwd err <= 1e-13"
+# FP64 FMA pipe: 152 SMs x 2 DFMA (4 flops) per clock x 2.07 GHz max SM clock.
+FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
+
+WORKLOADS = {
+    "svd4096": dict(kind="svd", m=4096, n=4096, kappa=1e12, r=8, sample_n=384,
+                    desc="Plain FP64 Zolo-SVD of one 4096x4096 matrix, sigma geometric 1..1e-12 "
+                         "(kappa 1e12), r=8, QR-form then Cholesky-form iteration, eig(H) included"),
+    "pd4096": dict(kind="pd", m=4096, n=4096, kappa=1e12, r=8, sample_n=384,
+                   desc="Plain FP64 Zolo-PD of one 4096x4096 matrix, kappa 1e12, r=8"),
+    "pd256": dict(kind="pd", m=256, n=256, kappa=1e8, r=3, sample_n=256,
+                  desc="Plain FP64 Zolo-PD of one 256x256 matrix, kappa 1e8, r=3"),
+    "svd256": dict(kind="svd", m=256, n=256, kappa=1e8, r=3, sample_n=256,
+                   desc="Plain FP64 Zolo-SVD of one 256x256 matrix, kappa 1e8, r=3"),
+    "pd16384x4096": dict(kind="pd", m=16384, n=4096, kappa=1e6, r=6, sample_n=384, tall=True,
+                         desc="Plain FP64 Zolo-PD of one 16384x4096 matrix, sigma uniform in "
+                              "[1e-6, 1], r=6"),
+}
+
+
+def pd_model_flops(m, n, r, used_qr):
+    """Zolo-PD flops credited per matrix: 5 r m n^2 per QR-form iteration (structured
+    QR 2mn^2 + structured Q 2mn^2 + Q1 Q2^T mn^2), m n^2 + r (n^3/3 + 2 m n^2) per
+    Cholesky-form iteration, 2 m n^2 for H."""
+    f = 2.0 * m * n * n
+    for qr in used_qr:
+        f += 5.0 * r * m * n * n if qr else m * n * n + r * (n ** 3 / 3.0 + 2.0 * m * n * n)
+    return f
+
+
+def make_input(w, seed):
+    from paper_1806_06204_gb300 import synth
+    if w.get("tall"):
+        return synth.tall_uniform(w["m"], w["n"], lo=1.0 / w["kappa"], seed=seed)
+    return synth.make_matrix(w["m"], w["n"], synth.geometric_sigma(w["n"], w["kappa"]), seed)
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.proc, self.lines = index, None, []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def accuracy(w, sm, outs):
+    """Backward error / orthogonality / sigma error of one result, on the device
+    with torch (a check of the output, not part of the timed path)."""
+    import torch
+    A = torch.from_numpy(sm.A).cuda()
+    nA = torch.linalg.norm(A)
+    n = w["n"]
+    I = torch.eye(n, dtype=torch.float64, device="cuda")
+    if w["kind"] == "svd":
+        U, S, V = outs
+        bwd = torch.linalg.norm(A - (U * S) @ V.T) / nA
+        sig = torch.from_numpy(sm.sigma).cuda()
+        return {"bwd_err": float(bwd),
+                "orth_U": float(torch.linalg.norm(U.T @ U - I) / math.sqrt(n)),
+                "orth_V": float(torch.linalg.norm(V.T @ V - I) / math.sqrt(n)),
+                "max_sigma_err": float(torch.max(torch.abs(S - sig)) / sig[0])}
+    Qp, H = outs
+    return {"bwd_err": float(torch.linalg.norm(A - Qp @ H) / nA),
+            "orth_Qp": float(torch.linalg.norm(Qp.T @ Qp - I) / math.sqrt(n)),
+            "H_symmetric": bool(torch.equal(H, H.T))}
+
+
+def oracle_sample(w, seed=None):
+    """Time the CPU oracle on a bounded sample of the workload: the same method,
+    kappa and r on an n_s x n_s (or m_s x n_s) matrix; scaled to the full size by
+    the cubic flop model.  Returns (matrices/s at full size, seconds, description)."""
+    from oracle import zolo_oracle as zo
+    from paper_1806_06204_gb300 import synth
+    ns = w["sample_n"]
+    ms = int(round(ns * w["m"] / w["n"]))
+    sm = synth.make_matrix(ms, ns, synth.geometric_sigma(ns, w["kappa"]), seed or 7000)
+    t0 = time.perf_counter()
+    if w["kind"] == "svd":
+        _, _, _, info = zo.zolo_svd(sm.A, 1.0, float(sm.sigma[-1]), r=w["r"])
+    else:
+        _, _, info = zo.zolo_pd(sm.A, 1.0, float(sm.sigma[-1]), r=w["r"])
+    dt = time.perf_counter() - t0
+    scale = pd_model_flops(w["m"], w["n"], w["r"], info.used_qr) / pd_model_flops(
+        ms, ns, w["r"], info.used_qr)
+    desc = (f"oracle zolo_{w['kind']} of one {ms}x{ns} matrix (kappa {w['kappa']:.0e}, r={w['r']}), "
+            f"{dt:.1f} s, scaled by the Zolo-PD flop model x{scale:.1f} to {w['m']}x{w['n']}")
+    return 1.0 / (dt * scale), dt, desc
+
+
+def blas_threads():
+    for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        if os.environ.get(k, "").isdigit():
+            return int(os.environ[k])
+    return os.cpu_count()
+
+
+def run_reference(args, w, rank):
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_sample(w)
+    vals, tot = [], 0.0
+    desc = ""
+    for _ in range(args.steps):
+        v, dt, desc = oracle_sample(w)
+        vals.append(v)
+        tot += dt
+    value = statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "matrices/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * tot / max(1, args.steps), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": w["desc"]},
+            "cpu_baseline": {"value": value, "unit": "matrices/s", "cores": blas_threads(),
+                             "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": "matrices/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="svd4096", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if args.impl == "ours" and torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+
+    if args.impl == "reference":
+        run_reference(args, w, rank)
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    import numpy as np
+    import torch
+    from paper_1806_06204_gb300 import build
+    build.build()
+    from paper_1806_06204_gb300 import binding as zb
+
+    torch.cuda.set_device(local)
+    sm = make_input(w, seed=2000 + rank)
+    A = torch.from_numpy(sm.A).cuda()
+    h = zb.Handle(local)
+    o = zb.opts(beta=float(np.min(sm.sigma)), alpha=1.0, r=w["r"])
+    m, n = w["m"], w["n"]
+
+    def step():
+        if w["kind"] == "svd":
+            U, S, V, info = zb.zolo_svd(h, A, o)
+            return (U, S, V), info
+        Qp, H, info = zb.zolo_pd(h, A, o)
+        return (Qp, H), info
+
+    for _ in range(args.warmup):
+        outs, info = step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    launches0 = zb.kernel_launches()
+    zb.profile(True)
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            outs, info = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    kstats = zb.profile_read()
+    zb.profile(False)
+    launches = zb.kernel_launches() - launches0
+    ms_step = e0.elapsed_time(e1) / args.steps
+    if dist:
+        t = torch.tensor([ms_step], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = world / (ms_step / 1000.0)                # matrices/s over all ranks
+    flops = pd_model_flops(m, n, info.r, info.used_qr)
+    acc = accuracy(w, sm, outs)
+
+    # roofline of the dominant kernel class (by device time inside the timed region)
+    dom_name, dom = max(((k, v) for k, v in kstats.items() if v["launches"] > 0),
+                        key=lambda kv: kv[1]["ms"])
+    achieved = dom["flops"] / (dom["ms"] / 1000.0) / 1e12
+    bound = "alu" if dom_name != "combine" else "hbm"
+    if bound == "alu":
+        roof = {"bound": "alu", "kernel": dom_name, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "derived: 152 SMs x 4 FP64 flops/clk x 2.07 GHz"}
+    else:
+        peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+        gbs = dom["bytes"] / (dom["ms"] / 1000.0) / 1e9
+        roof = {"bound": "hbm", "kernel": dom_name, "achieved": gbs, "peak": peak, "unit": "GB/s",
+                "frac": gbs / peak, "traffic": None}
+    roof["launches"] = dom["launches"]
+    roof["avg_launch_ms"] = dom["ms"] / dom["launches"]
+    roof["share_of_step"] = dom["ms"] / (ms_step * args.steps)
+
+    # end to end through the host-buffer entry point
+    e2e = None
+    if not args.no_e2e:
+        Ah = torch.from_numpy(sm.A).pin_memory().numpy()
+        Ah = np.asfortranarray(Ah)
+        if w["kind"] == "svd":
+            Uh = torch.empty((n, m), dtype=torch.float64).pin_memory().numpy().T
+            Vh = torch.empty((n, n), dtype=torch.float64).pin_memory().numpy().T
+            Sh = torch.empty(n, dtype=torch.float64).pin_memory().numpy()
+            host_step = lambda: zb.zolo_svd_host(h, Ah, o, Uh, Sh, Vh)
+            d2h = 8 * (m * n + n * n + n)
+        else:
+            Qh = torch.empty((n, m), dtype=torch.float64).pin_memory().numpy().T
+            Hh = torch.empty((n, n), dtype=torch.float64).pin_memory().numpy().T
+            host_step = lambda: zb.zolo_pd_host(h, Ah, o, Qh, Hh)
+            d2h = 8 * (m * n + n * n)
+        host_step()
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            host_step()
+        torch.cuda.synchronize()
+        barrier()
+        e2e_s = (time.perf_counter() - t0) / args.steps
+        if dist:
+            t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": world / e2e_s, "unit": "matrices/s", "h2d_bytes_per_step": 8 * m * n,
+               "d2h_bytes_per_step": d2h}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, dt, desc = oracle_sample(w)
+        cpu = {"value": v, "unit": "matrices/s", "cores": blas_threads(), "kind": "oracle",
+               "sample": desc}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "matrices/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic",
+                "config": {"workload": args.workload, "desc": w["desc"], "m": m, "n": n,
+                           "kappa": w["kappa"], "r": info.r, "prec": "fp64",
+                           "l2": "inputs larger than L2 (no flush)",
+                           "parallelism": "replicas" if world > 1 else "single"},
+                "eff_tflops": world * flops / (ms_step / 1000.0) / 1e12,
+                "pd_model_flops": flops, "iters": info.iters, "used_qr": info.used_qr,
+                "eig_sweeps": info.eig_sweeps, "accuracy": acc,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches,
+                "kernel_ms": {k: round(v["ms"], 3) for k, v in kstats.items() if v["launches"]},
+                "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    h.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,154 @@
+/*
+ * libzolo: Zolo-PD polar decomposition and Zolo-SVD on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Li, Liu, Du, "A new high performance and scalable SVD algorithm on
+ * distributed memory systems" (arxiv 1806.06204), after Nakatsukasa & Freund.
+ *
+ *   A = Qp H         polar decomposition (Eq. 1), Qp m x n with orthonormal
+ *                    columns, H n x n symmetric positive semidefinite;
+ *   A = U diag(S) V^T  SVD from H = V diag(S) V^T and U = Qp V (Algorithm 2).
+ *
+ * Every matrix is real FP64, column-major with a leading dimension (LAPACK
+ * convention), m >= n >= 1.  Unless an entry point says "host", every matrix
+ * pointer is a DEVICE pointer on the handle's device, owned by the caller.
+ * Calls are ordered on the given CUDA stream (a cudaStream_t passed as void*,
+ * NULL = the legacy default stream) and return after one final stream
+ * synchronisation that reads the status into `info`.
+ *
+ * Return codes: 0 on success; -i if argument i (1-based) is illegal, LAPACK
+ * style, before any work is queued; a positive ZOLO_E* code otherwise.
+ */
+#ifndef ZOLO_H_
+#define ZOLO_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ZOLO_MAX_R 8
+#define ZOLO_MAX_ITERS 8
+
+enum {
+  ZOLO_OK = 0,
+  ZOLO_ENONFINITE = 1, /* NaN or Inf in the input or an iterate                */
+  ZOLO_ECHOL = 2,      /* Cholesky breakdown (non-positive pivot)               */
+  ZOLO_ENOTCONV = 3,   /* a-posteriori test still failing after max_iter        */
+  ZOLO_ECUDA = 4,      /* a CUDA runtime call failed                            */
+  ZOLO_ENOMEM = 5,     /* workspace too small / device allocation failed        */
+  ZOLO_EEIG = 6        /* the Jacobi eigensolver did not converge               */
+};
+
+/* Arithmetic of the contractions.  ZOLO_FP64: plain FP64 (DFMA) everywhere. */
+enum { ZOLO_FP64 = 0, ZOLO_SPLIT_BF16 = 1 };
+
+typedef struct {
+  int r;           /* order parameter, 1..8 (Eq. 6: type (2r+1, 2r)); 0 = the
+                      smallest r needing at most two iterations (Table 1)      */
+  double alpha;    /* alpha >= sigma_max(A) (Algorithm 1 step 1); <= 0: use
+                      ||A||_F, an upper bound                                  */
+  double beta;     /* 0 < beta <= sigma_min(A) (step 2); l_0 = beta / alpha   */
+  int max_iter;    /* cap on iterations, 1..8 (default 6)                    */
+  int posteriori;  /* 1: after the a-priori iterations, apply the test of
+                      Algorithm 1 step (d) literally and iterate while
+                      ||X_{k+1}-X_k||_F/||X_{k+1}||_F > eps^(1/(2r+1))        */
+  int ns_steps;    /* Newton-Schulz steps X <- 1.5X - 0.5X(X^T X) after the
+                      iteration (not in the paper), 0..4                      */
+  int prec;        /* ZOLO_FP64 or ZOLO_SPLIT_BF16                            */
+  int force_qr;    /* -1: QR form while (1+c_1)/(l^2+c_1) > 100, then the
+                      Cholesky form; 0: Cholesky form always; 1: QR always     */
+} zolo_opts_t;
+
+typedef struct {
+  int status;                  /* the return code of the call                */
+  int iters;                   /* iterations run                             */
+  int r;                       /* order parameter used                       */
+  int used_qr[ZOLO_MAX_ITERS]; /* 1 if iteration k used the QR form (Eq. 12) */
+  double ell[ZOLO_MAX_ITERS + 1];   /* l_0, l_1, ... (Algorithm 1 step (c))  */
+  double delta[ZOLO_MAX_ITERS];     /* ||X_{k+1}-X_k||_F / ||X_{k+1}||_F      */
+  int chol_fallbacks;          /* Cholesky-form iterations redone in the QR
+                                  form after a non-positive pivot             */
+  int eig_sweeps;              /* Jacobi sweeps (zolo_svd only)              */
+  double ms;                   /* device time of the call (CUDA events)      */
+} zolo_info_t;
+
+typedef struct zolo_handle_s* zolo_handle_t;
+
+/* Defaults: r = 0, alpha = 1, beta = 0 (must be set), max_iter = 6,
+   posteriori = 0, ns_steps = 0, prec = ZOLO_FP64, force_qr = -1. */
+void zolo_opts_default(zolo_opts_t* opts);
+
+/* A handle binds a device and owns the library's workspace cache.
+   zolo_create makes `device` current; -1 = the current device. */
+int zolo_create(zolo_handle_t* handle, int device);
+int zolo_destroy(zolo_handle_t handle);
+
+/* Zolotarev coefficients for l in (0, 1], r in 1..8 (host, no GPU work):
+   c[0..2r-1] = c_1..c_2r of Eq. (7), a[0..r-1] = a_1..a_r of Eq. (10) read as
+   the partial-fraction residue (quotient of the two products), *Mhat = M_hat
+   of Eq. (8), *gap = 1 - Zhat(l; l) (the next l is 1 - gap, Algorithm 1
+   step (c)).  Any output pointer may be NULL.  Returns 0 or -1/-2. */
+int zolo_coefficients(double ell, int r, double* c, double* a, double* Mhat, double* gap);
+
+/* A-priori schedule (Table 1): l_0 = ell0 and l_{k+1} = Zhat(l_k; l_k) until
+   1 - l_K <= 1e-15 or K = max_iter.  Writes ells[0..K] and used_qr[0..K-1]
+   (QR form while (1+c_1)/(l_k^2+c_1) > 100) and returns K >= 0, or < 0 on
+   illegal arguments.  r = 0 selects r as zolo_opts_t does; *r_used receives
+   the r taken (may be NULL). */
+int zolo_schedule(double ell0, int r, int max_iter, double* ells, int* used_qr, int* r_used);
+
+/* Polar decomposition A = Qp H (Algorithm 1).
+   A (m x n, lda >= m) is read only; Qp (m x n, ldq >= m) and H (n x n,
+   ldh >= n) are written.  H is exactly symmetric. */
+int zolo_pd(zolo_handle_t handle, const double* A, int64_t m, int64_t n, int64_t lda,
+            double* Qp, int64_t ldq, double* H, int64_t ldh,
+            const zolo_opts_t* opts, zolo_info_t* info, void* stream);
+
+/* SVD A = U diag(S) V^T (Algorithm 2): Zolo-PD, the eigendecomposition of H
+   (one-sided block Jacobi on its Cholesky factor), U = Qp V.
+   U is m x n (ldu >= m), S has n entries (descending, >= 0), V is n x n
+   (ldv >= n).  All three are device pointers. */
+int zolo_svd(zolo_handle_t handle, const double* A, int64_t m, int64_t n, int64_t lda,
+             double* U, int64_t ldu, double* S, double* V, int64_t ldv,
+             const zolo_opts_t* opts, zolo_info_t* info, void* stream);
+
+/* As zolo_pd / zolo_svd, but every matrix pointer is a HOST pointer: the call
+   copies A to the device, computes, and copies the results back (pageable or
+   pinned host memory; pinned is faster).  Device buffers come from the
+   handle's cache. */
+int zolo_pd_host(zolo_handle_t handle, const double* A, int64_t m, int64_t n, int64_t lda,
+                 double* Qp, int64_t ldq, double* H, int64_t ldh,
+                 const zolo_opts_t* opts, zolo_info_t* info, void* stream);
+int zolo_svd_host(zolo_handle_t handle, const double* A, int64_t m, int64_t n, int64_t lda,
+                  double* U, int64_t ldu, double* S, double* V, int64_t ldv,
+                  const zolo_opts_t* opts, zolo_info_t* info, void* stream);
+
+/* Short text for a return code. */
+const char* zolo_strerror(int code);
+
+/* ---- Diagnostics (no counterpart in the paper). ---------------------------
+   zolo_kernel_launches: kernels this process has launched through libzolo.
+   zolo_profile(1) resets the statistics and brackets every later launch with
+   a CUDA event pair on its stream (a few microseconds each); zolo_profile(0)
+   stops.  zolo_profile_read synchronises on the pending events, fills up to
+   max_entries records (one per kernel class: launches, summed device time,
+   summed algorithmic flops and bytes as stated by each launch site) and
+   returns the number of classes. */
+typedef struct {
+  char name[32];
+  int64_t launches;
+  double ms;
+  double flops;
+  double bytes;
+} zolo_kstat_t;
+uint64_t zolo_kernel_launches(void);
+int zolo_profile(int enable);
+int zolo_profile_read(zolo_kstat_t* out, int max_entries);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ZOLO_H_ */

@@ -1,0 +1,268 @@
+"""Thin ctypes binding to libzolo.so (the C ABI declared in include/zolo.h).
+
+Argument marshalling only: every step of the decomposition runs in the CUDA
+library.  Matrices are torch tensors in column-major layout (stride(0) == 1),
+FP64, on the handle's device; PyTorch supplies device memory and the stream.
+If the shared library is missing this module raises at import time: there is
+no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libzolo.so")
+
+ZOLO_MAX_R = 8
+ZOLO_MAX_ITERS = 8
+ZOLO_FP64 = 0
+ZOLO_SPLIT_BF16 = 1
+
+ERRORS = {1: "ZOLO_ENONFINITE", 2: "ZOLO_ECHOL", 3: "ZOLO_ENOTCONV", 4: "ZOLO_ECUDA",
+          5: "ZOLO_ENOMEM", 6: "ZOLO_EEIG"}
+
+
+class ZoloOpts(ctypes.Structure):
+    _fields_ = [("r", ctypes.c_int), ("alpha", ctypes.c_double), ("beta", ctypes.c_double),
+                ("max_iter", ctypes.c_int), ("posteriori", ctypes.c_int),
+                ("ns_steps", ctypes.c_int), ("prec", ctypes.c_int), ("force_qr", ctypes.c_int)]
+
+
+class ZoloInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("r", ctypes.c_int),
+                ("used_qr", ctypes.c_int * ZOLO_MAX_ITERS),
+                ("ell", ctypes.c_double * (ZOLO_MAX_ITERS + 1)),
+                ("delta", ctypes.c_double * ZOLO_MAX_ITERS),
+                ("chol_fallbacks", ctypes.c_int), ("eig_sweeps", ctypes.c_int),
+                ("ms", ctypes.c_double)]
+
+
+class KStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("ms", ctypes.c_double),
+                ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libzolo.so is not built ({LIB_PATH}); run "
+                          "`python -m paper_1806_06204_gb300.build` (needs nvcc)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I64, I, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    DP = ctypes.POINTER(ctypes.c_double)
+    lib.zolo_opts_default.argtypes = [ctypes.POINTER(ZoloOpts)]
+    lib.zolo_opts_default.restype = None
+    lib.zolo_create.argtypes = [ctypes.POINTER(P), I]
+    lib.zolo_create.restype = I
+    lib.zolo_destroy.argtypes = [P]
+    lib.zolo_destroy.restype = I
+    lib.zolo_coefficients.argtypes = [D, I, DP, DP, DP, DP]
+    lib.zolo_coefficients.restype = I
+    lib.zolo_schedule.argtypes = [D, I, I, DP, ctypes.POINTER(I), ctypes.POINTER(I)]
+    lib.zolo_schedule.restype = I
+    pd_args = [P, P, I64, I64, I64, P, I64, P, I64, ctypes.POINTER(ZoloOpts),
+               ctypes.POINTER(ZoloInfo), P]
+    svd_args = [P, P, I64, I64, I64, P, I64, P, P, I64, ctypes.POINTER(ZoloOpts),
+                ctypes.POINTER(ZoloInfo), P]
+    for name, args in (("zolo_pd", pd_args), ("zolo_pd_host", pd_args),
+                       ("zolo_svd", svd_args), ("zolo_svd_host", svd_args)):
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = I
+    lib.zolo_strerror.argtypes = [I]
+    lib.zolo_strerror.restype = ctypes.c_char_p
+    lib.zolo_kernel_launches.argtypes = []
+    lib.zolo_kernel_launches.restype = ctypes.c_uint64
+    lib.zolo_profile.argtypes = [I]
+    lib.zolo_profile.restype = I
+    lib.zolo_profile_read.argtypes = [ctypes.POINTER(KStat), I]
+    lib.zolo_profile_read.restype = I
+    return lib
+
+
+LIB = _load()
+
+EXPORTED = ["zolo_opts_default", "zolo_create", "zolo_destroy", "zolo_coefficients",
+            "zolo_schedule", "zolo_pd", "zolo_svd", "zolo_pd_host", "zolo_svd_host",
+            "zolo_strerror", "zolo_kernel_launches", "zolo_profile", "zolo_profile_read"]
+
+
+def kernel_launches() -> int:
+    return int(LIB.zolo_kernel_launches())
+
+
+def profile(enable: bool) -> None:
+    LIB.zolo_profile(int(enable))
+
+
+def profile_read() -> dict:
+    """{class name: dict(launches, ms, flops, bytes)} accumulated since profile(True)."""
+    buf = (KStat * 16)()
+    k = LIB.zolo_profile_read(buf, 16)
+    return {buf[i].name.decode(): dict(launches=buf[i].launches, ms=buf[i].ms, flops=buf[i].flops,
+                                       bytes=buf[i].bytes) for i in range(min(k, 16))}
+
+
+class ZoloError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        msg = LIB.zolo_strerror(code).decode()
+        super().__init__(f"{where} returned {code} ({ERRORS.get(code, 'argument')}: {msg})")
+
+
+@dataclass
+class Info:
+    status: int
+    iters: int
+    r: int
+    used_qr: list
+    ell: list
+    delta: list
+    chol_fallbacks: int
+    eig_sweeps: int
+    ms: float
+
+    @staticmethod
+    def from_c(ci: ZoloInfo) -> "Info":
+        k = ci.iters
+        return Info(ci.status, k, ci.r, [bool(x) for x in ci.used_qr[:k]], list(ci.ell[:k + 1]),
+                    list(ci.delta[:k]), ci.chol_fallbacks, ci.eig_sweeps, ci.ms)
+
+
+def opts(beta: float, alpha: float = 1.0, r: int = 0, max_iter: int = 6, posteriori: bool = False,
+         ns_steps: int = 0, prec: int = ZOLO_FP64, force_qr: int = -1) -> ZoloOpts:
+    o = ZoloOpts()
+    LIB.zolo_opts_default(ctypes.byref(o))
+    o.r, o.alpha, o.beta, o.max_iter = r, alpha, beta, max_iter
+    o.posteriori, o.ns_steps, o.prec, o.force_qr = int(posteriori), ns_steps, prec, force_qr
+    return o
+
+
+def coefficients(ell: float, r: int):
+    c = (ctypes.c_double * (2 * r))()
+    a = (ctypes.c_double * r)()
+    mh, gap = ctypes.c_double(), ctypes.c_double()
+    e = LIB.zolo_coefficients(ell, r, c, a, ctypes.byref(mh), ctypes.byref(gap))
+    if e:
+        raise ZoloError(e, "zolo_coefficients")
+    return list(c), list(a), mh.value, gap.value
+
+
+def schedule(ell0: float, r: int = 0, max_iter: int = 8):
+    ells = (ctypes.c_double * (ZOLO_MAX_ITERS + 1))()
+    qr = (ctypes.c_int * ZOLO_MAX_ITERS)()
+    ru = ctypes.c_int()
+    k = LIB.zolo_schedule(ell0, r, max_iter, ells, qr, ctypes.byref(ru))
+    if k < 0:
+        raise ZoloError(k, "zolo_schedule")
+    return list(ells[:k + 1]), [bool(x) for x in qr[:k]], ru.value
+
+
+class Handle:
+    """Owns a libzolo handle (device binding and workspace cache)."""
+
+    def __init__(self, device: int = -1):
+        self._h = ctypes.c_void_p()
+        e = LIB.zolo_create(ctypes.byref(self._h), device)
+        if e:
+            raise ZoloError(e, "zolo_create")
+
+    def close(self):
+        if self._h:
+            LIB.zolo_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def ptr(self):
+        return self._h
+
+
+def _colmajor(t, name):
+    import torch
+    if t.dtype != torch.float64 or t.dim() != 2:
+        raise TypeError(f"{name} must be a 2-D float64 tensor")
+    if t.stride(0) != 1 or t.stride(1) < max(1, t.shape[0]):
+        raise ValueError(f"{name} must be column-major (stride(0) == 1)")
+    return t
+
+
+def empty_colmajor(m: int, n: int, device="cuda"):
+    import torch
+    return torch.empty((n, m), dtype=torch.float64, device=device).t()
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def zolo_pd(handle: Handle, A, o: ZoloOpts, Qp=None, H=None, stream=None, check=True):
+    """Polar decomposition of the device tensor A (m x n, column-major)."""
+    _colmajor(A, "A")
+    m, n = A.shape
+    Qp = empty_colmajor(m, n, A.device) if Qp is None else _colmajor(Qp, "Qp")
+    H = empty_colmajor(n, n, A.device) if H is None else _colmajor(H, "H")
+    info = ZoloInfo()
+    e = LIB.zolo_pd(handle.ptr, ctypes.c_void_p(A.data_ptr()), m, n, A.stride(1),
+                    ctypes.c_void_p(Qp.data_ptr()), Qp.stride(1), ctypes.c_void_p(H.data_ptr()),
+                    H.stride(1), ctypes.byref(o), ctypes.byref(info), _stream(stream))
+    if e and check:
+        raise ZoloError(e, "zolo_pd")
+    return Qp, H, Info.from_c(info)
+
+
+def zolo_svd(handle: Handle, A, o: ZoloOpts, stream=None, check=True):
+    """SVD of the device tensor A (m x n, column-major): (U, S, V, info)."""
+    import torch
+    _colmajor(A, "A")
+    m, n = A.shape
+    U = empty_colmajor(m, n, A.device)
+    V = empty_colmajor(n, n, A.device)
+    S = torch.empty(n, dtype=torch.float64, device=A.device)
+    info = ZoloInfo()
+    e = LIB.zolo_svd(handle.ptr, ctypes.c_void_p(A.data_ptr()), m, n, A.stride(1),
+                     ctypes.c_void_p(U.data_ptr()), U.stride(1), ctypes.c_void_p(S.data_ptr()),
+                     ctypes.c_void_p(V.data_ptr()), V.stride(1), ctypes.byref(o),
+                     ctypes.byref(info), _stream(stream))
+    if e and check:
+        raise ZoloError(e, "zolo_svd")
+    return U, S, V, Info.from_c(info)
+
+
+def _host_ptr(a):
+    import numpy as np
+    if a.dtype != np.float64 or not a.flags.f_contiguous:
+        raise ValueError("host matrices must be float64, Fortran (column-major) order")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def zolo_pd_host(handle: Handle, A, o: ZoloOpts, Qp, H, stream=None, check=True):
+    """Polar decomposition with host (numpy, Fortran-order) buffers; copies inside the call."""
+    m, n = A.shape
+    info = ZoloInfo()
+    e = LIB.zolo_pd_host(handle.ptr, _host_ptr(A), m, n, m, _host_ptr(Qp), m, _host_ptr(H), n,
+                         ctypes.byref(o), ctypes.byref(info), _stream(stream))
+    if e and check:
+        raise ZoloError(e, "zolo_pd_host")
+    return Info.from_c(info)
+
+
+def zolo_svd_host(handle: Handle, A, o: ZoloOpts, U, S, V, stream=None, check=True):
+    """SVD with host (numpy, Fortran-order) buffers; copies inside the call."""
+    m, n = A.shape
+    info = ZoloInfo()
+    e = LIB.zolo_svd_host(handle.ptr, _host_ptr(A), m, n, m, _host_ptr(U), m,
+                          ctypes.c_void_p(S.ctypes.data), _host_ptr(V), n, ctypes.byref(o),
+                          ctypes.byref(info), _stream(stream))
+    if e and check:
+        raise ZoloError(e, "zolo_svd_host")
+    return Info.from_c(info)

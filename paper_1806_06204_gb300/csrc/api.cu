@@ -1,0 +1,584 @@
+// C ABI of libzolo and the host orchestration of Zolo-PD / Zolo-SVD.
+//
+// zolo_pd follows Algorithm 1: X_0 = A / alpha, l_0 = beta / alpha, r from
+// Table 1's guidance, then the a-priori l-schedule (Algorithm 1 step (c),
+// stopping when 1 - l <= 1e-15 as Table 1 does) fixes every iteration's
+// coefficients before any GPU work, so the whole decomposition is queued
+// without a device round trip.  Each iteration forms the r shifted problems at
+// once (the paper's r process groups, Algorithm 3 step 4(c), become r batch
+// entries of one launch), in the QR form of Eq. (12) while the bound
+// (1 + c_1)/(l^2 + c_1) on kappa(Z_1) exceeds 100 and in the Cholesky form of
+// Algorithm 1 step (d) afterwards, and sums them on the device (the paper's
+// DGSUM2D, Algorithm 3 step 4(d)) fused into X_{k+1} = M_hat (X_k + sum T_j)
+// together with ||X_{k+1} - X_k||_F and ||X_{k+1}||_F.  H = (Qp^T A + A^T Qp)/2
+// uses the original A (Algorithm 1 step 5).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/zolo.h"
+#include "zolo_internal.h"
+
+using namespace zolo;
+
+struct zolo_handle_s {
+  int device = 0;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  void* io = nullptr;
+  size_t io_bytes = 0;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+};
+
+namespace {
+
+constexpr double kEps = 2.220446049250313e-16;
+
+// Bump allocator over one device block; with base == nullptr it only sizes.
+struct Carve {
+  char* base;
+  size_t off = 0;
+  explicit Carve(void* b) : base(static_cast<char*>(b)) {}
+  template <typename T>
+  T* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+struct PdBufs {
+  double *X, *Xn, *S, *M, *partials, *norms;
+  int* status;
+  double *Qp_int, *H_int;   // zolo_svd only
+  QrBuffers qr;
+  CholBuffers ch;
+  double *Y, *tmp;
+  int64_t strideY, strideTmp;
+  EigWork eig;
+};
+
+// Workspace layout for (m, n, r).  The QR, Cholesky and eigensolver regions
+// are never live at the same time and share one union region.
+size_t layout(void* base, int64_t m, int64_t n, int r, bool svd, PdBufs* b) {
+  Carve c(base);
+  PdBufs t{};
+  t.X = c.take<double>(m * n);
+  t.Xn = c.take<double>(m * n);
+  t.S = c.take<double>(m * n);
+  t.M = c.take<double>(n * n);
+  t.partials = c.take<double>(2 * 1024);
+  t.norms = c.take<double>(2 * (kMaxIters + 2));
+  t.status = c.take<int>(kStatSlots);
+  if (svd) {
+    t.Qp_int = c.take<double>(m * n);
+    t.H_int = c.take<double>(n * n);
+  }
+  const size_t union_start = (c.off + 255) & ~size_t(255);
+  // QR region
+  {
+    Carve q(base);
+    q.off = union_start;
+    const int64_t npan = (n + kQrNB - 1) / kQrNB;
+    t.qr.strideW = (m + n) * n;
+    t.qr.W = q.take<double>(r * t.qr.strideW);
+    t.qr.strideV = (m + kQrNB) * n;
+    t.qr.V = q.take<double>(r * t.qr.strideV);
+    t.qr.strideT = npan * kQrNB * kQrNB;
+    t.qr.T = q.take<double>(r * t.qr.strideT);
+    t.qr.strideW1 = kQrNB * n;
+    t.qr.W1 = q.take<double>(r * t.qr.strideW1);
+    t.qr.strideW2 = kQrNB * n;
+    t.qr.W2 = q.take<double>(r * t.qr.strideW2);
+    c.off = std::max(c.off, q.off);
+  }
+  // Cholesky region
+  {
+    Carve q(base);
+    q.off = union_start;
+    const int64_t nblk = (n + kCholNB - 1) / kCholNB;
+    t.ch.strideZ = n * n;
+    t.ch.Z = q.take<double>(r * t.ch.strideZ);
+    t.ch.strideRinv = nblk * kCholNB * kCholNB;
+    t.ch.Rinv = q.take<double>(r * t.ch.strideRinv);
+    t.strideY = m * n;
+    t.Y = q.take<double>(r * t.strideY);
+    t.strideTmp = m * kCholNB;
+    t.tmp = q.take<double>(r * t.strideTmp);
+    c.off = std::max(c.off, q.off);
+  }
+  // eigensolver region
+  if (svd) {
+    Carve q(base);
+    q.off = union_start;
+    const int64_t nblk = (n + kCholNB - 1) / kCholNB;
+    t.eig.R = q.take<double>(n * n);
+    t.eig.X = q.take<double>(n * n);
+    t.eig.HV = q.take<double>(std::max<int64_t>(n * n, 2 * 1024));
+    t.eig.Rinv = q.take<double>(nblk * kCholNB * kCholNB);
+    t.eig.lam = q.take<double>(std::max<int64_t>(n, 2));
+    t.eig.perm = q.take<int>(n);
+    t.eig.status = t.status;
+    c.off = std::max(c.off, q.off);
+  }
+  if (b) *b = t;
+  return c.off + 256;
+}
+
+int ensure_ws(zolo_handle_t h, size_t bytes) {
+  if (h->ws_bytes >= bytes) return 0;
+  if (h->ws) cudaFree(h->ws);
+  h->ws = nullptr;
+  h->ws_bytes = 0;
+  if (cudaMalloc(&h->ws, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return ZOLO_ENOMEM;
+  }
+  h->ws_bytes = bytes;
+  return 0;
+}
+
+#define CK(x)                                  \
+  do {                                         \
+    if ((x) != cudaSuccess) return ZOLO_ECUDA; \
+  } while (0)
+
+struct Run {
+  int64_t m, n;
+  int r;
+  PdBufs b;
+  cudaStream_t st;
+};
+
+// One Zolo-PD iteration from X into Xn; norms_k receives (||Xn - X||^2, ||Xn||^2).
+int iterate(const Run& R, const Coefficients& co, bool qr, const double* X, double* Xn,
+            double* norms_k) {
+  const int64_t m = R.m, n = R.n;
+  const int r = co.r;
+  const PdBufs& b = R.b;
+  if (qr) {
+    double sq[kMaxR];
+    for (int j = 0; j < r; ++j) sq[j] = std::sqrt(co.c[2 * j]);
+    CK(init_stacked(X, m, b.qr.W, b.qr.strideW, m, n, sq, r, R.st));
+    CK(structured_qr_q(b.qr, m, n, r, b.status, R.st));
+    GemmArgs g;   // S = sum_j a_j / sqrt(c_{2j-1}) Q1_j Q2_j^T   (Q2_j upper triangular)
+    g.M = (int)m; g.N = (int)n; g.K = (int)n; g.transA = 0; g.transB = 1;
+    g.A = b.qr.W; g.lda = m + n; g.strideA = b.qr.strideW;
+    g.B = b.qr.W + m; g.ldb = m + n; g.strideB = b.qr.strideW;
+    g.Cout = b.S; g.ldcout = m;
+    g.batch = r; g.reduce = 1; g.b_lower = 1;
+    for (int j = 0; j < r; ++j) g.alpha[j] = co.a[j] / sq[j];
+    CK(gemm_f64(g, R.st));
+    const double one = 1.0;
+    CK(combine(X, m, Xn, m, m, n, co.mhat, b.S, m, 0, &one, 1, b.partials, norms_k, b.status,
+               R.st));
+  } else {
+    GemmArgs g;   // G = X^T X (upper triangle), shared by every shift
+    g.M = g.N = (int)n; g.K = (int)m; g.transA = 1; g.transB = 0;
+    g.A = X; g.lda = m; g.B = X; g.ldb = m;
+    g.Cout = b.M; g.ldcout = n; g.c_upper = 1;
+    g.alpha[0] = 1.0;
+    CK(gemm_f64(g, R.st));
+    double shifts[kMaxR];
+    for (int j = 0; j < r; ++j) shifts[j] = co.c[2 * j];
+    CK(init_shifted(b.M, b.ch.Z, b.ch.strideZ, n, shifts, r, R.st));
+    CK(cholesky_upper_batched(b.ch, n, r, b.status, R.st));
+    CK(trsm_pair_batched(X, m, b.ch, b.Y, b.strideY, b.tmp, b.strideTmp, m, n, r, R.st));
+    CK(combine(X, m, Xn, m, m, n, co.mhat, b.Y, m, b.strideY, co.a, r, b.partials, norms_k,
+               b.status, R.st));
+  }
+  return 0;
+}
+
+int read_status(const Run& R, int* hstat) {
+  CK(cudaMemcpyAsync(hstat, R.b.status, sizeof(int) * kStatSlots, cudaMemcpyDeviceToHost, R.st));
+  CK(cudaStreamSynchronize(R.st));
+  return 0;
+}
+
+int validate(zolo_handle_t h, const void* A, int64_t m, int64_t n, int64_t lda, const void* P,
+             int64_t ldp, const void* Q, int64_t ldq, const zolo_opts_t* o) {
+  if (!h) return -1;
+  if (!A) return -2;
+  if (n < 1) return -4;
+  if (m < n) return -3;
+  if (lda < m) return -5;
+  if (!P) return -6;
+  if (ldp < m) return -7;
+  if (!Q) return -8;
+  if (ldq < n) return -9;
+  if (o) {
+    if (o->r < 0 || o->r > kMaxR || !std::isfinite(o->alpha) || !std::isfinite(o->beta) ||
+        !(o->beta > 0.0) || o->max_iter < 1 || o->max_iter > kMaxIters || o->ns_steps < 0 ||
+        o->ns_steps > 4 || o->prec != ZOLO_FP64 ||
+        o->force_qr < -1 || o->force_qr > 1 || (o->alpha > 0.0 && o->beta > o->alpha))
+      return -10;
+  } else {
+    return -10;   // beta has no default
+  }
+  return 0;
+}
+
+// The PD core on device buffers; Qp/H are written (may be internal buffers).
+int pd_core(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda, double* Qp,
+            int64_t ldq, double* H, int64_t ldh, const zolo_opts_t& o, zolo_info_t* info,
+            cudaStream_t st, bool svd, PdBufs* out_bufs) {
+  // alpha: caller's bound or ||A||_F
+  double alpha = o.alpha;
+  int r_sched = o.r;
+  // workspace needs r; an upper bound (r <= 8) is taken when r = 0 until alpha is known
+  if (alpha <= 0.0) {
+    PdBufs tmpb;
+    const size_t bytes = layout(nullptr, m, n, 1, svd, &tmpb);
+    if (int e = ensure_ws(h, bytes)) return e;
+    layout(h->ws, m, n, 1, svd, &tmpb);
+    CK(frob_norm2(A, lda, m, n, tmpb.partials, tmpb.norms, st));
+    double nrm2 = 0.0;
+    CK(cudaMemcpyAsync(&nrm2, tmpb.norms, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    alpha = std::sqrt(nrm2);
+    if (!(alpha > 0.0) || !std::isfinite(alpha)) return ZOLO_ENONFINITE;
+  }
+  const double ell0 = std::min(1.0, o.beta / alpha);
+  Schedule sch;
+  if (build_schedule(ell0, r_sched, o.max_iter, &sch) != 0) return -10;
+  const int r = sch.r;
+  Run R{m, n, r, {}, st};
+  const size_t bytes = layout(nullptr, m, n, r, svd, &R.b);
+  if (int e = ensure_ws(h, bytes)) return e;
+  layout(h->ws, m, n, r, svd, &R.b);
+  if (out_bufs) *out_bufs = R.b;
+  const PdBufs& b = R.b;
+  CK(cudaMemsetAsync(b.status, 0, sizeof(int) * kStatSlots, st));
+  CK(cudaMemsetAsync(b.norms, 0, sizeof(double) * 2 * (kMaxIters + 2), st));
+
+  double* X = b.X;
+  double* Xn = b.Xn;
+  CK(scale_copy(A, lda, X, m, m, n, 1.0 / alpha, st));
+  CK(check_finite(X, m, m, n, b.status, st));
+
+  info->r = r;
+  info->ell[0] = ell0;
+  info->chol_fallbacks = 0;
+  int it = 0;
+  int hstat[kStatSlots];
+  std::vector<Coefficients> cos;
+  std::vector<bool> qrs;
+  for (int k = 0; k < sch.iters; ++k) {
+    const Coefficients& co = sch.co[k];
+    bool qr = o.force_qr == 1 ? true : (o.force_qr == 0 ? false : sch.use_qr[k]);
+    if (int e = iterate(R, co, qr, X, Xn, b.norms + 2 * it)) return e;
+    if (!qr) {
+      // a non-positive Cholesky pivot: redo this iteration in the QR form (X is intact)
+      if (int e = read_status(R, hstat)) return e;
+      if (hstat[kStatCholFail]) {
+        CK(cudaMemsetAsync(b.status + kStatCholFail, 0, sizeof(int), st));
+        qr = true;
+        info->chol_fallbacks++;
+        if (int e = iterate(R, co, qr, X, Xn, b.norms + 2 * it)) return e;
+      }
+    }
+    info->used_qr[it] = qr ? 1 : 0;
+    info->ell[it + 1] = sch.ell[k + 1];
+    std::swap(X, Xn);
+    ++it;
+  }
+  // Algorithm 1 step (d), applied literally when asked for
+  int status = ZOLO_OK;
+  if (o.posteriori && it > 0) {
+    const double thr = std::pow(kEps, 1.0 / (2 * r + 1));
+    double ell = sch.ell[sch.iters];
+    while (true) {
+      double nk[2];
+      CK(cudaMemcpyAsync(nk, b.norms + 2 * (it - 1), sizeof(nk), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      const double delta = std::sqrt(nk[0] / nk[1]);
+      if (delta <= thr) break;
+      if (it >= o.max_iter) {
+        status = ZOLO_ENOTCONV;
+        break;
+      }
+      Coefficients co;
+      compute_coefficients(std::min(1.0, ell), r, &co);
+      if (int e = iterate(R, co, false, X, Xn, b.norms + 2 * it)) return e;
+      if (int e = read_status(R, hstat)) return e;
+      bool qr = false;
+      if (hstat[kStatCholFail]) {
+        CK(cudaMemsetAsync(b.status + kStatCholFail, 0, sizeof(int), st));
+        qr = true;
+        info->chol_fallbacks++;
+        if (int e = iterate(R, co, true, X, Xn, b.norms + 2 * it)) return e;
+      }
+      ell = 1.0 - co.gap;
+      info->used_qr[it] = qr;
+      info->ell[it + 1] = ell;
+      std::swap(X, Xn);
+      ++it;
+    }
+  }
+  // Newton-Schulz refinement steps
+  for (int s = 0; s < o.ns_steps; ++s) {
+    GemmArgs g;
+    g.M = g.N = (int)n; g.K = (int)m; g.transA = 1;
+    g.A = X; g.lda = m; g.B = X; g.ldb = m; g.Cout = b.M; g.ldcout = n;
+    g.alpha[0] = 1.0;
+    CK(gemm_f64(g, st));
+    GemmArgs u;
+    u.M = (int)m; u.N = (int)n; u.K = (int)n;
+    u.A = X; u.lda = m; u.B = b.M; u.ldb = n;
+    u.Cin = X; u.ldcin = m; u.beta = 1.5; u.Cout = Xn; u.ldcout = m;
+    u.alpha[0] = -0.5;
+    CK(gemm_f64(u, st));
+    std::swap(X, Xn);
+  }
+  // H = (Qp^T A + A^T Qp) / 2 with the original A
+  {
+    GemmArgs g;
+    g.M = g.N = (int)n; g.K = (int)m; g.transA = 1;
+    g.A = X; g.lda = m; g.B = A; g.ldb = lda; g.Cout = b.M; g.ldcout = n;
+    g.alpha[0] = 1.0;
+    CK(gemm_f64(g, st));
+    CK(symmetrize(b.M, n, H, ldh, n, st));
+    CK(copy_matrix(X, m, Qp, ldq, m, n, st));
+  }
+  // final status and norms
+  double hn[2 * (kMaxIters + 2)];
+  CK(cudaMemcpyAsync(hn, b.norms, sizeof(hn), cudaMemcpyDeviceToHost, st));
+  if (int e = read_status(R, hstat)) return e;
+  info->iters = it;
+  for (int k = 0; k < it; ++k) info->delta[k] = hn[2 * k + 1] > 0 ? std::sqrt(hn[2 * k] / hn[2 * k + 1]) : 0.0;
+  if (hstat[kStatNonFinite]) return ZOLO_ENONFINITE;
+  if (hstat[kStatCholFail]) return ZOLO_ECHOL;
+  return status;
+}
+
+}  // namespace
+
+extern "C" {
+
+void zolo_opts_default(zolo_opts_t* o) {
+  if (!o) return;
+  o->r = 0;
+  o->alpha = 1.0;
+  o->beta = 0.0;
+  o->max_iter = 6;
+  o->posteriori = 0;
+  o->ns_steps = 0;
+  o->prec = ZOLO_FP64;
+  o->force_qr = -1;
+}
+
+int zolo_create(zolo_handle_t* handle, int device) {
+  if (!handle) return -1;
+  int dev = device;
+  if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) return ZOLO_ECUDA;
+  if (cudaSetDevice(dev) != cudaSuccess) return ZOLO_ECUDA;
+  auto* h = new zolo_handle_s();
+  h->device = dev;
+  if (cudaEventCreate(&h->e0) != cudaSuccess || cudaEventCreate(&h->e1) != cudaSuccess) {
+    delete h;
+    return ZOLO_ECUDA;
+  }
+  *handle = h;
+  return 0;
+}
+
+int zolo_destroy(zolo_handle_t h) {
+  if (!h) return -1;
+  cudaSetDevice(h->device);
+  if (h->ws) cudaFree(h->ws);
+  if (h->io) cudaFree(h->io);
+  if (h->e0) cudaEventDestroy(h->e0);
+  if (h->e1) cudaEventDestroy(h->e1);
+  delete h;
+  return 0;
+}
+
+int zolo_coefficients(double ell, int r, double* c, double* a, double* Mhat, double* gap) {
+  Coefficients co;
+  const int e = compute_coefficients(ell, r, &co);
+  if (e) return e;
+  if (c) for (int i = 0; i < 2 * r; ++i) c[i] = co.c[i];
+  if (a) for (int j = 0; j < r; ++j) a[j] = co.a[j];
+  if (Mhat) *Mhat = co.mhat;
+  if (gap) *gap = co.gap;
+  return 0;
+}
+
+int zolo_schedule(double ell0, int r, int max_iter, double* ells, int* used_qr, int* r_used) {
+  Schedule s;
+  const int e = build_schedule(ell0, r, max_iter, &s);
+  if (e) return e;
+  if (ells) for (int k = 0; k <= s.iters; ++k) ells[k] = s.ell[k];
+  if (used_qr) for (int k = 0; k < s.iters; ++k) used_qr[k] = s.use_qr[k] ? 1 : 0;
+  if (r_used) *r_used = s.r;
+  return s.iters;
+}
+
+int zolo_pd(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda, double* Qp,
+            int64_t ldq, double* H, int64_t ldh, const zolo_opts_t* opts, zolo_info_t* info,
+            void* stream) {
+  if (int e = validate(h, A, m, n, lda, Qp, ldq, H, ldh, opts)) return e;
+  if (!info) return -11;
+  std::memset(info, 0, sizeof(*info));
+  if (cudaSetDevice(h->device) != cudaSuccess) return info->status = ZOLO_ECUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaEventRecord(h->e0, st);
+  int e = pd_core(h, A, m, n, lda, Qp, ldq, H, ldh, *opts, info, st, false, nullptr);
+  cudaEventRecord(h->e1, st);
+  if (cudaEventSynchronize(h->e1) == cudaSuccess) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->e0, h->e1);
+    info->ms = ms;
+  }
+  info->status = e;
+  return e;
+}
+
+int zolo_svd(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda, double* U,
+             int64_t ldu, double* S, double* V, int64_t ldv, const zolo_opts_t* opts,
+             zolo_info_t* info, void* stream) {
+  if (int e = validate(h, A, m, n, lda, U, ldu, V, ldv, opts)) return e;
+  if (!S) return -8;
+  if (!info) return -12;
+  std::memset(info, 0, sizeof(*info));
+  if (cudaSetDevice(h->device) != cudaSuccess) return info->status = ZOLO_ECUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaEventRecord(h->e0, st);
+  // Qp and H go to internal buffers carved ahead of the union region; their
+  // offsets do not depend on r, and sizing with r = 8 when r is chosen by the
+  // schedule means pd_core never has to grow (and move) the workspace.
+  PdBufs b{};
+  int e = 0;
+  const int r_size = opts->r == 0 ? kMaxR : opts->r;
+  {
+    const size_t bytes = layout(nullptr, m, n, r_size, true, &b);
+    if ((e = ensure_ws(h, bytes)) != 0) return info->status = e;
+    layout(h->ws, m, n, r_size, true, &b);
+  }
+  double* Qp = b.Qp_int;
+  double* Hm = b.H_int;
+  e = pd_core(h, A, m, n, lda, Qp, m, Hm, n, *opts, info, st, true, &b);
+  if (e == 0) {
+    std::vector<double> lam(n);
+    int sweeps = 0;
+    const int ee = eig_sym_jacobi(Hm, n, n, V, ldv, lam.data(), b.eig, &sweeps, st);
+    info->eig_sweeps = sweeps;
+    if (ee == 1) e = ZOLO_ECUDA;
+    else if (ee == 2) e = ZOLO_EEIG;
+    if (e == 0) {
+      // U = Qp V, with the sign of u_i flipped where lambda_i < 0 (sigma_i = |lambda_i|)
+      std::vector<double> sv(n), sg(n);
+      for (int64_t i = 0; i < n; ++i) {
+        sv[i] = std::fabs(lam[i]);
+        sg[i] = lam[i] < 0.0 ? -1.0 : 1.0;
+      }
+      GemmArgs g;
+      g.M = (int)m; g.N = (int)n; g.K = (int)n;
+      g.A = Qp; g.lda = m; g.B = V; g.ldb = ldv; g.Cout = U; g.ldcout = ldu;
+      g.alpha[0] = 1.0;
+      if (gemm_f64(g, st) != cudaSuccess) e = ZOLO_ECUDA;
+      if (e == 0 && cudaMemcpyAsync(b.eig.lam, sg.data(), sizeof(double) * n,
+                                    cudaMemcpyHostToDevice, st) != cudaSuccess)
+        e = ZOLO_ECUDA;
+      if (e == 0 && scale_columns(U, ldu, m, n, b.eig.lam, 0, st) != cudaSuccess) e = ZOLO_ECUDA;
+      if (e == 0 && cudaMemcpyAsync(S, sv.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st) !=
+                        cudaSuccess)
+        e = ZOLO_ECUDA;
+      if (cudaStreamSynchronize(st) != cudaSuccess) e = ZOLO_ECUDA;
+    }
+  }
+  cudaEventRecord(h->e1, st);
+  if (cudaEventSynchronize(h->e1) == cudaSuccess) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->e0, h->e1);
+    info->ms = ms;
+  }
+  info->status = e;
+  return e;
+}
+
+static int ensure_io(zolo_handle_t h, size_t bytes) {
+  if (h->io_bytes >= bytes) return 0;
+  if (h->io) cudaFree(h->io);
+  h->io = nullptr;
+  h->io_bytes = 0;
+  if (cudaMalloc(&h->io, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return ZOLO_ENOMEM;
+  }
+  h->io_bytes = bytes;
+  return 0;
+}
+
+int zolo_pd_host(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda, double* Qp,
+                 int64_t ldq, double* H, int64_t ldh, const zolo_opts_t* opts, zolo_info_t* info,
+                 void* stream) {
+  if (int e = validate(h, A, m, n, lda, Qp, ldq, H, ldh, opts)) return e;
+  if (!info) return -11;
+  if (cudaSetDevice(h->device) != cudaSuccess) return ZOLO_ECUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t mn = (size_t)m * n, nn = (size_t)n * n;
+  if (int e = ensure_io(h, sizeof(double) * (2 * mn + nn) + 1024)) return e;
+  double* dA = static_cast<double*>(h->io);
+  double* dQ = dA + mn;
+  double* dH = dQ + mn;
+  if (cudaMemcpy2DAsync(dA, m * sizeof(double), A, lda * sizeof(double), m * sizeof(double), n,
+                        cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return ZOLO_ECUDA;
+  int e = zolo_pd(h, dA, m, n, m, dQ, m, dH, n, opts, info, stream);
+  if (e > 0 && e != ZOLO_ENOTCONV) return e;
+  if (cudaMemcpy2DAsync(Qp, ldq * sizeof(double), dQ, m * sizeof(double), m * sizeof(double), n,
+                        cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpy2DAsync(H, ldh * sizeof(double), dH, n * sizeof(double), n * sizeof(double), n,
+                        cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return ZOLO_ECUDA;
+  return e;
+}
+
+int zolo_svd_host(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda, double* U,
+                  int64_t ldu, double* S, double* V, int64_t ldv, const zolo_opts_t* opts,
+                  zolo_info_t* info, void* stream) {
+  if (int e = validate(h, A, m, n, lda, U, ldu, V, ldv, opts)) return e;
+  if (!S) return -8;
+  if (!info) return -12;
+  if (cudaSetDevice(h->device) != cudaSuccess) return ZOLO_ECUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t mn = (size_t)m * n, nn = (size_t)n * n;
+  if (int e = ensure_io(h, sizeof(double) * (2 * mn + nn + n) + 2048)) return e;
+  double* dA = static_cast<double*>(h->io);
+  double* dU = dA + mn;
+  double* dV = dU + mn;
+  double* dS = dV + nn;
+  if (cudaMemcpy2DAsync(dA, m * sizeof(double), A, lda * sizeof(double), m * sizeof(double), n,
+                        cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return ZOLO_ECUDA;
+  int e = zolo_svd(h, dA, m, n, m, dU, m, dS, dV, n, opts, info, stream);
+  if (e > 0 && e != ZOLO_ENOTCONV) return e;
+  if (cudaMemcpy2DAsync(U, ldu * sizeof(double), dU, m * sizeof(double), m * sizeof(double), n,
+                        cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpy2DAsync(V, ldv * sizeof(double), dV, n * sizeof(double), n * sizeof(double), n,
+                        cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(S, dS, n * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return ZOLO_ECUDA;
+  return e;
+}
+
+const char* zolo_strerror(int code) {
+  switch (code) {
+    case ZOLO_OK: return "success";
+    case ZOLO_ENONFINITE: return "NaN or Inf in the input or an iterate";
+    case ZOLO_ECHOL: return "Cholesky breakdown";
+    case ZOLO_ENOTCONV: return "a-posteriori test failed at max_iter";
+    case ZOLO_ECUDA: return "CUDA runtime error";
+    case ZOLO_ENOMEM: return "device memory allocation failed";
+    case ZOLO_EEIG: return "Jacobi eigensolver did not converge";
+    default: return code < 0 ? "illegal argument" : "unknown error";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,114 @@
+// Launch counting and opt-in per-kernel-class timing with CUDA events.
+//
+// Every launch site constructs a ProfScope around its <<<>>>: the process-wide
+// counter always advances; while profiling is on, an event pair is recorded on
+// the launching stream and the pair is resolved (one synchronisation) when the
+// statistics are read.  Flops/bytes are the algorithmic counts the call site
+// states for that launch.
+#include <atomic>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "../../include/zolo.h"
+#include "zolo_internal.h"
+
+namespace zolo {
+namespace {
+
+const char* kClassNames[kProfClasses] = {"gemm_f64", "qr_panel", "chol_diag", "jacobi_round",
+                                         "combine", "other"};
+
+struct Pending {
+  int cls;
+  cudaEvent_t a, b;
+  double flops, bytes;
+};
+
+std::atomic<uint64_t> g_launches{0};
+std::atomic<bool> g_on{false};
+std::mutex g_mu;
+std::vector<Pending> g_pending;
+std::vector<cudaEvent_t> g_pool;
+zolo_kstat_t g_acc[kProfClasses];
+
+cudaEvent_t take_event() {
+  if (!g_pool.empty()) {
+    cudaEvent_t e = g_pool.back();
+    g_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void resolve_locked() {
+  for (Pending& p : g_pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      zolo_kstat_t& s = g_acc[p.cls];
+      s.launches += 1;
+      s.ms += ms;
+      s.flops += p.flops;
+      s.bytes += p.bytes;
+    }
+    g_pool.push_back(p.a);
+    g_pool.push_back(p.b);
+  }
+  g_pending.clear();
+}
+
+void reset_locked() {
+  resolve_locked();
+  for (int c = 0; c < kProfClasses; ++c) {
+    std::memset(&g_acc[c], 0, sizeof(g_acc[c]));
+    std::strncpy(g_acc[c].name, kClassNames[c], sizeof(g_acc[c].name) - 1);
+  }
+}
+
+}  // namespace
+
+ProfScope::ProfScope(int cls, cudaStream_t st, double flops, double bytes)
+    : cls_(cls), st_(st), flops_(flops), bytes_(bytes) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  if (g_on.load(std::memory_order_relaxed)) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    a_ = take_event();
+    cudaEventRecord(static_cast<cudaEvent_t>(a_), st_);
+  }
+}
+
+ProfScope::~ProfScope() {
+  if (!a_) return;
+  std::lock_guard<std::mutex> lk(g_mu);
+  cudaEvent_t b = take_event();
+  cudaEventRecord(b, st_);
+  g_pending.push_back({cls_, static_cast<cudaEvent_t>(a_), b, flops_, bytes_});
+  if (g_pending.size() > 100000) resolve_locked();
+}
+
+}  // namespace zolo
+
+using namespace zolo;
+
+extern "C" {
+
+uint64_t zolo_kernel_launches(void) { return g_launches.load(); }
+
+int zolo_profile(int enable) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (enable) reset_locked();
+  g_on.store(enable != 0);
+  return 0;
+}
+
+int zolo_profile_read(zolo_kstat_t* out, int max_entries) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  resolve_locked();
+  const int n = max_entries < kProfClasses ? max_entries : kProfClasses;
+  for (int c = 0; c < n && out; ++c) out[c] = g_acc[c];
+  return kProfClasses;
+}
+
+}  // extern "C"

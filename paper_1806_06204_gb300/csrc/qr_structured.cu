@@ -1,0 +1,231 @@
+// Structured Householder QR of the stacked matrix [X; sqrt(c) I] (Section 3.1,
+// Eq. 12) and the explicit thin Q = [Q1; Q2] (the structured ORGQR).
+//
+// Layout: the stacked (m+n) x n matrix is stored densely, column-major with
+// ld = m + n (top block rows 0..m-1, bottom block rows m..m+n-1).  The bottom
+// block starts diagonal; Householder vector c (column c) is non-zero only on
+// top rows c..m-1 and bottom rows 0..c, i.e. on the CONTIGUOUS stored rows
+// c..m+c: m+1 entries instead of m+n-c (the paper's "at most m+1 nonzero
+// elements").  A panel of NB columns starting at c0 therefore works on the row
+// window [c0, c0 + m + NB), and the compact-WY trailing update (I - V T V^T)
+// touches only that window: every step costs O((m + NB) NB n) whatever n is.
+//
+// Q2 (the bottom block of Q) stays exactly upper triangular: the explicit V
+// holds exact zeros outside each reflector's support, so every product that the
+// structure makes zero is an exact zero in floating point too.
+#include <cmath>
+
+#include "zolo_internal.h"
+
+namespace zolo {
+namespace {
+
+constexpr int kPanelThreads = 512;
+
+// One CTA per shift j.  Factors panel columns [c0, c0 + nbp) of W_j in place
+// (R on and above the diagonal, Householder vectors below it, as LAPACK), writes
+// the explicit reflectors (unit diagonal, exact zeros elsewhere) to V_j's
+// columns [c0, c0 + nbp) with rows relative to c0, and the upper-triangular
+// compact-WY factor T (H_0 ... H_{nbp-1} = I - V T V^T) to T_j's panel slot.
+template <int NB>
+__global__ void __launch_bounds__(kPanelThreads)
+qr_panel_kernel(double* W, int64_t strideW, int64_t ldw, int64_t m, int64_t c0, int nbp, double* V,
+                int64_t strideV, int64_t ldv, double* T, int64_t strideT, int* status) {
+  __shared__ double red[kPanelThreads / 32][NB];
+  __shared__ double dots[NB];
+  __shared__ double Ts[NB][NB + 1];
+  __shared__ double s_tau, s_scal, s_beta;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int kWarps = kPanelThreads / 32;
+  double* Wj = W + blockIdx.x * strideW;
+  double* Vp = V + blockIdx.x * strideV + c0 * ldv;
+  double* Tp = T + blockIdx.x * strideT + (c0 / NB) * (int64_t)(NB * NB);
+
+  for (int e = tid; e < NB * (NB + 1); e += blockDim.x) (&Ts[0][0])[e] = 0.0;
+
+  for (int i = 0; i < nbp; ++i) {
+    const int64_t c = c0 + i;
+    double* col = Wj + c * ldw;
+    // ---- 1. norm of the tail x[c+1 .. m+c]
+    double ss = 0.0;
+    for (int64_t r = c + 1 + tid; r <= m + c; r += kPanelThreads) {
+      const double v = col[r];
+      ss = fma(v, v, ss);
+    }
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    __syncthreads();
+    if (lane == 0) red[warp][0] = ss;
+    __syncthreads();
+    if (tid == 0) {
+      double s = 0.0;
+      for (int w = 0; w < kWarps; ++w) s += red[w][0];
+      const double alpha = col[c];
+      double beta, tau, scal;
+      if (s == 0.0) {
+        beta = alpha; tau = 0.0; scal = 0.0;
+      } else {
+        beta = -copysign(sqrt(fma(alpha, alpha, s)), alpha);
+        tau = (beta - alpha) / beta;
+        scal = 1.0 / (alpha - beta);
+      }
+      if (!isfinite(beta) || !isfinite(tau)) atomicOr(status + kStatNonFinite, 1);
+      s_beta = beta; s_tau = tau; s_scal = scal;
+    }
+    __syncthreads();
+    const double tau = s_tau, scal = s_scal;
+    // ---- 2. v = x / (alpha - beta), explicit copy into V (window rows c0 .. c0+m+NB-1)
+    double* Vcol = Vp + (int64_t)i * ldv;
+    for (int64_t rel = tid; rel < m + NB; rel += kPanelThreads) {
+      const int64_t r = c0 + rel;
+      double v;
+      if (r < c || r > m + c) {
+        v = 0.0;
+      } else if (r == c) {
+        v = 1.0;
+      } else {
+        v = col[r] * scal;
+        col[r] = v;
+      }
+      Vcol[rel] = v;
+    }
+    __syncthreads();
+    if (tid == 0) col[c] = s_beta;
+    // ---- 3. dots of v with the later panel columns (for the update) and with
+    //         the earlier reflectors (for T), in one pass over the support
+    double acc[NB];
+#pragma unroll
+    for (int q = 0; q < NB; ++q) acc[q] = 0.0;
+    for (int64_t r = c + tid; r <= m + c; r += kPanelThreads) {
+      const double v = Vcol[r - c0];
+#pragma unroll
+      for (int q = 0; q < NB; ++q) {
+        if (q < nbp && q != i) {
+          const double o = q > i ? Wj[r + (c0 + q) * ldw] : Vp[(r - c0) + (int64_t)q * ldv];
+          acc[q] = fma(v, o, acc[q]);
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      double v = acc[q];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) red[warp][q] = v;
+    }
+    __syncthreads();
+    if (tid < NB) {
+      double s = 0.0;
+      for (int w = 0; w < kWarps; ++w) s += red[w][tid];
+      dots[tid] = s;
+    }
+    __syncthreads();
+    // ---- 4. apply H_i to the later panel columns: W[:, q] -= tau * dots[q] * v
+    for (int64_t r = c + tid; r <= m + c; r += kPanelThreads) {
+      const double v = Vcol[r - c0];
+#pragma unroll
+      for (int q = 0; q < NB; ++q) {
+        if (q > i && q < nbp) {
+          double* p = Wj + r + (c0 + q) * ldw;
+          *p = fma(-tau * dots[q], v, *p);
+        }
+      }
+    }
+    // ---- 5. T(0:i, i) = -tau T(0:i, 0:i) V^T v_i,  T(i, i) = tau
+    if (tid < i) {
+      double s = 0.0;
+      for (int p = tid; p < i; ++p) s = fma(Ts[tid][p], dots[p], s);
+      Ts[tid][i] = -tau * s;
+    }
+    if (tid == 0) Ts[i][i] = tau;
+    __syncthreads();
+  }
+  for (int e = tid; e < NB * NB; e += kPanelThreads) Tp[e] = Ts[e % NB][e / NB];
+}
+
+}  // namespace
+
+cudaError_t structured_qr_q(const QrBuffers& b, int64_t m, int64_t n, int r, int* status,
+                            cudaStream_t st) {
+  constexpr int NB = kQrNB;
+  const int64_t ldw = m + n;
+  const int64_t ldv = m + NB;
+  cudaError_t err;
+  const int npanels = (int)((n + NB - 1) / NB);
+  // ---------------- factorisation (structured GEQRF)
+  for (int p = 0; p < npanels; ++p) {
+    const int64_t c0 = (int64_t)p * NB;
+    const int nbp = (int)(n - c0 < NB ? n - c0 : NB);
+    {
+      ProfScope ps(kProfPanel, st, 3.0 * r * (double)(m + 1) * nbp * nbp,
+                   8.0 * r * (double)(m + NB) * nbp * 2.0);
+      qr_panel_kernel<NB><<<r, kPanelThreads, 0, st>>>(b.W, b.strideW, ldw, m, c0, nbp, b.V,
+                                                        b.strideV, ldv, b.T, b.strideT, status);
+    }
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    const int64_t ntr = n - c0 - nbp;
+    if (ntr <= 0) continue;
+    const double* Vp = b.V + c0 * ldv;
+    double* C = b.W + c0 + (c0 + nbp) * ldw;   // window rows [c0, c0+m+nbp), trailing columns
+    const double* Tp = b.T + (int64_t)p * NB * NB;
+    GemmArgs g;
+    // W1 = V^T C
+    g.M = nbp; g.N = (int)ntr; g.K = (int)(m + nbp); g.transA = 1; g.transB = 0;
+    g.A = Vp; g.lda = ldv; g.strideA = b.strideV;
+    g.B = C; g.ldb = ldw; g.strideB = b.strideW;
+    g.Cout = b.W1; g.ldcout = NB; g.strideCout = b.strideW1;
+    g.batch = r;
+    for (int j = 0; j < r; ++j) g.alpha[j] = 1.0;
+    if ((err = gemm_f64(g, st)) != cudaSuccess) return err;
+    // W2 = T^T W1
+    GemmArgs h = g;
+    h.K = nbp; h.transA = 1;
+    h.A = Tp; h.lda = NB; h.strideA = b.strideT;
+    h.B = b.W1; h.ldb = NB; h.strideB = b.strideW1;
+    h.Cout = b.W2; h.strideCout = b.strideW2;
+    if ((err = gemm_f64(h, st)) != cudaSuccess) return err;
+    // C -= V W2
+    GemmArgs u = g;
+    u.M = (int)(m + nbp); u.N = (int)ntr; u.K = nbp; u.transA = 0; u.transB = 0;
+    u.A = Vp; u.lda = ldv; u.strideA = b.strideV;
+    u.B = b.W2; u.ldb = NB; u.strideB = b.strideW2;
+    u.Cin = C; u.ldcin = ldw; u.strideCin = b.strideW; u.beta = 1.0;
+    u.Cout = C; u.ldcout = ldw; u.strideCout = b.strideW;
+    for (int j = 0; j < r; ++j) u.alpha[j] = -1.0;
+    if ((err = gemm_f64(u, st)) != cudaSuccess) return err;
+  }
+  // ---------------- explicit Q (structured ORGQR), overwriting W
+  if ((err = init_q_identity(b.W, b.strideW, m, n, r, st)) != cudaSuccess) return err;
+  for (int p = npanels - 1; p >= 0; --p) {
+    const int64_t c0 = (int64_t)p * NB;
+    const int nbp = (int)(n - c0 < NB ? n - c0 : NB);
+    const int64_t ncol = n - c0;
+    const double* Vp = b.V + c0 * ldv;
+    double* C = b.W + c0 + c0 * ldw;
+    const double* Tp = b.T + (int64_t)p * NB * NB;
+    GemmArgs g;
+    g.M = nbp; g.N = (int)ncol; g.K = (int)(m + nbp); g.transA = 1; g.transB = 0;
+    g.A = Vp; g.lda = ldv; g.strideA = b.strideV;
+    g.B = C; g.ldb = ldw; g.strideB = b.strideW;
+    g.Cout = b.W1; g.ldcout = NB; g.strideCout = b.strideW1;
+    g.batch = r;
+    for (int j = 0; j < r; ++j) g.alpha[j] = 1.0;
+    if ((err = gemm_f64(g, st)) != cudaSuccess) return err;
+    GemmArgs h = g;   // W2 = T W1
+    h.K = nbp; h.transA = 0;
+    h.A = Tp; h.lda = NB; h.strideA = b.strideT;
+    h.B = b.W1; h.ldb = NB; h.strideB = b.strideW1;
+    h.Cout = b.W2; h.strideCout = b.strideW2;
+    if ((err = gemm_f64(h, st)) != cudaSuccess) return err;
+    GemmArgs u = g;   // C -= V W2
+    u.M = (int)(m + nbp); u.N = (int)ncol; u.K = nbp; u.transA = 0; u.transB = 0;
+    u.A = Vp; u.lda = ldv; u.strideA = b.strideV;
+    u.B = b.W2; u.ldb = NB; u.strideB = b.strideW2;
+    u.Cin = C; u.ldcin = ldw; u.strideCin = b.strideW; u.beta = 1.0;
+    u.Cout = C; u.ldcout = ldw; u.strideCout = b.strideW;
+    for (int j = 0; j < r; ++j) u.alpha[j] = -1.0;
+    if ((err = gemm_f64(u, st)) != cudaSuccess) return err;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace zolo

@@ -1,0 +1,177 @@
+// Internal declarations shared by the libzolo translation units.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#ifdef __CUDACC__
+#include <cuda_runtime.h>
+#else
+typedef struct CUstream_st* cudaStream_t;
+#endif
+
+namespace zolo {
+
+constexpr int kMaxR = 8;
+constexpr int kMaxIters = 8;
+constexpr double kTable1Tol = 1e-15;
+
+// ---------------------------------------------------------------- coefficients
+struct Coefficients {
+  double ell = 0.0;
+  int r = 0;
+  double c[2 * kMaxR] = {};   // c_1 .. c_{2r}
+  double a[kMaxR] = {};       // a_1 .. a_r
+  double mhat = 0.0;          // M_hat
+  double gap = 0.0;           // 1 - Zhat(l; l)
+};
+
+struct Schedule {
+  int r = 0;
+  int iters = 0;
+  bool converged = false;
+  double ell[kMaxIters + 1] = {};
+  bool use_qr[kMaxIters] = {};
+  Coefficients co[kMaxIters];
+};
+
+int compute_coefficients(double ell, int r, Coefficients* out);
+bool qr_form_needed(const Coefficients& co);
+int build_schedule(double ell0, int r, int max_iter, Schedule* out);
+
+#ifdef __CUDACC__
+
+// ------------------------------------------------------------- launch scopes
+enum ProfClass { kProfGemm = 0, kProfPanel, kProfCholDiag, kProfJacobi, kProfCombine, kProfOther,
+                 kProfClasses };
+// Counts the launch made inside its scope and, while profiling is on, brackets
+// it with CUDA events on `st`.  flops/bytes: the launch's algorithmic work.
+class ProfScope {
+ public:
+  ProfScope(int cls, cudaStream_t st, double flops = 0.0, double bytes = 0.0);
+  ~ProfScope();
+  ProfScope(const ProfScope&) = delete;
+  ProfScope& operator=(const ProfScope&) = delete;
+
+ private:
+  int cls_;
+  cudaStream_t st_;
+  double flops_, bytes_;
+  void* a_ = nullptr;
+};
+
+// ----------------------------------------------------------------- device flags
+// A small device array of int counters written by kernels and read once at the
+// end of a call.
+enum StatusSlot {
+  kStatNonFinite = 0,   // a NaN/Inf was produced
+  kStatCholFail = 1,    // non-positive pivot in a Cholesky diagonal block
+  kStatJacobiRot = 2,   // rotations applied in the current Jacobi sweep
+  kStatSlots = 4
+};
+
+// ------------------------------------------------------------------- FP64 GEMM
+// C_out[b] = beta * C_in[b] + alpha[b] * op(A[b]) op(B[b])          (reduce = 0)
+// C_out    = beta * C_in    + sum_b alpha[b] * op(A[b]) op(B[b])    (reduce = 1)
+// Column-major, op = N or T.  Structural flags let the kernel skip known zeros:
+//   b_lower  : op(B)[k][j] == 0 for k < j (e.g. op(B) = Q2^T with Q2 upper)
+//   c_upper  : only tiles touching the upper triangle (i <= j) are computed
+constexpr int kGemmMaxBatch = 16;
+struct GemmArgs {
+  int M = 0, N = 0, K = 0;
+  int transA = 0, transB = 0;
+  const double* A = nullptr; int64_t lda = 0; int64_t strideA = 0;
+  const double* B = nullptr; int64_t ldb = 0; int64_t strideB = 0;
+  const double* Cin = nullptr; int64_t ldcin = 0; int64_t strideCin = 0;
+  double* Cout = nullptr; int64_t ldcout = 0; int64_t strideCout = 0;
+  double beta = 0.0;
+  double alpha[kGemmMaxBatch] = {};
+  int batch = 1;
+  int reduce = 0;
+  int b_lower = 0;
+  int c_upper = 0;
+};
+cudaError_t gemm_f64(const GemmArgs& g, cudaStream_t st);
+
+// --------------------------------------------------------------- elementwise
+cudaError_t scale_copy(const double* A, int64_t lda, double* X, int64_t ldx, int64_t m, int64_t n,
+                       double s, cudaStream_t st);
+cudaError_t copy_matrix(const double* A, int64_t lda, double* B, int64_t ldb, int64_t m, int64_t n,
+                        cudaStream_t st);
+// W_j = [X; sqrt(c_j) I] for j < r, W_j at W + j*strideW with ld = m + n
+cudaError_t init_stacked(const double* X, int64_t ldx, double* W, int64_t strideW, int64_t m,
+                         int64_t n, const double* sqrt_c, int r, cudaStream_t st);
+// Q_j = [I_n; 0] ((m+n) x n, ld m+n) for j < r
+cudaError_t init_q_identity(double* Q, int64_t strideQ, int64_t m, int64_t n, int r,
+                            cudaStream_t st);
+// Z_j = G + shift_j I for j < r (full copy of G, n x n, ld n)
+cudaError_t init_shifted(const double* G, double* Z, int64_t strideZ, int64_t n, const double* shift,
+                         int r, cudaStream_t st);
+// Xn = mhat * (X + sum_j coef_j * T_j) (T_j at T + j*strideT, ld ldt; nt may be 0),
+// partial sums of ||Xn - X||^2 and ||Xn||^2 to norms[0..1] (after norms_finish).
+cudaError_t combine(const double* X, int64_t ldx, double* Xn, int64_t ldxn, int64_t m, int64_t n,
+                    double mhat, const double* T, int64_t ldt, int64_t strideT, const double* coef,
+                    int nt, double* partials, double* norms, int* status, cudaStream_t st);
+// H = (M + M^T) / 2
+cudaError_t symmetrize(const double* M, int64_t ldm, double* H, int64_t ldh, int64_t n,
+                       cudaStream_t st);
+cudaError_t check_finite(const double* A, int64_t lda, int64_t m, int64_t n, int* status,
+                         cudaStream_t st);
+// ||A||_F^2 into out[0] (via partials)
+cudaError_t frob_norm2(const double* A, int64_t lda, int64_t m, int64_t n, double* partials,
+                       double* out, cudaStream_t st);
+
+// ------------------------------------------------------------ structured QR
+constexpr int kQrNB = 32;
+struct QrBuffers {
+  double* W;   int64_t strideW;   // stacked (m+n) x n per shift, ld m+n
+  double* V;   int64_t strideV;   // explicit reflectors (m+nb) x n per shift, ld m+nb
+  double* T;   int64_t strideT;   // nb x nb triangular factor per panel
+  double* W1;  int64_t strideW1;  // nb x n scratch
+  double* W2;  int64_t strideW2;  // nb x n scratch
+};
+// Factor [X; sqrt(c_j) I] for j < r and overwrite W_j with the thin Q_j.
+cudaError_t structured_qr_q(const QrBuffers& b, int64_t m, int64_t n, int r, int* status,
+                            cudaStream_t st);
+
+// ----------------------------------------------------------------- Cholesky
+constexpr int kCholNB = 64;
+struct CholBuffers {
+  double* Z;    int64_t strideZ;     // n x n, ld n: in = Z_j (upper), out = R_j (upper)
+  double* Rinv; int64_t strideRinv;  // inverses of the nb x nb diagonal blocks, nb x nb each
+};
+cudaError_t cholesky_upper_batched(const CholBuffers& b, int64_t n, int r, int* status,
+                                   cudaStream_t st);
+// Y_j = X R_j^{-1} then Y_j <- Y_j R_j^{-T} (in place), j < r.
+cudaError_t trsm_pair_batched(const double* X, int64_t ldx, const CholBuffers& b, double* Y,
+                              int64_t strideY, double* tmp, int64_t strideTmp, int64_t m,
+                              int64_t n, int r, cudaStream_t st);
+
+// ------------------------------------------------------------ eigensolver
+struct EigWork {
+  double* R;        // n x n
+  double* X;        // n x n, one-sided Jacobi iterate
+  double* HV;       // n x n
+  double* Rinv;     // (n/nb+1) * nb * nb
+  double* lam;      // n
+  int* perm;        // n (device)
+  int* status;
+};
+int eig_sym_jacobi(const double* H, int64_t ldh, int64_t n, double* V, int64_t ldv, double* lam_out,
+                   const EigWork& w, int* sweeps, cudaStream_t st);
+cudaError_t column_norms(const double* X, int64_t ldx, int64_t m, int64_t n, double* out,
+                         cudaStream_t st);
+cudaError_t scale_columns(double* X, int64_t ldx, int64_t m, int64_t n, const double* s, int invert,
+                          cudaStream_t st);
+cudaError_t column_dots(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t m,
+                        int64_t n, double* out, cudaStream_t st);
+cudaError_t gather_columns(const double* X, int64_t ldx, double* Y, int64_t ldy, int64_t m,
+                           int64_t n, const int* perm, const double* sign, cudaStream_t st);
+cudaError_t transpose_lower(const double* R, int64_t ldr, double* X, int64_t ldx, int64_t n,
+                            cudaStream_t st);
+cudaError_t jacobi_round(double* X, int64_t ldx, int64_t m, int64_t n_even, int64_t n_real, int round,
+                         int* status, cudaStream_t st);
+
+#endif  // __CUDACC__
+
+}  // namespace zolo

@@ -1,0 +1,85 @@
+"""CPU checks of libzolo: it builds, loads, exports every symbol of include/zolo.h,
+its host-side coefficient module agrees with the oracle and Table 1, and illegal
+arguments are rejected before any device work."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import zolo_oracle as zo
+from tests.conftest import ROOT
+
+HEADER = os.path.join(ROOT, "include", "zolo.h")
+
+
+@pytest.fixture(scope="module")
+def zb():
+    from paper_1806_06204_gb300 import build
+    build.build()
+    from paper_1806_06204_gb300 import binding
+    return binding
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(zolo_[a-z_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(zb):
+    names = declared_functions()
+    assert len(names) >= 10
+    for name in names:
+        assert hasattr(zb.LIB, name), name
+    assert sorted(zb.EXPORTED) == names
+
+
+def test_coefficients_match_oracle(zb):
+    for ell in [1e-16, 1e-12, 1e-8, 1e-4, 1e-2, 0.1, 0.5, 0.9, 0.999, 1.0]:
+        for r in range(1, 9):
+            c, a, mh, gap = zb.coefficients(ell, r)
+            co = zo.zolotarev_coeffs(ell, r)
+            assert np.allclose(c, co.c, rtol=2e-14, atol=0), (ell, r)
+            assert np.allclose(a, co.a, rtol=1e-12, atol=0), (ell, r)
+            assert mh == pytest.approx(co.Mhat, rel=1e-14)
+            assert gap == pytest.approx(zo.one_minus_zhat_at_ell(co), rel=1e-12, abs=1e-300)
+
+
+def test_schedule_reproduces_table1(zb):
+    from tests.test_oracle_coefficients import read_table1
+    kappas, table = read_table1()
+    for r, row in table.items():
+        got = [len(zb.schedule(1.0 / k, r)[0]) - 1 for k in kappas]
+        assert got == row, (r, got, row)
+
+
+def test_schedule_r_choice_and_switch_match_oracle(zb):
+    for kappa in [1.5, 10, 1e2, 1e4, 1e8, 1e12, 1e16]:
+        ells, qr, r = zb.schedule(1.0 / kappa, 0)
+        assert r == zo.choose_r(1.0 / kappa)
+        oe = zo.ell_schedule(1.0 / kappa, r)
+        assert np.allclose(ells, oe, rtol=1e-14, atol=1e-16)
+        assert qr == [zo.uses_qr(zo.zolotarev_coeffs(e, r), e) for e in oe[:-1]]
+
+
+def test_illegal_arguments_rejected_before_device_work(zb):
+    fake = ctypes.c_void_p(1)   # never dereferenced: validation fails first
+    o = zb.opts(beta=1e-3)
+    info = zb.ZoloInfo()
+    P = ctypes.c_void_p(16)
+    call = lambda *a: zb.LIB.zolo_pd(*a, ctypes.byref(info), None)
+    assert zb.LIB.zolo_pd(None, P, 4, 4, 4, P, 4, P, 4, ctypes.byref(o), ctypes.byref(info), None) == -1
+    assert call(fake, None, 4, 4, 4, P, 4, P, 4, ctypes.byref(o)) == -2
+    assert call(fake, P, 3, 4, 4, P, 4, P, 4, ctypes.byref(o)) == -3
+    assert call(fake, P, 4, 0, 4, P, 4, P, 4, ctypes.byref(o)) == -4
+    assert call(fake, P, 4, 4, 3, P, 4, P, 4, ctypes.byref(o)) == -5
+    assert call(fake, P, 4, 4, 4, P, 3, P, 4, ctypes.byref(o)) == -7
+    assert call(fake, P, 4, 4, 4, P, 4, P, 3, ctypes.byref(o)) == -9
+    for bad in [dict(beta=0.0), dict(beta=1e-3, r=9), dict(beta=2.0, alpha=1.0),
+                dict(beta=1e-3, max_iter=0), dict(beta=float("nan"))]:
+        ob = zb.opts(**bad)
+        assert call(fake, P, 4, 4, 4, P, 4, P, 4, ctypes.byref(ob)) == -10, bad
+    assert zb.LIB.zolo_coefficients(0.0, 3, None, None, None, None) == -1
+    assert zb.LIB.zolo_coefficients(0.5, 9, None, None, None, None) == -2
