@@ -38,10 +38,15 @@ enum {
   ZOLO_ENOTCONV = 3,   /* a-posteriori test still failing after max_iter        */
   ZOLO_ECUDA = 4,      /* a CUDA runtime call failed                            */
   ZOLO_ENOMEM = 5,     /* workspace too small / device allocation failed        */
-  ZOLO_EEIG = 6        /* the Jacobi eigensolver did not converge               */
+  ZOLO_EEIG = 6,       /* the Jacobi eigensolver did not converge               */
+  ZOLO_ETIMEOUT = 7    /* a bounded wait inside a tensor-core kernel expired    */
 };
 
-/* Arithmetic of the contractions.  ZOLO_FP64: plain FP64 (DFMA) everywhere. */
+/* Arithmetic of the contractions.  ZOLO_FP64: plain FP64 on the FP64 FMA pipe.
+   ZOLO_SPLIT_BF16: the iterations' products on the BF16 tensor cores, each FP64
+   operand cut into 8 power-of-two-scaled 6-bit slices (Ozaki scheme, product
+   error ~2^-48 of max|row| max|column|), 9 slices for the Newton-Schulz step;
+   panel factorisations, diagonal blocks and coefficients stay FP64. */
 enum { ZOLO_FP64 = 0, ZOLO_SPLIT_BF16 = 1 };
 
 typedef struct {
@@ -124,6 +129,16 @@ int zolo_pd_host(zolo_handle_t handle, const double* A, int64_t m, int64_t n, in
 int zolo_svd_host(zolo_handle_t handle, const double* A, int64_t m, int64_t n, int64_t lda,
                   double* U, int64_t ldu, double* S, double* V, int64_t ldv,
                   const zolo_opts_t* opts, zolo_info_t* info, void* stream);
+
+/* C = alpha op(A) op(B) + beta C for device FP64 matrices (column-major,
+   op = identity or transpose: trans = 0 / 1), the contraction the iterations
+   run on.  prec = ZOLO_FP64 (DFMA) or ZOLO_SPLIT_BF16 with `slices` = 8 or 9
+   (0 = 8) six-bit slices per operand on the tensor cores.  Not in the paper as
+   an interface; it exposes the building block for testing and reuse.
+   Synchronises the stream before returning. */
+int zolo_dgemm(zolo_handle_t handle, int transA, int transB, int64_t m, int64_t n, int64_t k,
+               double alpha, const double* A, int64_t lda, const double* B, int64_t ldb,
+               double beta, double* C, int64_t ldc, int prec, int slices, void* stream);
 
 /* Short text for a return code. */
 const char* zolo_strerror(int code);

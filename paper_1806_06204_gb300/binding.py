@@ -21,7 +21,7 @@ ZOLO_FP64 = 0
 ZOLO_SPLIT_BF16 = 1
 
 ERRORS = {1: "ZOLO_ENONFINITE", 2: "ZOLO_ECHOL", 3: "ZOLO_ENOTCONV", 4: "ZOLO_ECUDA",
-          5: "ZOLO_ENOMEM", 6: "ZOLO_EEIG"}
+          5: "ZOLO_ENOMEM", 6: "ZOLO_EEIG", 7: "ZOLO_ETIMEOUT"}
 
 
 class ZoloOpts(ctypes.Structure):
@@ -72,6 +72,8 @@ def _load():
         f.restype = I
     lib.zolo_strerror.argtypes = [I]
     lib.zolo_strerror.restype = ctypes.c_char_p
+    lib.zolo_dgemm.argtypes = [P, I, I, I64, I64, I64, D, P, I64, P, I64, D, P, I64, I, I, P]
+    lib.zolo_dgemm.restype = I
     lib.zolo_kernel_launches.argtypes = []
     lib.zolo_kernel_launches.restype = ctypes.c_uint64
     lib.zolo_profile.argtypes = [I]
@@ -85,7 +87,8 @@ LIB = _load()
 
 EXPORTED = ["zolo_opts_default", "zolo_create", "zolo_destroy", "zolo_coefficients",
             "zolo_schedule", "zolo_pd", "zolo_svd", "zolo_pd_host", "zolo_svd_host",
-            "zolo_strerror", "zolo_kernel_launches", "zolo_profile", "zolo_profile_read"]
+            "zolo_strerror", "zolo_kernel_launches", "zolo_profile", "zolo_profile_read",
+            "zolo_dgemm"]
 
 
 def kernel_launches() -> int:
@@ -188,9 +191,15 @@ def _colmajor(t, name):
     import torch
     if t.dtype != torch.float64 or t.dim() != 2:
         raise TypeError(f"{name} must be a 2-D float64 tensor")
-    if t.stride(0) != 1 or t.stride(1) < max(1, t.shape[0]):
+    # strides of size-1 dimensions carry no information (torch may normalise them)
+    if (t.shape[0] > 1 and t.stride(0) != 1) or _ld(t) < max(1, t.shape[0]):
         raise ValueError(f"{name} must be column-major (stride(0) == 1)")
     return t
+
+
+def _ld(t) -> int:
+    """Leading dimension of a column-major matrix view."""
+    return t.stride(1) if t.shape[1] > 1 else max(1, t.shape[0])
 
 
 def empty_colmajor(m: int, n: int, device="cuda"):
@@ -212,9 +221,9 @@ def zolo_pd(handle: Handle, A, o: ZoloOpts, Qp=None, H=None, stream=None, check=
     Qp = empty_colmajor(m, n, A.device) if Qp is None else _colmajor(Qp, "Qp")
     H = empty_colmajor(n, n, A.device) if H is None else _colmajor(H, "H")
     info = ZoloInfo()
-    e = LIB.zolo_pd(handle.ptr, ctypes.c_void_p(A.data_ptr()), m, n, A.stride(1),
-                    ctypes.c_void_p(Qp.data_ptr()), Qp.stride(1), ctypes.c_void_p(H.data_ptr()),
-                    H.stride(1), ctypes.byref(o), ctypes.byref(info), _stream(stream))
+    e = LIB.zolo_pd(handle.ptr, ctypes.c_void_p(A.data_ptr()), m, n, _ld(A),
+                    ctypes.c_void_p(Qp.data_ptr()), _ld(Qp), ctypes.c_void_p(H.data_ptr()),
+                    _ld(H), ctypes.byref(o), ctypes.byref(info), _stream(stream))
     if e and check:
         raise ZoloError(e, "zolo_pd")
     return Qp, H, Info.from_c(info)
@@ -229,9 +238,9 @@ def zolo_svd(handle: Handle, A, o: ZoloOpts, stream=None, check=True):
     V = empty_colmajor(n, n, A.device)
     S = torch.empty(n, dtype=torch.float64, device=A.device)
     info = ZoloInfo()
-    e = LIB.zolo_svd(handle.ptr, ctypes.c_void_p(A.data_ptr()), m, n, A.stride(1),
-                     ctypes.c_void_p(U.data_ptr()), U.stride(1), ctypes.c_void_p(S.data_ptr()),
-                     ctypes.c_void_p(V.data_ptr()), V.stride(1), ctypes.byref(o),
+    e = LIB.zolo_svd(handle.ptr, ctypes.c_void_p(A.data_ptr()), m, n, _ld(A),
+                     ctypes.c_void_p(U.data_ptr()), _ld(U), ctypes.c_void_p(S.data_ptr()),
+                     ctypes.c_void_p(V.data_ptr()), _ld(V), ctypes.byref(o),
                      ctypes.byref(info), _stream(stream))
     if e and check:
         raise ZoloError(e, "zolo_svd")
@@ -266,3 +275,24 @@ def zolo_svd_host(handle: Handle, A, o: ZoloOpts, U, S, V, stream=None, check=Tr
     if e and check:
         raise ZoloError(e, "zolo_svd_host")
     return Info.from_c(info)
+
+
+def zolo_dgemm(handle: Handle, A, B, C=None, alpha=1.0, beta=0.0, transA=False, transB=False,
+               prec: int = ZOLO_FP64, slices: int = 0, stream=None, check=True):
+    """C = alpha op(A) op(B) + beta C on the device (column-major float64 tensors)."""
+    _colmajor(A, "A")
+    _colmajor(B, "B")
+    m = A.shape[1] if transA else A.shape[0]
+    k = A.shape[0] if transA else A.shape[1]
+    n = B.shape[0] if transB else B.shape[1]
+    if C is None:
+        C = empty_colmajor(m, n, A.device)
+        if beta != 0.0:
+            raise ValueError("beta != 0 needs C")
+    _colmajor(C, "C")
+    e = LIB.zolo_dgemm(handle.ptr, int(transA), int(transB), m, n, k, alpha,
+                       ctypes.c_void_p(A.data_ptr()), _ld(A), ctypes.c_void_p(B.data_ptr()), _ld(B),
+                       beta, ctypes.c_void_p(C.data_ptr()), _ld(C), prec, slices, _stream(stream))
+    if e and check:
+        raise ZoloError(e, "zolo_dgemm")
+    return C

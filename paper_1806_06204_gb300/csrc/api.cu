@@ -12,6 +12,8 @@
 // DGSUM2D, Algorithm 3 step 4(d)) fused into X_{k+1} = M_hat (X_k + sum T_j)
 // together with ||X_{k+1} - X_k||_F and ||X_{k+1}||_F.  H = (Qp^T A + A^T Qp)/2
 // uses the original A (Algorithm 1 step 5).
+#include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -28,6 +30,11 @@ struct zolo_handle_s {
   size_t ws_bytes = 0;
   void* io = nullptr;
   size_t io_bytes = 0;
+  void* slices = nullptr;     // split-precision slice planes (BF16)
+  size_t slice_elems = 0;
+  int* exps = nullptr;        // slice exponents
+  size_t exp_elems = 0;
+  int* err = nullptr;         // device error flag of the tensor-core kernels
   cudaEvent_t e0 = nullptr, e1 = nullptr;
 };
 
@@ -140,6 +147,69 @@ int ensure_ws(zolo_handle_t h, size_t bytes) {
   return 0;
 }
 
+// Slice-plane elements for the largest contraction of a decomposition of an
+// m x n matrix (one batch entry, S = 9, the widest slicing used).
+size_t split_elems_per_entry(int64_t m, int64_t n) {
+  const int64_t shapes[][3] = {{kQrNB, n, m + kQrNB}, {m + kQrNB, n, kQrNB}, {m, n, n},
+                               {n, n, m}, {m, kCholNB, n}, {m, n, n}};
+  size_t mx = 0;
+  for (auto& sh : shapes) mx = std::max(mx, split_slice_elems(sh[0], sh[1], sh[2], 1, 9));
+  return mx;
+}
+
+// Grow the handle's slice workspace to hold `want` elements (at least `need`).
+int ensure_split(zolo_handle_t h, size_t need, size_t want, size_t exps) {
+  if (!h->err && cudaMalloc(&h->err, sizeof(int)) != cudaSuccess) return ZOLO_ENOMEM;
+  if (h->slice_elems < need) {
+    if (h->slices) cudaFree(h->slices);
+    h->slices = nullptr;
+    h->slice_elems = 0;
+    size_t n = std::max(want, need);
+    while (cudaMalloc(&h->slices, n * 2) != cudaSuccess) {
+      cudaGetLastError();
+      h->slices = nullptr;
+      if (n == need) return ZOLO_ENOMEM;
+      n = std::max(need, n / 2);
+    }
+    h->slice_elems = n;
+  }
+  if (h->exp_elems < exps) {
+    if (h->exps) cudaFree(h->exps);
+    if (cudaMalloc(&h->exps, exps * sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      h->exps = nullptr;
+      h->exp_elems = 0;
+      return ZOLO_ENOMEM;
+    }
+    h->exp_elems = exps;
+  }
+  return 0;
+}
+
+// Installs the split tensor-core engine for the contractions of one call.
+struct SplitScope {
+  SplitWork w{};
+  bool on = false;
+  ~SplitScope() { set_split_engine(nullptr); }
+  int begin(zolo_handle_t h, int64_t m, int64_t n, int r, cudaStream_t st) {
+    const size_t per = split_elems_per_entry(m, n);
+    const size_t budget = (size_t)8 << 30;   // 16 GB of BF16 planes at most
+    size_t want = std::max(per, std::min(per * (size_t)r, budget));
+    const size_t exps = (size_t)2 * kGemmMaxBatch * (size_t)(std::max(m, n) + m + n + 512);
+    if (int e = ensure_split(h, per, want, exps)) return e;
+    if (cudaMemsetAsync(h->err, 0, sizeof(int), st) != cudaSuccess) return ZOLO_ECUDA;
+    w.slices = h->slices;
+    w.slice_elems = h->slice_elems;
+    w.exps = h->exps;
+    w.exp_elems = h->exp_elems;
+    w.err = h->err;
+    w.slices_s = 8;
+    set_split_engine(&w);
+    on = true;
+    return 0;
+  }
+};
+
 #define CK(x)                                  \
   do {                                         \
     if ((x) != cudaSuccess) return ZOLO_ECUDA; \
@@ -170,7 +240,7 @@ int iterate(const Run& R, const Coefficients& co, bool qr, const double* X, doub
     g.Cout = b.S; g.ldcout = m;
     g.batch = r; g.reduce = 1; g.b_lower = 1;
     for (int j = 0; j < r; ++j) g.alpha[j] = co.a[j] / sq[j];
-    CK(gemm_f64(g, R.st));
+    CK(gemm_any(g, R.st));
     const double one = 1.0;
     CK(combine(X, m, Xn, m, m, n, co.mhat, b.S, m, 0, &one, 1, b.partials, norms_k, b.status,
                R.st));
@@ -180,7 +250,7 @@ int iterate(const Run& R, const Coefficients& co, bool qr, const double* X, doub
     g.A = X; g.lda = m; g.B = X; g.ldb = m;
     g.Cout = b.M; g.ldcout = n; g.c_upper = 1;
     g.alpha[0] = 1.0;
-    CK(gemm_f64(g, R.st));
+    CK(gemm_any(g, R.st));
     double shifts[kMaxR];
     for (int j = 0; j < r; ++j) shifts[j] = co.c[2 * j];
     CK(init_shifted(b.M, b.ch.Z, b.ch.strideZ, n, shifts, r, R.st));
@@ -212,7 +282,7 @@ int validate(zolo_handle_t h, const void* A, int64_t m, int64_t n, int64_t lda, 
   if (o) {
     if (o->r < 0 || o->r > kMaxR || !std::isfinite(o->alpha) || !std::isfinite(o->beta) ||
         !(o->beta > 0.0) || o->max_iter < 1 || o->max_iter > kMaxIters || o->ns_steps < 0 ||
-        o->ns_steps > 4 || o->prec != ZOLO_FP64 ||
+        o->ns_steps > 4 || (o->prec != ZOLO_FP64 && o->prec != ZOLO_SPLIT_BF16) ||
         o->force_qr < -1 || o->force_qr > 1 || (o->alpha > 0.0 && o->beta > o->alpha))
       return -10;
   } else {
@@ -251,6 +321,9 @@ int pd_core(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda,
   layout(h->ws, m, n, r, svd, &R.b);
   if (out_bufs) *out_bufs = R.b;
   const PdBufs& b = R.b;
+  SplitScope split;
+  if (o.prec == ZOLO_SPLIT_BF16)
+    if (int e = split.begin(h, m, n, r, st)) return e;
   CK(cudaMemsetAsync(b.status, 0, sizeof(int) * kStatSlots, st));
   CK(cudaMemsetAsync(b.norms, 0, sizeof(double) * 2 * (kMaxIters + 2), st));
 
@@ -318,19 +391,20 @@ int pd_core(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda,
       ++it;
     }
   }
-  // Newton-Schulz refinement steps
+  // Newton-Schulz refinement steps (nine slices on the split path: FP64-level products)
+  split.w.slices_s = 9;
   for (int s = 0; s < o.ns_steps; ++s) {
     GemmArgs g;
     g.M = g.N = (int)n; g.K = (int)m; g.transA = 1;
     g.A = X; g.lda = m; g.B = X; g.ldb = m; g.Cout = b.M; g.ldcout = n;
     g.alpha[0] = 1.0;
-    CK(gemm_f64(g, st));
+    CK(gemm_any(g, st));
     GemmArgs u;
     u.M = (int)m; u.N = (int)n; u.K = (int)n;
     u.A = X; u.lda = m; u.B = b.M; u.ldb = n;
     u.Cin = X; u.ldcin = m; u.beta = 1.5; u.Cout = Xn; u.ldcout = m;
     u.alpha[0] = -0.5;
-    CK(gemm_f64(u, st));
+    CK(gemm_any(u, st));
     std::swap(X, Xn);
   }
   // H = (Qp^T A + A^T Qp) / 2 with the original A
@@ -339,7 +413,7 @@ int pd_core(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda,
     g.M = g.N = (int)n; g.K = (int)m; g.transA = 1;
     g.A = X; g.lda = m; g.B = A; g.ldb = lda; g.Cout = b.M; g.ldcout = n;
     g.alpha[0] = 1.0;
-    CK(gemm_f64(g, st));
+    CK(gemm_any(g, st));
     CK(symmetrize(b.M, n, H, ldh, n, st));
     CK(copy_matrix(X, m, Qp, ldq, m, n, st));
   }
@@ -349,6 +423,11 @@ int pd_core(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda,
   if (int e = read_status(R, hstat)) return e;
   info->iters = it;
   for (int k = 0; k < it; ++k) info->delta[k] = hn[2 * k + 1] > 0 ? std::sqrt(hn[2 * k] / hn[2 * k + 1]) : 0.0;
+  if (split.on) {
+    int herr = 0;
+    CK(cudaMemcpy(&herr, h->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (herr) return ZOLO_ETIMEOUT;
+  }
   if (hstat[kStatNonFinite]) return ZOLO_ENONFINITE;
   if (hstat[kStatCholFail]) return ZOLO_ECHOL;
   return status;
@@ -390,6 +469,9 @@ int zolo_destroy(zolo_handle_t h) {
   cudaSetDevice(h->device);
   if (h->ws) cudaFree(h->ws);
   if (h->io) cudaFree(h->io);
+  if (h->slices) cudaFree(h->slices);
+  if (h->exps) cudaFree(h->exps);
+  if (h->err) cudaFree(h->err);
   if (h->e0) cudaEventDestroy(h->e0);
   if (h->e1) cudaEventDestroy(h->e1);
   delete h;
@@ -479,7 +561,7 @@ int zolo_svd(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda
       g.M = (int)m; g.N = (int)n; g.K = (int)n;
       g.A = Qp; g.lda = m; g.B = V; g.ldb = ldv; g.Cout = U; g.ldcout = ldu;
       g.alpha[0] = 1.0;
-      if (gemm_f64(g, st) != cudaSuccess) e = ZOLO_ECUDA;
+      if (gemm_any(g, st) != cudaSuccess) e = ZOLO_ECUDA;
       if (e == 0 && cudaMemcpyAsync(b.eig.lam, sg.data(), sizeof(double) * n,
                                     cudaMemcpyHostToDevice, st) != cudaSuccess)
         e = ZOLO_ECUDA;
@@ -568,6 +650,51 @@ int zolo_svd_host(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_
   return e;
 }
 
+int zolo_dgemm(zolo_handle_t h, int transA, int transB, int64_t m, int64_t n, int64_t k,
+               double alpha, const double* A, int64_t lda, const double* B, int64_t ldb,
+               double beta, double* C, int64_t ldc, int prec, int slices, void* stream) {
+  if (!h) return -1;
+  if (transA != 0 && transA != 1) return -2;
+  if (transB != 0 && transB != 1) return -3;
+  if (m < 0 || m > INT32_MAX) return -4;
+  if (n < 0 || n > INT32_MAX) return -5;
+  if (k < 0 || k > INT32_MAX) return -6;
+  if (!std::isfinite(alpha)) return -7;
+  if (k > 0 && m > 0 && !A) return -8;
+  if (lda < std::max<int64_t>(1, transA ? k : m)) return -9;
+  if (k > 0 && n > 0 && !B) return -10;
+  if (ldb < std::max<int64_t>(1, transB ? n : k)) return -11;
+  if (!std::isfinite(beta)) return -12;
+  if (m > 0 && n > 0 && !C) return -13;
+  if (ldc < std::max<int64_t>(1, m)) return -14;
+  if (prec != ZOLO_FP64 && prec != ZOLO_SPLIT_BF16) return -15;
+  if (slices != 0 && slices != 8 && slices != 9) return -16;
+  if (cudaSetDevice(h->device) != cudaSuccess) return ZOLO_ECUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  GemmArgs g;
+  g.M = (int)m; g.N = (int)n; g.K = (int)k; g.transA = transA; g.transB = transB;
+  g.A = A; g.lda = lda; g.B = B; g.ldb = ldb;
+  g.Cin = beta != 0.0 ? C : nullptr; g.ldcin = ldc; g.beta = beta;
+  g.Cout = C; g.ldcout = ldc;
+  g.alpha[0] = alpha;
+  if (prec == ZOLO_FP64) {
+    if (gemm_f64(g, st) != cudaSuccess) return ZOLO_ECUDA;
+    return cudaStreamSynchronize(st) == cudaSuccess ? 0 : ZOLO_ECUDA;
+  }
+  const int S = slices ? slices : 8;
+  const size_t per = split_slice_elems(m, n, k, 1, S);
+  const size_t exps = (size_t)2 * (size_t)(std::max(m, n) + m + n + 512);
+  if (int e = ensure_split(h, per, per, exps)) return e;
+  if (cudaMemsetAsync(h->err, 0, sizeof(int), st) != cudaSuccess) return ZOLO_ECUDA;
+  SplitWork w{h->slices, h->slice_elems, h->exps, h->exp_elems, h->err, S};
+  if (gemm_split(g, w, st) != cudaSuccess) return ZOLO_ECUDA;
+  int herr = 0;
+  if (cudaMemcpyAsync(&herr, h->err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return ZOLO_ECUDA;
+  return herr ? ZOLO_ETIMEOUT : 0;
+}
+
 const char* zolo_strerror(int code) {
   switch (code) {
     case ZOLO_OK: return "success";
@@ -577,6 +704,7 @@ const char* zolo_strerror(int code) {
     case ZOLO_ECUDA: return "CUDA runtime error";
     case ZOLO_ENOMEM: return "device memory allocation failed";
     case ZOLO_EEIG: return "Jacobi eigensolver did not converge";
+    case ZOLO_ETIMEOUT: return "a bounded device wait expired (tensor-core pipeline)";
     default: return code < 0 ? "illegal argument" : "unknown error";
   }
 }

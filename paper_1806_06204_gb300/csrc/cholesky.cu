@@ -101,7 +101,7 @@ cudaError_t cholesky_upper_batched(const CholBuffers& b, int64_t n, int r, int* 
     g.Cout = panel; g.ldcout = n; g.strideCout = b.strideZ;
     g.batch = r;
     for (int j = 0; j < r; ++j) g.alpha[j] = 1.0;
-    if ((err = gemm_f64(g, st)) != cudaSuccess) return err;
+    if ((err = gemm_any(g, st)) != cudaSuccess) return err;
     GemmArgs u;   // trailing SYRK, upper tiles only
     double* trail = b.Z + (k0 + nbk) + (k0 + nbk) * n;
     u.M = u.N = (int)rest; u.K = nbk; u.transA = 1; u.transB = 0;
@@ -111,7 +111,7 @@ cudaError_t cholesky_upper_batched(const CholBuffers& b, int64_t n, int r, int* 
     u.Cout = trail; u.ldcout = n; u.strideCout = b.strideZ;
     u.batch = r; u.c_upper = 1;
     for (int j = 0; j < r; ++j) u.alpha[j] = -1.0;
-    if ((err = gemm_f64(u, st)) != cudaSuccess) return err;
+    if ((err = gemm_any(u, st)) != cudaSuccess) return err;
   }
   return cudaSuccess;
 }
@@ -134,7 +134,7 @@ cudaError_t trsm_pair_batched(const double* X, int64_t ldx, const CholBuffers& b
     g.Cout = tmp; g.ldcout = m; g.strideCout = strideTmp;
     g.batch = r;
     for (int j = 0; j < r; ++j) g.alpha[j] = -1.0;
-    if ((err = gemm_f64(g, st)) != cudaSuccess) return err;
+    if ((err = gemm_any(g, st)) != cudaSuccess) return err;
     GemmArgs h;   // Y_j = tmp Rinv_jj
     h.M = (int)m; h.N = nbj; h.K = nbj; h.transA = 0; h.transB = 0;
     h.A = tmp; h.lda = m; h.strideA = strideTmp;
@@ -142,7 +142,7 @@ cudaError_t trsm_pair_batched(const double* X, int64_t ldx, const CholBuffers& b
     h.Cout = Y + j0 * m; h.ldcout = m; h.strideCout = strideY;
     h.batch = r;
     for (int j = 0; j < r; ++j) h.alpha[j] = 1.0;
-    if ((err = gemm_f64(h, st)) != cudaSuccess) return err;
+    if ((err = gemm_any(h, st)) != cudaSuccess) return err;
   }
   // backward: W R^T = Y, last block column first, W overwriting Y
   for (int jb = nblk - 1; jb >= 0; --jb) {
@@ -157,7 +157,7 @@ cudaError_t trsm_pair_batched(const double* X, int64_t ldx, const CholBuffers& b
     g.Cout = tmp; g.ldcout = m; g.strideCout = strideTmp;
     g.batch = r;
     for (int j = 0; j < r; ++j) g.alpha[j] = -1.0;
-    if ((err = gemm_f64(g, st)) != cudaSuccess) return err;
+    if ((err = gemm_any(g, st)) != cudaSuccess) return err;
     GemmArgs h;   // W_j = tmp Rinv_jj^T
     h.M = (int)m; h.N = nbj; h.K = nbj; h.transA = 0; h.transB = 1;
     h.A = tmp; h.lda = m; h.strideA = strideTmp;
@@ -165,7 +165,7 @@ cudaError_t trsm_pair_batched(const double* X, int64_t ldx, const CholBuffers& b
     h.Cout = Y + j0 * m; h.ldcout = m; h.strideCout = strideY;
     h.batch = r;
     for (int j = 0; j < r; ++j) h.alpha[j] = 1.0;
-    if ((err = gemm_f64(h, st)) != cudaSuccess) return err;
+    if ((err = gemm_any(h, st)) != cudaSuccess) return err;
   }
   return cudaSuccess;
 }

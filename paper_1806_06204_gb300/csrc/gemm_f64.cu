@@ -107,14 +107,6 @@ __global__ void gemm_beta_only(const GemmArgs g) {
   C[i + j * g.ldcout] = (Cin && g.beta != 0.0) ? g.beta * Cin[i + j * g.ldcin] : 0.0;
 }
 
-// Algorithmic flops of one call: the products the structure leaves non-zero.
-double gemm_flops(const GemmArgs& g) {
-  double per = 2.0 * g.M * (double)g.N * g.K;
-  if (g.c_upper) per = (double)g.K * g.N * (g.N + 1.0);
-  else if (g.b_lower) per = 2.0 * g.M * ((double)g.N * g.K - 0.5 * (double)g.N * (g.N - 1.0));
-  return per * g.batch;
-}
-
 template <int BM, int BN>
 cudaError_t launch(const GemmArgs& g, cudaStream_t st) {
   dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, g.reduce ? 1 : g.batch);
@@ -126,6 +118,14 @@ cudaError_t launch(const GemmArgs& g, cudaStream_t st) {
 }
 
 }  // namespace
+
+// Algorithmic flops of one call: the products the structure leaves non-zero.
+double gemm_flops(const GemmArgs& g) {
+  double per = 2.0 * g.M * (double)g.N * g.K;
+  if (g.c_upper) per = (double)g.K * g.N * (g.N + 1.0);
+  else if (g.b_lower) per = 2.0 * g.M * ((double)g.N * g.K - 0.5 * (double)g.N * (g.N - 1.0));
+  return per * g.batch;
+}
 
 cudaError_t gemm_f64(const GemmArgs& g, cudaStream_t st) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;

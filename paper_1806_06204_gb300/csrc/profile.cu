@@ -17,7 +17,7 @@ namespace zolo {
 namespace {
 
 const char* kClassNames[kProfClasses] = {"gemm_f64", "qr_panel", "chol_diag", "jacobi_round",
-                                         "combine", "other"};
+                                         "combine", "other", "gemm_split", "slice"};
 
 struct Pending {
   int cls;

@@ -175,14 +175,14 @@ cudaError_t structured_qr_q(const QrBuffers& b, int64_t m, int64_t n, int r, int
     g.Cout = b.W1; g.ldcout = NB; g.strideCout = b.strideW1;
     g.batch = r;
     for (int j = 0; j < r; ++j) g.alpha[j] = 1.0;
-    if ((err = gemm_f64(g, st)) != cudaSuccess) return err;
+    if ((err = gemm_any(g, st)) != cudaSuccess) return err;
     // W2 = T^T W1
     GemmArgs h = g;
     h.K = nbp; h.transA = 1;
     h.A = Tp; h.lda = NB; h.strideA = b.strideT;
     h.B = b.W1; h.ldb = NB; h.strideB = b.strideW1;
     h.Cout = b.W2; h.strideCout = b.strideW2;
-    if ((err = gemm_f64(h, st)) != cudaSuccess) return err;
+    if ((err = gemm_any(h, st)) != cudaSuccess) return err;
     // C -= V W2
     GemmArgs u = g;
     u.M = (int)(m + nbp); u.N = (int)ntr; u.K = nbp; u.transA = 0; u.transB = 0;
@@ -191,7 +191,7 @@ cudaError_t structured_qr_q(const QrBuffers& b, int64_t m, int64_t n, int r, int
     u.Cin = C; u.ldcin = ldw; u.strideCin = b.strideW; u.beta = 1.0;
     u.Cout = C; u.ldcout = ldw; u.strideCout = b.strideW;
     for (int j = 0; j < r; ++j) u.alpha[j] = -1.0;
-    if ((err = gemm_f64(u, st)) != cudaSuccess) return err;
+    if ((err = gemm_any(u, st)) != cudaSuccess) return err;
   }
   // ---------------- explicit Q (structured ORGQR), overwriting W
   if ((err = init_q_identity(b.W, b.strideW, m, n, r, st)) != cudaSuccess) return err;
@@ -209,13 +209,13 @@ cudaError_t structured_qr_q(const QrBuffers& b, int64_t m, int64_t n, int r, int
     g.Cout = b.W1; g.ldcout = NB; g.strideCout = b.strideW1;
     g.batch = r;
     for (int j = 0; j < r; ++j) g.alpha[j] = 1.0;
-    if ((err = gemm_f64(g, st)) != cudaSuccess) return err;
+    if ((err = gemm_any(g, st)) != cudaSuccess) return err;
     GemmArgs h = g;   // W2 = T W1
     h.K = nbp; h.transA = 0;
     h.A = Tp; h.lda = NB; h.strideA = b.strideT;
     h.B = b.W1; h.ldb = NB; h.strideB = b.strideW1;
     h.Cout = b.W2; h.strideCout = b.strideW2;
-    if ((err = gemm_f64(h, st)) != cudaSuccess) return err;
+    if ((err = gemm_any(h, st)) != cudaSuccess) return err;
     GemmArgs u = g;   // C -= V W2
     u.M = (int)(m + nbp); u.N = (int)ncol; u.K = nbp; u.transA = 0; u.transB = 0;
     u.A = Vp; u.lda = ldv; u.strideA = b.strideV;
@@ -223,7 +223,7 @@ cudaError_t structured_qr_q(const QrBuffers& b, int64_t m, int64_t n, int r, int
     u.Cin = C; u.ldcin = ldw; u.strideCin = b.strideW; u.beta = 1.0;
     u.Cout = C; u.ldcout = ldw; u.strideCout = b.strideW;
     for (int j = 0; j < r; ++j) u.alpha[j] = -1.0;
-    if ((err = gemm_f64(u, st)) != cudaSuccess) return err;
+    if ((err = gemm_any(u, st)) != cudaSuccess) return err;
   }
   return cudaSuccess;
 }

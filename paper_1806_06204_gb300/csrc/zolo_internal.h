@@ -43,7 +43,7 @@ int build_schedule(double ell0, int r, int max_iter, Schedule* out);
 
 // ------------------------------------------------------------- launch scopes
 enum ProfClass { kProfGemm = 0, kProfPanel, kProfCholDiag, kProfJacobi, kProfCombine, kProfOther,
-                 kProfClasses };
+                 kProfSplitGemm, kProfSlice, kProfClasses };
 // Counts the launch made inside its scope and, while profiling is on, brackets
 // it with CUDA events on `st`.  flops/bytes: the launch's algorithmic work.
 class ProfScope {
@@ -92,6 +92,27 @@ struct GemmArgs {
   int c_upper = 0;
 };
 cudaError_t gemm_f64(const GemmArgs& g, cudaStream_t st);
+// algorithmic flops of one call (structural zeros excluded)
+double gemm_flops(const GemmArgs& g);
+
+// --------------------------------------------------- split-precision GEMM
+// Same contract as gemm_f64 (c_upper / b_lower are computed in full), on the
+// BF16 tensor cores with S = 8 or 9 six-bit slices per operand.
+struct SplitWork {
+  void* slices;          // BF16 slice planes
+  size_t slice_elems;
+  int* exps;             // per-row / per-column power-of-two exponents
+  size_t exp_elems;
+  int* err;              // device error flag (bounded waits)
+  int slices_s;          // S
+};
+cudaError_t gemm_split(const GemmArgs& g, SplitWork& w, cudaStream_t st);
+// slice elements one call of the given shape needs
+size_t split_slice_elems(int64_t M, int64_t N, int64_t K, int batch, int S);
+// The engine every contraction of the current call goes through: FP64 (DFMA)
+// when no split workspace is installed, the split tensor-core path otherwise.
+void set_split_engine(SplitWork* w);
+cudaError_t gemm_any(const GemmArgs& g, cudaStream_t st);
 
 // --------------------------------------------------------------- elementwise
 cudaError_t scale_copy(const double* A, int64_t lda, double* X, int64_t ldx, int64_t m, int64_t n,

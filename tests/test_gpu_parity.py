@@ -49,7 +49,8 @@ def host(t):
 
 def polar_tol(sm, alpha=1.0, c=200.0):
     s = np.sort(sm.sigma)
-    return c * EPS / ((s[0] + s[1]) / alpha)
+    gap = s[0] + s[1] if len(s) > 1 else s[0]
+    return c * EPS / (gap / alpha)
 
 
 def check_pd_invariants(A, Qp, H):
