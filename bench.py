@@ -45,8 +45,9 @@ WORKLOADS = {
     "svd256": dict(kind="svd", m=256, n=256, kappa=1e8, r=3, sample_n=256,
                    desc="Plain FP64 Zolo-SVD of one 256x256 matrix, kappa 1e8, r=3"),
     "pd16384x4096": dict(kind="pd", m=16384, n=4096, kappa=1e6, r=6, sample_n=384, tall=True,
-                         desc="Plain FP64 Zolo-PD of one 16384x4096 matrix, sigma uniform in "
-                              "[1e-6, 1], r=6"),
+                         desc="Zolo-PD of one 16384x4096 matrix, sigma uniform in [1e-6, 1], r=6"),
+    "pd1024": dict(kind="pd", m=1024, n=1024, kappa=1e8, r=6, sample_n=256,
+                   desc="Zolo-PD of one 1024x1024 matrix, kappa 1e8, r=6"),
 }
 
 
@@ -201,6 +202,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="svd4096", choices=sorted(WORKLOADS))
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "split"],
+                    help="split: the iterations' products on the BF16 tensor cores (Ozaki slices)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -234,7 +237,9 @@ def main():
     sm = make_input(w, seed=2000 + rank)
     A = torch.from_numpy(sm.A).cuda()
     h = zb.Handle(local)
-    o = zb.opts(beta=float(np.min(sm.sigma)), alpha=1.0, r=w["r"])
+    split = args.prec == "split"
+    o = zb.opts(beta=float(np.min(sm.sigma)), alpha=1.0, r=w["r"],
+                prec=zb.ZOLO_SPLIT_BF16 if split else zb.ZOLO_FP64, ns_steps=1 if split else 0)
     m, n = w["m"], w["n"]
 
     def step():
@@ -282,8 +287,17 @@ def main():
     dom_name, dom = max(((k, v) for k, v in kstats.items() if v["launches"] > 0),
                         key=lambda kv: kv[1]["ms"])
     achieved = dom["flops"] / (dom["ms"] / 1000.0) / 1e12
-    bound = "alu" if dom_name != "combine" else "hbm"
-    if bound == "alu":
+    bound = {"combine": "hbm", "slice": "hbm", "gemm_split": "tensor"}.get(dom_name, "alu")
+    if bound == "tensor":
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        peak = peaks["bf16_tflops_sustained"]
+        # tensor flops actually issued: one BF16 product per slice pair (S(S+1)/2 of them)
+        issued = dom["flops"] * 36 / (dom["ms"] / 1000.0) / 1e12
+        roof = {"bound": "tensor", "kernel": dom_name, "achieved": issued, "peak": peak,
+                "unit": "TFLOP/s", "frac": issued / peak, "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained",
+                "fp64_equivalent_tflops": dom["flops"] / (dom["ms"] / 1000.0) / 1e12}
+    elif bound == "alu":
         roof = {"bound": "alu", "kernel": dom_name, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
                 "peak_source": "derived: 152 SMs x 4 FP64 flops/clk x 2.07 GHz"}
@@ -337,10 +351,11 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "matrices/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if not split else "bf16x8-slices->f64",
                 "data": "synthetic",
                 "config": {"workload": args.workload, "desc": w["desc"], "m": m, "n": n,
-                           "kappa": w["kappa"], "r": info.r, "prec": "fp64",
+                           "kappa": w["kappa"], "r": info.r, "prec": args.prec,
                            "l2": "inputs larger than L2 (no flush)",
                            "parallelism": "replicas" if world > 1 else "single"},
                 "eff_tflops": world * flops / (ms_step / 1000.0) / 1e12,

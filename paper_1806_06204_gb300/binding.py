@@ -296,3 +296,4 @@ def zolo_dgemm(handle: Handle, A, B, C=None, alpha=1.0, beta=0.0, transA=False, 
     if e and check:
         raise ZoloError(e, "zolo_dgemm")
     return C
+

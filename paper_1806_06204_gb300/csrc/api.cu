@@ -128,6 +128,12 @@ size_t layout(void* base, int64_t m, int64_t n, int r, bool svd, PdBufs* b) {
     t.eig.lam = q.take<double>(std::max<int64_t>(n, 2));
     t.eig.perm = q.take<int>(n);
     t.eig.status = t.status;
+    t.eig.X32 = q.take<float>(n * n);
+    t.eig.Z32 = q.take<float>(n * n);
+    t.eig.Z = q.take<double>(n * n);
+    t.eig.tmp = q.take<double>(n * kCholNB);
+    t.eig.bar = q.take<unsigned>(2);
+    t.eig.err = q.take<int>(1);
     c.off = std::max(c.off, q.off);
   }
   if (b) *b = t;
@@ -203,7 +209,7 @@ struct SplitScope {
     w.exps = h->exps;
     w.exp_elems = h->exp_elems;
     w.err = h->err;
-    w.slices_s = 8;
+    w.slices_s = 9;
     set_split_engine(&w);
     on = true;
     return 0;
@@ -391,8 +397,7 @@ int pd_core(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda,
       ++it;
     }
   }
-  // Newton-Schulz refinement steps (nine slices on the split path: FP64-level products)
-  split.w.slices_s = 9;
+  // Newton-Schulz refinement steps (nine slices on the split path, as the iteration)
   for (int s = 0; s < o.ns_steps; ++s) {
     GemmArgs g;
     g.M = g.N = (int)n; g.K = (int)m; g.transA = 1;
@@ -550,6 +555,7 @@ int zolo_svd(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda
     info->eig_sweeps = sweeps;
     if (ee == 1) e = ZOLO_ECUDA;
     else if (ee == 2) e = ZOLO_EEIG;
+    else if (ee == 3) e = ZOLO_ETIMEOUT;
     if (e == 0) {
       // U = Qp V, with the sign of u_i flipped where lambda_i < 0 (sigma_i = |lambda_i|)
       std::vector<double> sv(n), sg(n);

@@ -116,13 +116,13 @@ cudaError_t cholesky_upper_batched(const CholBuffers& b, int64_t n, int r, int* 
   return cudaSuccess;
 }
 
-cudaError_t trsm_pair_batched(const double* X, int64_t ldx, const CholBuffers& b, double* Y,
-                              int64_t strideY, double* tmp, int64_t strideTmp, int64_t m,
-                              int64_t n, int r, cudaStream_t st) {
+cudaError_t trsm_right_upper_batched(const double* X, int64_t ldx, const CholBuffers& b, double* Y,
+                                     int64_t strideY, double* tmp, int64_t strideTmp, int64_t m,
+                                     int64_t n, int r, cudaStream_t st) {
   constexpr int NB = kCholNB;
   cudaError_t err;
   const int nblk = (int)((n + NB - 1) / NB);
-  // forward: Y R = X, block column by block column
+  // Y R = X, block column by block column
   for (int jb = 0; jb < nblk; ++jb) {
     const int64_t j0 = (int64_t)jb * NB;
     const int nbj = (int)(n - j0 < NB ? n - j0 : NB);
@@ -144,6 +144,18 @@ cudaError_t trsm_pair_batched(const double* X, int64_t ldx, const CholBuffers& b
     for (int j = 0; j < r; ++j) h.alpha[j] = 1.0;
     if ((err = gemm_any(h, st)) != cudaSuccess) return err;
   }
+  return cudaSuccess;
+}
+
+cudaError_t trsm_pair_batched(const double* X, int64_t ldx, const CholBuffers& b, double* Y,
+                              int64_t strideY, double* tmp, int64_t strideTmp, int64_t m,
+                              int64_t n, int r, cudaStream_t st) {
+  constexpr int NB = kCholNB;
+  cudaError_t err;
+  const int nblk = (int)((n + NB - 1) / NB);
+  if ((err = trsm_right_upper_batched(X, ldx, b, Y, strideY, tmp, strideTmp, m, n, r, st)) !=
+      cudaSuccess)
+    return err;
   // backward: W R^T = Y, last block column first, W overwriting Y
   for (int jb = nblk - 1; jb >= 0; --jb) {
     const int64_t j0 = (int64_t)jb * NB;

@@ -7,17 +7,21 @@
 // is then sum over pairs (s, t), s + t <= S + 1, of BF16 x BF16 GEMMs whose
 // FP32 accumulation is exact as long as each sum stays below 2^24 units of its
 // last place: with |d| <= 63 a level (fixed s + t) of p pairs over k terms needs
-// p k 2^12 <= 2^24.  Levels 2..5 (p <= 4) therefore accumulate exactly in their
-// own TMEM accumulator over K-chunks of 1024; the levels >= 6 share one FP32
-// accumulator whose rounding (2^-24 of a term already 2^-36 below the leading
-// level) is below the slicing error.  The epilogue adds the five accumulators in
-// FP64 after every chunk and applies 2^(e_i + f_j), alpha and beta.
+// p k 2^12 <= 2^24.  Levels 2..7 (p <= 6) therefore accumulate exactly in their
+// own TMEM accumulator over K-chunks of 512; the levels >= 8 share one FP32
+// accumulator.  That one is rounded at every MMA (about 500 additions per
+// chunk), but its terms lie 2^-36 below the leading level, so the accumulated
+// rounding stays near 2^-51 of the result.  (Merging from level 6 on instead
+// leaves ~2^-38: a single FP32 accumulator over ~1700 MMAs is not enough.)
+// The epilogue adds the seven accumulators in FP64 after every chunk and
+// applies 2^(e_i + f_j), alpha and beta.
 // Accuracy: |C - AB| <~ K 2^-6S max|A_i.| max|B_.j| (normwise ~2^-48 for S = 8).
 #include <cuda.h>
 #include <cuda_bf16.h>
 
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <algorithm>
 #include <mutex>
 
@@ -30,76 +34,131 @@ namespace {
 constexpr int kBeta = 6;
 constexpr int kTileM = 128;
 constexpr int kBK = 64;            // one 128-byte swizzle row of BF16
-constexpr int kChunkK = 1024;      // exact-accumulation span of the level sums
+constexpr int kChunkK = 512;       // exact-accumulation span of the level sums
+constexpr int kAcc = 7;            // TMEM accumulators: levels 2..7 exact, levels >= 8 merged
 constexpr int kARing = 4;
-constexpr int kThreads = 192;      // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue
+constexpr int kEpiWarps = 16;      // four per TMEM lane quarter, each owning a quarter of the columns
+constexpr int kThreads = 64 + 32 * kEpiWarps;   // warp 0 TMA, warp 1 MMA, the rest epilogue
 
 // ----------------------------------------------------------------- slicing
-// max-exponent of each row of op(X) (rows x K): e with max|x| < 2^e (0 for a zero row)
-__global__ void row_exp_kernel(const double* __restrict__ X, int64_t ldx, int trans, int rows, int K,
-                               int* __restrict__ e_out) {
-  // trans = 0: op(X) = X (column-major, rows contiguous): one thread per row.
-  // trans = 1: op(X) = X^T: row i is column i of X: one warp per row.
-  if (!trans) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= rows) return;
-    double mx = 0.0;
-    for (int k = 0; k < K; ++k) mx = fmax(mx, fabs(X[i + (int64_t)k * ldx]));
-    int e = 0;
-    if (mx > 0.0) frexp(mx, &e);
-    e_out[i] = e;
-  } else {
-    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (w >= rows) return;
-    double mx = 0.0;
-    for (int k = lane; k < K; k += 32) mx = fmax(mx, fabs(X[k + (int64_t)w * ldx]));
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    int e = 0;
-    if (mx > 0.0) frexp(mx, &e);
-    if (lane == 0) e_out[w] = e;
+// One batch entry per blockIdx.z; operand b starts at X + b * strideX.
+// Row i of op(X) (rows x K):  trans = 0: X[i + k ldx] (rows contiguous),
+//                             trans = 1: X[k + i ldx] (row contiguous along k).
+
+// e_i with max_k |op(X)_ik| < 2^e_i (0 for a zero row).  Integer arithmetic on
+// the FP64 bit patterns (|x| orders like its magnitude bits); no FP64 pipe work.
+__device__ __forceinline__ int exp_above(unsigned long long mag) {
+  if (mag == 0) return 0;
+  const int ef = (int)(mag >> 52);
+  return ef ? ef - 1022 : -1022;   // normal: |x| < 2^(ef-1022); subnormal: < 2^-1022
+}
+
+__global__ void row_exp_kernel(const double* __restrict__ X, int64_t ldx, int64_t strideX, int trans,
+                               int rows, int K, int* __restrict__ e_out, int rows_pad) {
+  __shared__ unsigned long long red[8][33];
+  const double* Xb = X + blockIdx.z * strideX;
+  const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+  const unsigned long long kMag = 0x7FFFFFFFFFFFFFFFull;
+  unsigned long long mx = 0;
+  if (!trans) {   // 32 rows per block along tx, k split over ty
+    const int i = blockIdx.x * 32 + tx;
+    if (i < rows)
+      for (int k = ty; k < K; k += 8) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(Xb[i + (int64_t)k * ldx]) & kMag;
+        mx = b > mx ? b : mx;
+      }
+    red[ty][tx] = mx;
+    __syncthreads();
+    if (ty == 0) {
+      for (int y = 1; y < 8; ++y) mx = red[y][tx] > mx ? red[y][tx] : mx;
+      if (i < rows_pad) e_out[blockIdx.z * rows_pad + i] = exp_above(mx);
+    }
+  } else {        // 8 rows per block, one warp per row, lanes along k
+    const int i = blockIdx.x * 8 + ty;
+    if (i < rows)
+      for (int k = tx; k < K; k += 32) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(Xb[k + (int64_t)i * ldx]) & kMag;
+        mx = b > mx ? b : mx;
+      }
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long t = __shfl_xor_sync(0xffffffffu, mx, o);
+      mx = t > mx ? t : mx;
+    }
+    if (tx == 0 && i < rows_pad) e_out[blockIdx.z * rows_pad + i] = exp_above(mx);
   }
 }
 
-// S slices of op(X), each rows_pad x K_pad BF16, K contiguous, at out + s*rows_pad*K_pad.
+// F = floor(|x| 2^(6S - e)) < 2^(6S) from the bit pattern (|x| < 2^e); the S
+// base-64 digits of F, each times 2^-6s and with the sign of x, are the slices.
+template <int S>
+__device__ __forceinline__ unsigned long long fixed_point(double x, int e, bool* neg) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  *neg = (bits >> 63) != 0;
+  const unsigned long long mag = bits & 0x7FFFFFFFFFFFFFFFull;
+  if (mag == 0) return 0;
+  const int ef = (int)(mag >> 52);
+  const unsigned long long M = (mag & ((1ull << 52) - 1)) | (ef ? (1ull << 52) : 0ull);
+  const int E = ef ? ef - 1075 : -1074;          // |x| = M 2^E
+  const int k = E - e + 6 * S;
+  if (k >= 0) return k < 11 ? M << k : 0;        // |x| < 2^e keeps M 2^k below 2^(6S)
+  return -k < 64 ? M >> (-k) : 0;
+}
+
+// S slices of op(X), each rows_pad x K_pad BF16, K contiguous; batch entry b at
+// out + b * S * rows_pad * K_pad, slice s (1-based) at + (s-1) * rows_pad * K_pad.
 // 32 x 32 tiles through shared memory so that both the read (along X's
 // contiguous dimension) and the write (along K) are coalesced.
 template <int S>
-__global__ void slice_kernel(const double* __restrict__ X, int64_t ldx, int trans, int rows, int K,
-                             const int* __restrict__ e_in, __nv_bfloat16* __restrict__ out,
-                             int rows_pad, int K_pad) {
+__global__ void slice_kernel(const double* __restrict__ X, int64_t ldx, int64_t strideX, int trans,
+                             int rows, int K, const int* __restrict__ e_in,
+                             __nv_bfloat16* __restrict__ out, int rows_pad, int K_pad) {
   __shared__ double tile[32][33];
+  const double* Xb = X + blockIdx.z * strideX;
+  const int* eb = e_in + blockIdx.z * rows_pad;
+  const size_t plane = (size_t)rows_pad * K_pad;
+  __nv_bfloat16* ob = out + (size_t)blockIdx.z * S * plane;
   const int i0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
   const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
   for (int r = ty; r < 32; r += 8) {
     double v = 0.0;
-    if (!trans) {   // X[i + k ldx]: tx runs along i
+    if (!trans) {   // tx runs along i
       const int i = i0 + tx, k = k0 + r;
-      if (i < rows && k < K) v = X[i + (int64_t)k * ldx];
-      tile[tx][r] = v;    // tile[i][k]
-    } else {        // X[k + i ldx]: tx runs along k
+      if (i < rows && k < K) v = Xb[i + (int64_t)k * ldx];
+      tile[tx][r] = v;
+    } else {        // tx runs along k
       const int i = i0 + r, k = k0 + tx;
-      if (i < rows && k < K) v = X[k + (int64_t)i * ldx];
+      if (i < rows && k < K) v = Xb[k + (int64_t)i * ldx];
       tile[r][tx] = v;
     }
   }
   __syncthreads();
-  const size_t plane = (size_t)rows_pad * K_pad;
   for (int r = ty; r < 32; r += 8) {
     const int i = i0 + r, k = k0 + tx;
     if (i >= rows_pad || k >= K_pad) continue;
-    double y = (i < rows) ? ldexp(tile[r][tx], -e_in[i]) : 0.0;
-    __nv_bfloat16* o = out + (size_t)i * K_pad + k;
+    bool neg = false;
+    const unsigned long long F = (i < rows) ? fixed_point<S>(tile[r][tx], eb[i], &neg) : 0ull;
+    __nv_bfloat16* o = ob + (size_t)i * K_pad + k;
 #pragma unroll
     for (int s = 1; s <= S; ++s) {
-      const double t = y * 64.0;
-      const double d = trunc(t);
-      y = t - d;
-      o[(s - 1) * plane] = __double2bfloat16(ldexp(d, -kBeta * s));
+      const int d = (int)((F >> (kBeta * (S - s))) & 63ull);
+      // d 2^-6s is exact in FP32 and in BF16 (at most six significant bits)
+      const float v = (float)d * __int_as_float((127 - kBeta * s) << 23);
+      o[(s - 1) * plane] = __float2bfloat16_rn(neg ? -v : v);
     }
   }
 }
 
 // ----------------------------------------------------------------- GEMM
+// (h, l) += x for a float pair h + l: TwoSum(h, x), then renormalise.
+__device__ __forceinline__ void pair_add(float& h, float& l, float x) {
+  const float s1 = h + x;
+  const float bb = s1 - h;
+  const float e = (h - (s1 - bb)) + (x - bb);
+  const float lt = l + e;
+  h = s1 + lt;
+  l = lt - (h - s1);
+}
+
 struct SplitEpi {
   double* C;                // output (column-major), per-batch stride
   int64_t ldc, strideC;
@@ -128,7 +187,7 @@ struct SmemLayout {
 };
 
 template <int BN, int S>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __maxnreg__(112)
 split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                   const SplitEpi p) {
   using L = SmemLayout<BN, S>;
@@ -161,7 +220,7 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     for (int i = 0; i < 2; ++i) { tc::mbar_init(&bfull[i], 1); tc::mbar_init(&bempty[i], 1); }
     for (int i = 0; i < kARing; ++i) { tc::mbar_init(&afull[i], 1); tc::mbar_init(&aempty[i], 1); }
     tc::mbar_init(tfull, 1);
-    tc::mbar_init(tempty, 4);
+    tc::mbar_init(tempty, kEpiWarps);
     tc::mbar_init(tdone, 1);
     tc::fence_barrier_init();
   }
@@ -209,7 +268,7 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     for (int c = 0; c < nchunks && ok; ++c) {
       if (c > 0 && !(ok = tc::mbar_wait(tempty, (c - 1) & 1, err))) break;
       tc::tc_fence_after();
-      uint32_t fresh = 0x1F;   // accumulator a starts (accumulate = 0) at its first MMA
+      uint32_t fresh = (1u << kAcc) - 1;   // accumulator a starts (accumulate = 0) at its first MMA
       const int kc = c % nchunk_k;
       const int kb_end = min(nkb, (kc + 1) * (kChunkK / kBK));
       for (int kb = kc * (kChunkK / kBK); kb < kb_end && ok; ++kb, ++kbg) {
@@ -224,7 +283,7 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
           const uint32_t a0 = tc::smem_u32(sA + sa * L::kATile);
           for (int t = 0; s + t <= S - 1; ++t) {   // level (s+1)+(t+1) <= S+1
             const int lvl = s + t;                 // 0 -> level 2
-            const int acc = lvl < 4 ? lvl : 4;
+            const int acc = lvl < kAcc - 1 ? lvl : kAcc - 1;
             const uint32_t d = tmem + acc * BN;
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {
@@ -242,57 +301,78 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     }
     tc::mma_commit(tdone);   // arrives once every MMA issued above has completed
   } else if (warp >= 2) {
-    // ---------------- epilogue: drain chunks into FP64 registers
+    // ---------------- epilogue: drain chunks into float-pair accumulators
+    // Level 2 is an integer multiple of 2^-12: times 2^12 it is an integer of
+    // magnitude below 512 * 63^2 < 2^21 per chunk, so an int32 sums it exactly
+    // over any K used here.  The lower levels go into a float pair (hr, lr)
+    // whose rounding (2^-48 of values at least 2^-6 below level 2) is
+    // negligible.  FP64 is used only when a batch entry's result is scaled and
+    // written.
+    constexpr int HALF = BN / (kEpiWarps / 4);     // columns of this warp
     const int q = warp & 3;
+    const int half = (warp - 2) >> 2;              // which column slice
     const int row = m0 + q * 32 + lane;            // tile row
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-    double acc[BN];
+    int i2[HALF];
+    float hr[HALF], lr[HALF];
 #pragma unroll
-    for (int j = 0; j < BN; ++j) acc[j] = 0.0;
+    for (int j = 0; j < HALF; ++j) {
+      i2[j] = 0;
+      hr[j] = lr[j] = 0.f;
+    }
     bool ok = true;
+    const int z = p.reduce ? 0 : blockIdx.z;
+    double* C = p.C + (int64_t)z * p.strideC;
+    const double* Cin = p.Cin ? p.Cin + (int64_t)z * p.strideCin : nullptr;
     for (int c = 0; c < nchunks; ++c) {
-      const int b = b_first + c / nchunk_k;
-      const int* ebb = p.eb + b * p.Npad + n0;
       if (!(ok = tc::mbar_wait(tfull, c & 1, err))) break;
       tc::tc_fence_after();
-      const int ei = p.ea[b * p.Mpad + row];
-      const double al = p.alpha[b];
 #pragma unroll
-      for (int g = 0; g < BN / 16; ++g) {
-        double part[16];
+      for (int a = 0; a < kAcc; ++a) {
 #pragma unroll
-        for (int i = 0; i < 16; ++i) part[i] = 0.0;
-#pragma unroll
-        for (int a = 0; a < 5; ++a) {
+        for (int g = 0; g < HALF / 16; ++g) {
           float v[16];
-          tc::tmem_ld16(tmem + lane_off + a * BN + g * 16, v);
+          tc::tmem_ld16(tmem + lane_off + a * BN + half * HALF + g * 16, v);
+          if (a == 0) {
 #pragma unroll
-          for (int i = 0; i < 16; ++i) part[i] += (double)v[i];
+            for (int i = 0; i < 16; ++i) i2[g * 16 + i] += __float2int_rn(v[i] * 4096.0f);
+          } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) pair_add(hr[g * 16 + i], lr[g * 16 + i], v[i]);
+          }
         }
-#pragma unroll
-        for (int i = 0; i < 16; ++i)
-          acc[g * 16 + i] = fma(al, ldexp(part[i], ei + __ldg(ebb + g * 16 + i)), acc[g * 16 + i]);
       }
       tc::tc_fence_before();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(tempty);
-    }
-    if (ok) {
-      const int z = p.reduce ? 0 : blockIdx.z;
-      double* C = p.C + (int64_t)z * p.strideC;
-      const double* Cin = p.Cin ? p.Cin + (int64_t)z * p.strideCin : nullptr;
+      // end of a batch entry: scale, combine with beta C_in (first entry) or with
+      // the running sum already in C (reduce mode), write, reset
+      if ((c + 1) % nchunk_k == 0) {
+        const int b = b_first + c / nchunk_k;
+        const bool first = c / nchunk_k == 0;
+        const int ei = p.ea[b * p.Mpad + row];
+        const int* ebb = p.eb + b * p.Npad + n0 + half * HALF;
+        const double al = p.alpha[b];
 #pragma unroll
-      for (int j = 0; j < BN; ++j) {
-        const int col = n0 + j;
-        // tile (row, col) is C(row, col), or C(col, row) when the tile computes C^T
-        const int ci = p.swap ? col : row, cj = p.swap ? row : col;
-        if (row < (p.swap ? p.N : p.M) && col < (p.swap ? p.M : p.N)) {
-          double v = acc[j];
-          if (Cin && p.beta != 0.0) v = fma(p.beta, Cin[ci + (int64_t)cj * p.ldcin], v);
-          C[ci + (int64_t)cj * p.ldc] = v;
+        for (int j = 0; j < HALF; ++j) {
+          const int col = n0 + half * HALF + j;
+          const int ci = p.swap ? col : row, cj = p.swap ? row : col;
+          if (row < (p.swap ? p.N : p.M) && col < (p.swap ? p.M : p.N)) {
+            const double t = (double)i2[j] * (1.0 / 4096.0) + ((double)hr[j] + (double)lr[j]);
+            double v = al * ldexp(t, ei + __ldg(ebb + j));
+            if (first) {
+              if (Cin && p.beta != 0.0) v = fma(p.beta, Cin[ci + (int64_t)cj * p.ldcin], v);
+            } else {
+              v += C[ci + (int64_t)cj * p.ldc];
+            }
+            C[ci + (int64_t)cj * p.ldc] = v;
+          }
+          i2[j] = 0;
+          hr[j] = lr[j] = 0.f;
         }
       }
     }
+    (void)ok;
   }
   tc::tc_fence_before();
   __syncthreads();
@@ -339,16 +419,22 @@ bool make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t K_pad, int
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 template <int S>
-cudaError_t slice_operand(const double* X, int64_t ldx, int trans, int rows, int K, int* e,
-                          __nv_bfloat16* out, int rows_pad, int K_pad, cudaStream_t st) {
+cudaError_t slice_operand(const double* X, int64_t ldx, int64_t strideX, int trans, int rows, int K,
+                          int batch, int* e, __nv_bfloat16* out, int rows_pad, int K_pad,
+                          cudaStream_t st) {
   {
-    ProfScope ps(kProfSlice, st, 0.0, 8.0 * rows * (double)K);
-    if (!trans) row_exp_kernel<<<(rows + 255) / 256, 256, 0, st>>>(X, ldx, 0, rows, K, e);
-    else row_exp_kernel<<<(rows * 32 + 255) / 256, 256, 0, st>>>(X, ldx, 1, rows, K, e);
+    ProfScope ps(kProfSlice, st, 0.0, 8.0 * batch * rows * (double)K);
+    if (!trans)
+      row_exp_kernel<<<dim3((rows_pad + 31) / 32, 1, batch), dim3(32, 8), 0, st>>>(
+          X, ldx, strideX, 0, rows, K, e, rows_pad);
+    else
+      row_exp_kernel<<<dim3((rows_pad + 7) / 8, 1, batch), dim3(32, 8), 0, st>>>(
+          X, ldx, strideX, 1, rows, K, e, rows_pad);
   }
-  ProfScope ps(kProfSlice, st, 0.0, (8.0 + 2.0 * S) * rows_pad * (double)K_pad);
-  dim3 grid((unsigned)(K_pad / 32), (unsigned)(rows_pad / 32));
-  slice_kernel<S><<<grid, dim3(32, 8), 0, st>>>(X, ldx, trans, rows, K, e, out, rows_pad, K_pad);
+  ProfScope ps(kProfSlice, st, 0.0, (8.0 + 2.0 * S) * batch * rows_pad * (double)K_pad);
+  dim3 grid((unsigned)(K_pad / 32), (unsigned)(rows_pad / 32), batch);
+  slice_kernel<S><<<grid, dim3(32, 8), 0, st>>>(X, ldx, strideX, trans, rows, K, e, out, rows_pad,
+                                                K_pad);
   return cudaGetLastError();
 }
 
@@ -367,23 +453,19 @@ cudaError_t run_split(const GemmArgs& g, SplitWork& w, cudaStream_t st) {
   int* ea = w.exps;
   int* eb = w.exps + (size_t)nb * Mpad;
   cudaError_t err;
-  for (int b = 0; b < nb; ++b) {
-    // op(A) rows: M x K.  With swap the tile's A side is op(B)^T, rows = columns of op(B).
-    const double* Xa = swap ? g.B + b * g.strideB : g.A + b * g.strideA;
-    const double* Xb = swap ? g.A + b * g.strideA : g.B + b * g.strideB;
-    const int64_t lda = swap ? g.ldb : g.lda, ldb = swap ? g.lda : g.ldb;
-    // tile-A operand = op(A) (or op(B)^T): rows along M.  op(A) row i, col k:
-    //   transA = 0: A[i + k lda]  (rows contiguous)   transA = 1: A[k + i lda]
-    // op(B)^T row j, col k = op(B)[k][j]: transB = 0: B[k + j ldb]  -> "trans" layout
-    const int ta = swap ? (g.transB ? 0 : 1) : g.transA;
-    const int tb = swap ? g.transA : (g.transB ? 0 : 1);
-    if ((err = slice_operand<S>(Xa, lda, ta, M, K, ea + (size_t)b * Mpad,
-                                sa + (size_t)b * S * Mpad * Kpad, Mpad, Kpad, st)) != cudaSuccess)
-      return err;
-    if ((err = slice_operand<S>(Xb, ldb, tb, N, K, eb + (size_t)b * Npad,
-                                sb + (size_t)b * S * Npad * Kpad, Npad, Kpad, st)) != cudaSuccess)
-      return err;
-  }
+  // op(A) rows: M x K.  With swap the tile's A side is op(B)^T (rows = columns of op(B)).
+  //   op(A) row i, col k:   transA = 0: A[i + k lda]   transA = 1: A[k + i lda]
+  //   op(B)^T row j, col k: transB = 0: B[k + j ldb]   transB = 1: B[j + k ldb]
+  const double* Xa = swap ? g.B : g.A;
+  const double* Xb = swap ? g.A : g.B;
+  const int64_t lda = swap ? g.ldb : g.lda, ldb = swap ? g.lda : g.ldb;
+  const int64_t sta = swap ? g.strideB : g.strideA, stb = swap ? g.strideA : g.strideB;
+  const int ta = swap ? (g.transB ? 0 : 1) : g.transA;
+  const int tb = swap ? g.transA : (g.transB ? 0 : 1);
+  if ((err = slice_operand<S>(Xa, lda, sta, ta, M, K, nb, ea, sa, Mpad, Kpad, st)) != cudaSuccess)
+    return err;
+  if ((err = slice_operand<S>(Xb, ldb, stb, tb, N, K, nb, eb, sb, Npad, Kpad, st)) != cudaSuccess)
+    return err;
   CUtensorMap mA, mB;
   if (!make_map(&mA, sa, (int64_t)nb * S * Mpad, Kpad, kTileM) ||
       !make_map(&mB, sb, (int64_t)nb * S * Npad, Kpad, BN))
@@ -401,14 +483,29 @@ cudaError_t run_split(const GemmArgs& g, SplitWork& w, cudaStream_t st) {
   if (!attr_set) {
     if ((err = cudaFuncSetAttribute(split_gemm_kernel<BN, S>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, L::kAlloc)) !=
-        cudaSuccess)
+        cudaSuccess) {
+      if (std::getenv("ZOLO_DEBUG"))
+        std::fprintf(stderr, "zolo: cudaFuncSetAttribute(%d B): %s\n", L::kAlloc,
+                     cudaGetErrorString(err));
       return err;
+    }
     attr_set = true;
   }
   dim3 grid((unsigned)(Npad / BN), (unsigned)(Mpad / kTileM), g.reduce ? 1 : nb);
   ProfScope ps(kProfSplitGemm, st, gemm_flops(g), 0.0);
   split_gemm_kernel<BN, S><<<grid, kThreads, L::kAlloc, st>>>(mA, mB, p);
-  return cudaGetLastError();
+  err = cudaGetLastError();
+  if (err != cudaSuccess && std::getenv("ZOLO_DEBUG")) {
+    cudaFuncAttributes fa{};
+    cudaFuncGetAttributes(&fa, split_gemm_kernel<BN, S>);
+    std::fprintf(stderr,
+                 "zolo: split_gemm_kernel<%d,%d> launch (grid %u x %u x %u, %d threads, %d B smem): %s"
+                 " [maxThreadsPerBlock %d, numRegs %d, localSizeBytes %zu, maxDynamicSmem %d]\n",
+                 BN, S, grid.x, grid.y, grid.z, kThreads, L::kAlloc, cudaGetErrorString(err),
+                 fa.maxThreadsPerBlock, fa.numRegs, fa.localSizeBytes,
+                 fa.maxDynamicSharedSizeBytes);
+  }
+  return err;
 }
 
 }  // namespace
@@ -448,10 +545,22 @@ thread_local SplitWork* t_split = nullptr;
 
 void set_split_engine(SplitWork* w) { t_split = w; }
 
+// Estimated seconds on GB300 of one call on the FP64 pipe and on the split
+// tensor-core path (slicing traffic + output traffic + slice-pair products +
+// launch latency); the cheaper one runs.
 cudaError_t gemm_any(const GemmArgs& g, cudaStream_t st) {
-  // the tensor-core path pays a slicing pass per operand: small products stay on DFMA
-  if (t_split && (double)g.M * g.N * g.K >= 4.0e6) return gemm_split(g, *t_split, st);
-  return gemm_f64(g, st);
+  if (!t_split || g.M <= 0 || g.N <= 0 || g.K <= 0) return gemm_f64(g, st);
+  const double t64 = gemm_flops(g) / 0.9e12;
+  const bool swap = g.M < kTileM && g.N > g.M;
+  const double ra = (double)round_up(swap ? g.N : g.M, kTileM);
+  const double rb = (double)round_up(swap ? g.M : g.N, 64);
+  const double kp = (double)round_up(g.K, kBK);
+  const double S = t_split->slices_s;
+  const double slice_bytes = g.batch * (8.0 + 2.0 * S) * (ra + rb) * kp;
+  const double out_bytes = (g.reduce ? 1 : g.batch) * 8.0 * g.M * (double)g.N * (g.beta != 0.0 ? 2 : 1);
+  const double tensor = S * (S + 1) / 2 * 2.0 * ra * rb * kp * g.batch / 0.7e15;
+  const double tsplit = slice_bytes / 4e12 + out_bytes / 5e12 + tensor + 30e-6;
+  return tsplit < t64 ? gemm_split(g, *t_split, st) : gemm_f64(g, st);
 }
 
 size_t split_slice_elems(int64_t M, int64_t N, int64_t K, int batch, int S) {

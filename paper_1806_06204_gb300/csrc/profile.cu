@@ -17,7 +17,7 @@ namespace zolo {
 namespace {
 
 const char* kClassNames[kProfClasses] = {"gemm_f64", "qr_panel", "chol_diag", "jacobi_round",
-                                         "combine", "other", "gemm_split", "slice"};
+                                         "combine", "other", "gemm_split", "slice", "jacobi32_sweep"};
 
 struct Pending {
   int cls;

@@ -13,6 +13,8 @@
 // Q2 (the bottom block of Q) stays exactly upper triangular: the explicit V
 // holds exact zeros outside each reflector's support, so every product that the
 // structure makes zero is an exact zero in floating point too.
+#include <cooperative_groups.h>
+
 #include <cmath>
 
 #include "zolo_internal.h"
@@ -21,6 +23,8 @@ namespace zolo {
 namespace {
 
 constexpr int kPanelThreads = 512;
+constexpr int kPanelCluster = 8;            // CTAs per shift in the cluster panel
+constexpr int64_t kClusterPanelMinRows = 512;
 
 // One CTA per shift j.  Factors panel columns [c0, c0 + nbp) of W_j in place
 // (R on and above the diagonal, Householder vectors below it, as LAPACK), writes
@@ -142,6 +146,159 @@ qr_panel_kernel(double* W, int64_t strideW, int64_t ldw, int64_t m, int64_t c0, 
   for (int e = tid; e < NB * NB; e += kPanelThreads) Tp[e] = Ts[e % NB][e / NB];
 }
 
+// Cluster form of the panel factorisation: CG CTAs per shift (one thread-block
+// cluster), each owning a contiguous slice of the panel's row window.  Per
+// column, every CTA reduces its rows' part of the norm (and the owner of the
+// diagonal row contributes alpha), the partials are exchanged through
+// distributed shared memory, every CTA forms the same beta/tau from the same
+// ordered sum, scales its rows of v, and the same exchange gives the dot
+// products for the update and for T.  Two hardware cluster barriers per
+// column; the partial buffers alternate between columns so that no third
+// barrier is needed before they are rewritten.  All rows a CTA reads or writes
+// in W and V are its own, so the only cross-CTA traffic is the partials.
+template <int NB, int CG>
+__global__ void __cluster_dims__(CG, 1, 1) __launch_bounds__(256)
+qr_panel_cluster_kernel(double* W, int64_t strideW, int64_t ldw, int64_t m, int64_t c0, int nbp,
+                        double* V, int64_t strideV, int64_t ldv, double* T, int64_t strideT,
+                        int* status) {
+  namespace cgrp = cooperative_groups;
+  cgrp::cluster_group cluster = cgrp::this_cluster();
+  constexpr int kT = 256, kWarps = kT / 32;
+  __shared__ double part[2][NB + 2];        // [0, NB): dots, NB: norm^2, NB+1: alpha
+  __shared__ double red[kWarps][NB + 2];
+  __shared__ double dots[NB];
+  __shared__ double Ts[NB][NB + 1];
+  __shared__ double s_tau, s_scal, s_beta;
+
+  const int rank = (int)cluster.block_rank();
+  const int shift = blockIdx.x / CG;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double* Wj = W + shift * strideW;
+  double* Vp = V + shift * strideV + c0 * ldv;
+  double* Tp = T + shift * strideT + (c0 / NB) * (int64_t)(NB * NB);
+  const int64_t height = m + NB;
+  const int64_t chunk = (height + CG - 1) / CG;
+  const int64_t lo = c0 + rank * chunk;                   // my window rows [lo, hi)
+  const int64_t hi = lo + chunk < c0 + height ? lo + chunk : c0 + height;
+
+  for (int e = tid; e < NB * (NB + 1); e += kT) (&Ts[0][0])[e] = 0.0;
+
+  for (int i = 0; i < nbp; ++i) {
+    const int64_t c = c0 + i;
+    const int buf = i & 1;
+    double* col = Wj + c * ldw;
+    const int64_t r0 = lo > c ? lo : c;                  // my part of the support [c, m + c]
+    const int64_t r1 = hi < m + c + 1 ? hi : m + c + 1;
+    // ---- 1. partial norm of the tail (rows > c) and alpha from the owner of row c
+    double ss = 0.0;
+    for (int64_t r = (r0 > c + 1 ? r0 : c + 1) + tid; r < r1; r += kT) {
+      const double v = col[r];
+      ss = fma(v, v, ss);
+    }
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    if (lane == 0) red[warp][0] = ss;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < kWarps; ++w) t += red[w][0];
+      part[buf][NB] = t;
+      part[buf][NB + 1] = (c >= lo && c < hi) ? col[c] : 0.0;
+    }
+    cluster.sync();
+    if (tid == 0) {
+      double s = 0.0, alpha = 0.0;
+      for (int rk = 0; rk < CG; ++rk) {
+        const double* rp = cluster.map_shared_rank(&part[buf][0], rk);
+        s += rp[NB];
+        alpha += rp[NB + 1];
+      }
+      double beta, tau, scal;
+      if (s == 0.0) {
+        beta = alpha; tau = 0.0; scal = 0.0;
+      } else {
+        beta = -copysign(sqrt(fma(alpha, alpha, s)), alpha);
+        tau = (beta - alpha) / beta;
+        scal = 1.0 / (alpha - beta);
+      }
+      if (rank == 0 && (!isfinite(beta) || !isfinite(tau))) atomicOr(status + kStatNonFinite, 1);
+      s_beta = beta; s_tau = tau; s_scal = scal;
+    }
+    __syncthreads();
+    const double tau = s_tau, scal = s_scal;
+    // ---- 2. my rows of v, and of the explicit reflector (zeros outside the support)
+    double* Vcol = Vp + (int64_t)i * ldv;
+    for (int64_t r = lo + tid; r < hi; r += kT) {
+      double v;
+      if (r < c || r > m + c) {
+        v = 0.0;
+      } else if (r == c) {
+        v = 1.0;
+      } else {
+        v = col[r] * scal;
+        col[r] = v;
+      }
+      Vcol[r - c0] = v;
+    }
+    __syncthreads();
+    if (tid == 0 && c >= lo && c < hi) col[c] = s_beta;
+    // ---- 3. partial dots of v with the later panel columns and the earlier reflectors
+    double acc[NB];
+#pragma unroll
+    for (int q = 0; q < NB; ++q) acc[q] = 0.0;
+    for (int64_t r = r0 + tid; r < r1; r += kT) {
+      const double v = Vcol[r - c0];
+#pragma unroll
+      for (int q = 0; q < NB; ++q) {
+        if (q < nbp && q != i) {
+          const double o = q > i ? Wj[r + (c0 + q) * ldw] : Vp[(r - c0) + (int64_t)q * ldv];
+          acc[q] = fma(v, o, acc[q]);
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      double v = acc[q];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) red[warp][q] = v;
+    }
+    __syncthreads();
+    if (tid < NB) {
+      double t = 0.0;
+      for (int w = 0; w < kWarps; ++w) t += red[w][tid];
+      part[buf][tid] = t;
+    }
+    cluster.sync();
+    if (tid < NB) {
+      double t = 0.0;
+      for (int rk = 0; rk < CG; ++rk) t += cluster.map_shared_rank(&part[buf][0], rk)[tid];
+      dots[tid] = t;
+    }
+    __syncthreads();
+    // ---- 4. my rows of the later panel columns: W[:, q] -= tau * dots[q] * v
+    for (int64_t r = r0 + tid; r < r1; r += kT) {
+      const double v = Vcol[r - c0];
+#pragma unroll
+      for (int q = 0; q < NB; ++q) {
+        if (q > i && q < nbp) {
+          double* pq = Wj + r + (c0 + q) * ldw;
+          *pq = fma(-tau * dots[q], v, *pq);
+        }
+      }
+    }
+    // ---- 5. T(0:i, i) = -tau T(0:i, 0:i) V^T v_i (same in every CTA)
+    if (tid < i) {
+      double t = 0.0;
+      for (int pc = tid; pc < i; ++pc) t = fma(Ts[tid][pc], dots[pc], t);
+      Ts[tid][i] = -tau * t;
+    }
+    if (tid == 0) Ts[i][i] = tau;
+    __syncthreads();
+  }
+  if (rank == 0)
+    for (int e = tid; e < NB * NB; e += kT) Tp[e] = Ts[e % NB][e / NB];
+  cluster.sync();   // no CTA leaves while another may still read its partials
+}
+
 }  // namespace
 
 cudaError_t structured_qr_q(const QrBuffers& b, int64_t m, int64_t n, int r, int* status,
@@ -158,8 +315,12 @@ cudaError_t structured_qr_q(const QrBuffers& b, int64_t m, int64_t n, int r, int
     {
       ProfScope ps(kProfPanel, st, 3.0 * r * (double)(m + 1) * nbp * nbp,
                    8.0 * r * (double)(m + NB) * nbp * 2.0);
-      qr_panel_kernel<NB><<<r, kPanelThreads, 0, st>>>(b.W, b.strideW, ldw, m, c0, nbp, b.V,
-                                                        b.strideV, ldv, b.T, b.strideT, status);
+      if (m >= kClusterPanelMinRows)
+        qr_panel_cluster_kernel<NB, kPanelCluster><<<r * kPanelCluster, 256, 0, st>>>(
+            b.W, b.strideW, ldw, m, c0, nbp, b.V, b.strideV, ldv, b.T, b.strideT, status);
+      else
+        qr_panel_kernel<NB><<<r, kPanelThreads, 0, st>>>(b.W, b.strideW, ldw, m, c0, nbp, b.V,
+                                                          b.strideV, ldv, b.T, b.strideT, status);
     }
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     const int64_t ntr = n - c0 - nbp;

@@ -43,7 +43,7 @@ int build_schedule(double ell0, int r, int max_iter, Schedule* out);
 
 // ------------------------------------------------------------- launch scopes
 enum ProfClass { kProfGemm = 0, kProfPanel, kProfCholDiag, kProfJacobi, kProfCombine, kProfOther,
-                 kProfSplitGemm, kProfSlice, kProfClasses };
+                 kProfSplitGemm, kProfSlice, kProfJacobi32, kProfClasses };
 // Counts the launch made inside its scope and, while profiling is on, brackets
 // it with CUDA events on `st`.  flops/bytes: the launch's algorithmic work.
 class ProfScope {
@@ -67,6 +67,7 @@ enum StatusSlot {
   kStatNonFinite = 0,   // a NaN/Inf was produced
   kStatCholFail = 1,    // non-positive pivot in a Cholesky diagonal block
   kStatJacobiRot = 2,   // rotations applied in the current Jacobi sweep
+  kStatJacobiMaxCos = 3,  // largest |cos| between two columns seen in the sweep (float bits)
   kStatSlots = 4
 };
 
@@ -177,7 +178,17 @@ struct EigWork {
   double* lam;      // n
   int* perm;        // n (device)
   int* status;
+  float* X32;       // n x n, FP32 sweeps
+  float* Z32;       // n x n, accumulated FP32 rotations
+  double* Z;        // n x n, Z orthonormalised in FP64
+  double* tmp;      // n x 64 scratch of the triangular solve
+  unsigned* bar;    // grid-barrier words (2)
+  int* err;         // bounded-wait error flag
 };
+// Y <- X R^{-1} for upper R with inverted diagonal blocks (cholesky_upper_batched output)
+cudaError_t trsm_right_upper_batched(const double* X, int64_t ldx, const CholBuffers& b, double* Y,
+                                     int64_t strideY, double* tmp, int64_t strideTmp, int64_t m,
+                                     int64_t n, int r, cudaStream_t st);
 int eig_sym_jacobi(const double* H, int64_t ldh, int64_t n, double* V, int64_t ldv, double* lam_out,
                    const EigWork& w, int* sweeps, cudaStream_t st);
 cudaError_t column_norms(const double* X, int64_t ldx, int64_t m, int64_t n, double* out,
@@ -191,7 +202,7 @@ cudaError_t gather_columns(const double* X, int64_t ldx, double* Y, int64_t ldy,
 cudaError_t transpose_lower(const double* R, int64_t ldr, double* X, int64_t ldx, int64_t n,
                             cudaStream_t st);
 cudaError_t jacobi_round(double* X, int64_t ldx, int64_t m, int64_t n_even, int64_t n_real, int round,
-                         int* status, cudaStream_t st);
+                         double tol, int* status, cudaStream_t st);
 
 #endif  // __CUDACC__
 
