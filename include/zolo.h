@@ -119,6 +119,24 @@ int zolo_svd(zolo_handle_t handle, const double* A, int64_t m, int64_t n, int64_
              double* U, int64_t ldu, double* S, double* V, int64_t ldv,
              const zolo_opts_t* opts, zolo_info_t* info, void* stream);
 
+/* Many polar decompositions in one call.  Matrix i is A[i] (m[i] x n[i],
+   leading dimension lda[i]) with its own options opts[i] (its own r, bounds,
+   precision); results go to Qp[i] (ldq[i]) and H[i] (ldh[i]), and info[i].
+   The pointer and size arrays are HOST arrays of `count` entries; the matrix
+   pointers are device pointers.  Every matrix's iterations are queued without
+   host round trips on the handle's internal streams (forked from and joined
+   back to `stream`), so small matrices of different sizes run concurrently;
+   the whole batch is recorded as one CUDA graph and the graph is replayed when
+   the same batch (pointers, sizes, options) is decomposed again.  A Cholesky
+   breakdown found at the end is redone for that matrix on the single-matrix
+   path.  opts[i].posteriori must be 0.  Returns the first non-zero status
+   (info[i].status per matrix); -i codes refer to the arguments as in zolo_pd
+   with the offending matrix's info[].status set. */
+int zolo_pd_batched(zolo_handle_t handle, int count, const double* const* A, const int64_t* m,
+                    const int64_t* n, const int64_t* lda, double* const* Qp, const int64_t* ldq,
+                    double* const* H, const int64_t* ldh, const zolo_opts_t* opts,
+                    zolo_info_t* info, void* stream);
+
 /* As zolo_pd / zolo_svd, but every matrix pointer is a HOST pointer: the call
    copies A to the device, computes, and copies the results back (pageable or
    pinned host memory; pinned is faster).  Device buffers come from the

@@ -74,6 +74,9 @@ def _load():
     lib.zolo_strerror.restype = ctypes.c_char_p
     lib.zolo_dgemm.argtypes = [P, I, I, I64, I64, I64, D, P, I64, P, I64, D, P, I64, I, I, P]
     lib.zolo_dgemm.restype = I
+    lib.zolo_pd_batched.argtypes = [P, I, P, P, P, P, P, P, P, P, ctypes.POINTER(ZoloOpts),
+                                    ctypes.POINTER(ZoloInfo), P]
+    lib.zolo_pd_batched.restype = I
     lib.zolo_kernel_launches.argtypes = []
     lib.zolo_kernel_launches.restype = ctypes.c_uint64
     lib.zolo_profile.argtypes = [I]
@@ -88,7 +91,7 @@ LIB = _load()
 EXPORTED = ["zolo_opts_default", "zolo_create", "zolo_destroy", "zolo_coefficients",
             "zolo_schedule", "zolo_pd", "zolo_svd", "zolo_pd_host", "zolo_svd_host",
             "zolo_strerror", "zolo_kernel_launches", "zolo_profile", "zolo_profile_read",
-            "zolo_dgemm"]
+            "zolo_dgemm", "zolo_pd_batched"]
 
 
 def kernel_launches() -> int:
@@ -247,6 +250,45 @@ def zolo_svd(handle: Handle, A, o: ZoloOpts, stream=None, check=True):
     return U, S, V, Info.from_c(info)
 
 
+def zolo_pd_batched(handle: Handle, As, os, Qps=None, Hs=None, stream=None, check=True):
+    """Polar decompositions of a list of device tensors in one call.
+
+    `os` is one ZoloOpts for all matrices or a list with one per matrix.
+    Returns (Qps, Hs, infos, status)."""
+    n_mat = len(As)
+    if isinstance(os, ZoloOpts):
+        os = [os] * n_mat
+    if len(os) != n_mat:
+        raise ValueError("one option set per matrix")
+    for a in As:
+        _colmajor(a, "A")
+    Qps = [empty_colmajor(a.shape[0], a.shape[1], a.device) for a in As] if Qps is None else Qps
+    Hs = [empty_colmajor(a.shape[1], a.shape[1], a.device) for a in As] if Hs is None else Hs
+    for q, h in zip(Qps, Hs):
+        _colmajor(q, "Qp")
+        _colmajor(h, "H")
+    PA = ctypes.c_void_p * max(n_mat, 1)
+    LA = ctypes.c_int64 * max(n_mat, 1)
+    a_p = PA(*[a.data_ptr() for a in As])
+    q_p = PA(*[q.data_ptr() for q in Qps])
+    h_p = PA(*[h.data_ptr() for h in Hs])
+    m_a = LA(*[a.shape[0] for a in As])
+    n_a = LA(*[a.shape[1] for a in As])
+    lda = LA(*[_ld(a) for a in As])
+    ldq = LA(*[_ld(q) for q in Qps])
+    ldh = LA(*[_ld(h) for h in Hs])
+    o_a = (ZoloOpts * max(n_mat, 1))(*os)
+    i_a = (ZoloInfo * max(n_mat, 1))()
+    e = LIB.zolo_pd_batched(handle.ptr, n_mat, ctypes.cast(a_p, ctypes.c_void_p),
+                            ctypes.cast(m_a, ctypes.c_void_p), ctypes.cast(n_a, ctypes.c_void_p),
+                            ctypes.cast(lda, ctypes.c_void_p), ctypes.cast(q_p, ctypes.c_void_p),
+                            ctypes.cast(ldq, ctypes.c_void_p), ctypes.cast(h_p, ctypes.c_void_p),
+                            ctypes.cast(ldh, ctypes.c_void_p), o_a, i_a, _stream(stream))
+    if e and check:
+        raise ZoloError(e, "zolo_pd_batched")
+    return Qps, Hs, [Info.from_c(i_a[i]) for i in range(n_mat)], e
+
+
 def _host_ptr(a):
     import numpy as np
     if a.dtype != np.float64 or not a.flags.f_contiguous:
@@ -296,4 +338,3 @@ def zolo_dgemm(handle: Handle, A, B, C=None, alpha=1.0, beta=0.0, transA=False, 
     if e and check:
         raise ZoloError(e, "zolo_dgemm")
     return C
-

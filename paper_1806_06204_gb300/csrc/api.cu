@@ -18,14 +18,44 @@
 #include <cstdio>
 #include <cstring>
 #include <vector>
+#include <algorithm>
+#include <cstdint>
 
 #include "../../include/zolo.h"
 #include "zolo_internal.h"
 
 using namespace zolo;
 
+// One concurrent lane of zolo_pd_batched: a stream with its own workspace.
+struct BatchSlot {
+  cudaStream_t st = nullptr;
+  cudaEvent_t done = nullptr;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  void* slices = nullptr;
+  size_t slice_elems = 0;
+  int* exps = nullptr;
+  size_t exp_elems = 0;
+  int* err = nullptr;
+};
+
+struct BatchGraph {
+  std::vector<uint64_t> key;
+  cudaGraphExec_t exec = nullptr;
+  uint64_t launches = 0;         // kernels recorded in the graph
+};
+
 struct zolo_handle_s {
   int device = 0;
+  std::vector<BatchSlot> slots;
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t joined = nullptr;
+  cudaStream_t cap = nullptr;    // the stream the batch graph is captured on and launched from
+  double* brec = nullptr;        // per-matrix device records (status + norms)
+  size_t brec_count = 0;
+  double* hrec = nullptr;        // pinned host mirror of brec
+  size_t hrec_count = 0;
+  std::vector<BatchGraph> graphs;
   void* ws = nullptr;
   size_t ws_bytes = 0;
   void* io = nullptr;
@@ -438,6 +468,65 @@ int pd_core(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda,
   return status;
 }
 
+// Per-matrix device record of the batched path: status words, then norms.
+constexpr int kRecDoubles = 4 + 2 * (kMaxIters + 2);
+
+// Queue one polar decomposition on `st` without any host synchronisation:
+// status and norms go to R.b.status / R.b.norms (the matrix's own record).
+int pd_enqueue(const Run& R, const double* A, int64_t lda, double* Qp, int64_t ldq, double* H,
+               int64_t ldh, const Schedule& sch, const zolo_opts_t& o, double alpha) {
+  const int64_t m = R.m, n = R.n;
+  const PdBufs& b = R.b;
+  cudaStream_t st = R.st;
+  CK(cudaMemsetAsync(b.status, 0, sizeof(int) * kStatSlots, st));
+  CK(cudaMemsetAsync(b.norms, 0, sizeof(double) * 2 * (kMaxIters + 2), st));
+  double* X = b.X;
+  double* Xn = b.Xn;
+  CK(scale_copy(A, lda, X, m, m, n, 1.0 / alpha, st));
+  CK(check_finite(X, m, m, n, b.status, st));
+  for (int k = 0; k < sch.iters; ++k) {
+    const bool qr = o.force_qr == 1 ? true : (o.force_qr == 0 ? false : sch.use_qr[k]);
+    if (int e = iterate(R, sch.co[k], qr, X, Xn, b.norms + 2 * k)) return e;
+    std::swap(X, Xn);
+  }
+  for (int s = 0; s < o.ns_steps; ++s) {
+    GemmArgs g;
+    g.M = g.N = (int)n; g.K = (int)m; g.transA = 1;
+    g.A = X; g.lda = m; g.B = X; g.ldb = m; g.Cout = b.M; g.ldcout = n;
+    g.alpha[0] = 1.0;
+    CK(gemm_any(g, st));
+    GemmArgs u;
+    u.M = (int)m; u.N = (int)n; u.K = (int)n;
+    u.A = X; u.lda = m; u.B = b.M; u.ldb = n;
+    u.Cin = X; u.ldcin = m; u.beta = 1.5; u.Cout = Xn; u.ldcout = m;
+    u.alpha[0] = -0.5;
+    CK(gemm_any(u, st));
+    std::swap(X, Xn);
+  }
+  GemmArgs g;
+  g.M = g.N = (int)n; g.K = (int)m; g.transA = 1;
+  g.A = X; g.lda = m; g.B = A; g.ldb = lda; g.Cout = b.M; g.ldcout = n;
+  g.alpha[0] = 1.0;
+  CK(gemm_any(g, st));
+  CK(symmetrize(b.M, n, H, ldh, n, st));
+  CK(copy_matrix(X, m, Qp, ldq, m, n, st));
+  return 0;
+}
+
+int grow(void** p, size_t* have, size_t bytes) {
+  if (*have >= bytes) return 0;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *have = 0;
+  if (cudaMalloc(p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return ZOLO_ENOMEM;
+  }
+  *have = bytes;
+  return 0;
+}
+
 }  // namespace
 
 extern "C" {
@@ -477,6 +566,21 @@ int zolo_destroy(zolo_handle_t h) {
   if (h->slices) cudaFree(h->slices);
   if (h->exps) cudaFree(h->exps);
   if (h->err) cudaFree(h->err);
+  for (BatchSlot& sl : h->slots) {
+    if (sl.st) cudaStreamDestroy(sl.st);
+    if (sl.done) cudaEventDestroy(sl.done);
+    if (sl.ws) cudaFree(sl.ws);
+    if (sl.slices) cudaFree(sl.slices);
+    if (sl.exps) cudaFree(sl.exps);
+    if (sl.err) cudaFree(sl.err);
+  }
+  for (BatchGraph& g : h->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (h->fork) cudaEventDestroy(h->fork);
+  if (h->joined) cudaEventDestroy(h->joined);
+  if (h->cap) cudaStreamDestroy(h->cap);
+  if (h->brec) cudaFree(h->brec);
+  if (h->hrec) cudaFreeHost(h->hrec);
   if (h->e0) cudaEventDestroy(h->e0);
   if (h->e1) cudaEventDestroy(h->e1);
   delete h;
@@ -699,6 +803,269 @@ int zolo_dgemm(zolo_handle_t h, int transA, int transB, int64_t m, int64_t n, in
       cudaStreamSynchronize(st) != cudaSuccess)
     return ZOLO_ECUDA;
   return herr ? ZOLO_ETIMEOUT : 0;
+}
+
+int zolo_pd_batched(zolo_handle_t h, int count, const double* const* A, const int64_t* m,
+                    const int64_t* n, const int64_t* lda, double* const* Qp, const int64_t* ldq,
+                    double* const* H, const int64_t* ldh, const zolo_opts_t* opts,
+                    zolo_info_t* info, void* stream) {
+  if (!h) return -1;
+  if (count < 0) return -2;
+  if (count == 0) return 0;
+  if (!A || !m || !n || !lda || !Qp || !ldq || !H || !ldh || !opts || !info) return -3;
+  for (int i = 0; i < count; ++i) {
+    std::memset(&info[i], 0, sizeof(zolo_info_t));
+    int e = validate(h, A[i], m[i], n[i], lda[i], Qp[i], ldq[i], H[i], ldh[i], &opts[i]);
+    if (e == 0 && opts[i].posteriori) e = -10;
+    if (e) {
+      info[i].status = e;
+      return e;
+    }
+  }
+  if (cudaSetDevice(h->device) != cudaSuccess) return ZOLO_ECUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaEventRecord(h->e0, st);
+  // ---- bounds and schedules (alpha <= 0: ||A_i||_F, all norms in one pass)
+  std::vector<double> alpha(count);
+  std::vector<Schedule> sch(count);
+  {
+    std::vector<int> need;
+    for (int i = 0; i < count; ++i) {
+      alpha[i] = opts[i].alpha;
+      if (alpha[i] <= 0.0) need.push_back(i);
+    }
+    if (!need.empty()) {
+      double* tmp = nullptr;
+      if (cudaMalloc(&tmp, sizeof(double) * (2 * need.size() + 2 * 1024)) != cudaSuccess) {
+        cudaGetLastError();
+        return ZOLO_ENOMEM;
+      }
+      std::vector<double> nr(2 * need.size());
+      int e = 0;
+      for (size_t q = 0; q < need.size() && !e; ++q) {
+        const int i = need[q];
+        if (frob_norm2(A[i], lda[i], m[i], n[i], tmp + 2 * need.size(), tmp + 2 * q, st) != cudaSuccess)
+          e = ZOLO_ECUDA;
+      }
+      if (!e && (cudaMemcpyAsync(nr.data(), tmp, sizeof(double) * nr.size(), cudaMemcpyDeviceToHost,
+                                 st) != cudaSuccess ||
+                 cudaStreamSynchronize(st) != cudaSuccess))
+        e = ZOLO_ECUDA;
+      cudaFree(tmp);
+      if (e) return e;
+      for (size_t q = 0; q < need.size(); ++q) alpha[need[q]] = std::sqrt(nr[2 * q]);
+    }
+    for (int i = 0; i < count; ++i) {
+      if (!(alpha[i] > 0.0) || !std::isfinite(alpha[i])) {
+        info[i].status = ZOLO_ENONFINITE;
+        return ZOLO_ENONFINITE;
+      }
+      if (build_schedule(std::min(1.0, opts[i].beta / alpha[i]), opts[i].r, opts[i].max_iter,
+                         &sch[i]) != 0) {
+        info[i].status = -10;
+        return -10;
+      }
+    }
+  }
+  // ---- lanes: streams with workspace for the largest matrix of the batch
+  const int nslots = std::min(count, 16);
+  int64_t mmax = 0, nmax = 0;
+  int rmax = 1;
+  bool any_split = false;
+  for (int i = 0; i < count; ++i) {
+    mmax = std::max(mmax, m[i]);
+    nmax = std::max(nmax, n[i]);
+    rmax = std::max(rmax, sch[i].r);
+    any_split |= opts[i].prec == ZOLO_SPLIT_BF16;
+  }
+  if ((int)h->slots.size() < nslots) h->slots.resize(nslots);
+  if (!h->fork && cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming) != cudaSuccess)
+    return ZOLO_ECUDA;
+  const size_t ws_bytes = layout(nullptr, mmax, nmax, rmax, false, nullptr);
+  for (int k = 0; k < nslots; ++k) {
+    BatchSlot& sl = h->slots[k];
+    if (!sl.st && cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) != cudaSuccess)
+      return ZOLO_ECUDA;
+    if (!sl.done && cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess)
+      return ZOLO_ECUDA;
+    if (int e = grow(&sl.ws, &sl.ws_bytes, ws_bytes)) return e;
+    if (any_split) {
+      const size_t per = split_elems_per_entry(mmax, nmax) * (size_t)rmax;
+      size_t have = sl.slice_elems * 2;
+      if (int e = grow(&sl.slices, &have, per * 2)) return e;
+      sl.slice_elems = have / 2;
+      const size_t ex = (size_t)2 * kGemmMaxBatch * (size_t)(2 * mmax + nmax + 512);
+      size_t hx = sl.exp_elems * sizeof(int);
+      if (int e = grow((void**)&sl.exps, &hx, ex * sizeof(int))) return e;
+      sl.exp_elems = hx / sizeof(int);
+      size_t he = sl.err ? sizeof(int) : 0;
+      if (int e = grow((void**)&sl.err, &he, sizeof(int))) return e;
+    }
+  }
+  // ---- per-matrix records
+  {
+    size_t have = h->brec_count * sizeof(double);
+    if (int e = grow((void**)&h->brec, &have, sizeof(double) * kRecDoubles * (size_t)count)) return e;
+    h->brec_count = have / sizeof(double);
+    if (h->hrec_count < (size_t)count * kRecDoubles) {
+      if (h->hrec) cudaFreeHost(h->hrec);
+      h->hrec = nullptr;
+      h->hrec_count = 0;
+      if (cudaMallocHost(&h->hrec, sizeof(double) * kRecDoubles * (size_t)count) != cudaSuccess) {
+        cudaGetLastError();
+        return ZOLO_ENOMEM;
+      }
+      h->hrec_count = (size_t)count * kRecDoubles;
+    }
+  }
+  if (!h->cap && cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess)
+    return ZOLO_ECUDA;
+  if (!h->joined && cudaEventCreateWithFlags(&h->joined, cudaEventDisableTiming) != cudaSuccess)
+    return ZOLO_ECUDA;
+  if (any_split) split_prepare();
+  // ---- the batch as one graph: key = every pointer, size and option of the call
+  std::vector<uint64_t> key;
+  key.reserve(8 + 12 * (size_t)count);
+  key.push_back((uint64_t)count);
+  key.push_back((uint64_t)(uintptr_t)h->brec);
+  for (int k = 0; k < nslots; ++k) key.push_back((uint64_t)(uintptr_t)h->slots[k].ws);
+  for (int i = 0; i < count; ++i) {
+    const uint64_t f[] = {(uint64_t)(uintptr_t)A[i], (uint64_t)m[i], (uint64_t)n[i],
+                          (uint64_t)lda[i], (uint64_t)(uintptr_t)Qp[i], (uint64_t)ldq[i],
+                          (uint64_t)(uintptr_t)H[i], (uint64_t)ldh[i]};
+    key.insert(key.end(), f, f + 8);
+    uint64_t ob[sizeof(zolo_opts_t) / 8 + 1] = {};
+    std::memcpy(ob, &opts[i], sizeof(zolo_opts_t));
+    key.insert(key.end(), ob, ob + sizeof(zolo_opts_t) / 8 + 1);
+    uint64_t ab;
+    std::memcpy(&ab, &alpha[i], 8);
+    key.push_back(ab);
+  }
+  cudaGraphExec_t exec = nullptr;
+  for (BatchGraph& g : h->graphs)
+    if (g.key == key) exec = g.exec;
+  // largest matrices first, dealt round-robin over the lanes
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return m[a] * n[a] * n[a] * sch[a].r > m[b] * n[b] * n[b] * sch[b].r;
+  });
+  cudaStream_t cap = h->cap;
+  auto enqueue_all = [&]() -> int {
+    CK(cudaEventRecord(h->fork, cap));
+    for (int k = 0; k < nslots; ++k) CK(cudaStreamWaitEvent(h->slots[k].st, h->fork, 0));
+    for (int q = 0; q < count; ++q) {
+      const int i = order[q];
+      BatchSlot& sl = h->slots[q % nslots];
+      Run R{m[i], n[i], sch[i].r, {}, sl.st};
+      layout(sl.ws, m[i], n[i], sch[i].r, false, &R.b);
+      double* rec = h->brec + (size_t)i * kRecDoubles;
+      R.b.status = reinterpret_cast<int*>(rec);
+      R.b.norms = rec + 4;
+      SplitWork w{sl.slices, sl.slice_elems, sl.exps, sl.exp_elems, sl.err, 9};
+      set_split_engine(opts[i].prec == ZOLO_SPLIT_BF16 ? &w : nullptr);
+      const int e = pd_enqueue(R, A[i], lda[i], Qp[i], ldq[i], H[i], ldh[i], sch[i], opts[i], alpha[i]);
+      set_split_engine(nullptr);
+      if (e) return e;
+    }
+    for (int k = 0; k < nslots; ++k) {
+      CK(cudaEventRecord(h->slots[k].done, h->slots[k].st));
+      CK(cudaStreamWaitEvent(cap, h->slots[k].done, 0));
+    }
+    return 0;
+  };
+  if (any_split)
+    for (int k = 0; k < nslots; ++k)
+      if (h->slots[k].err) CK(cudaMemsetAsync(h->slots[k].err, 0, sizeof(int), st));
+  // the capture stream starts after everything queued on the caller's stream
+  CK(cudaEventRecord(h->joined, st));
+  CK(cudaStreamWaitEvent(cap, h->joined, 0));
+  // with per-kernel profiling on, the work is queued directly (events cannot
+  // bracket the nodes of a graph)
+  const bool use_graph = !profiling_enabled();
+  uint64_t graph_launches = 0;
+  for (BatchGraph& g : h->graphs)
+    if (g.exec == exec) graph_launches = g.launches;
+  if (!exec && use_graph) {
+    cudaGraph_t graph = nullptr;
+    const uint64_t l0 = zolo_kernel_launches();
+    if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      const int e = enqueue_all();
+      const cudaError_t ce = cudaStreamEndCapture(cap, &graph);
+      if (e == 0 && ce == cudaSuccess && graph &&
+          cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
+        graph_launches = zolo_kernel_launches() - l0;
+        // the capture itself ran no kernel: take the recorded ones back off the counter
+        add_launches(-(int64_t)graph_launches);
+        h->graphs.push_back({key, exec, graph_launches});
+        if (h->graphs.size() > 8) {
+          cudaGraphExecDestroy(h->graphs.front().exec);
+          h->graphs.erase(h->graphs.begin());
+        }
+      } else {
+        exec = nullptr;
+      }
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+    }
+  }
+  if (exec) {
+    CK(cudaGraphLaunch(exec, cap));
+    add_launches((int64_t)graph_launches);
+  } else if (int e = enqueue_all()) {
+    return e;
+  }
+  CK(cudaEventRecord(h->joined, cap));
+  CK(cudaStreamWaitEvent(st, h->joined, 0));
+  // ---- statuses and norms, once
+  CK(cudaMemcpyAsync(h->hrec, h->brec, sizeof(double) * kRecDoubles * (size_t)count,
+                     cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  int worst = 0;
+  bool timeout = false;
+  if (any_split)
+    for (int k = 0; k < nslots; ++k) {
+      int he = 0;
+      if (h->slots[k].err) CK(cudaMemcpy(&he, h->slots[k].err, sizeof(int), cudaMemcpyDeviceToHost));
+      timeout |= he != 0;
+    }
+  for (int i = 0; i < count; ++i) {
+    const double* rec = h->hrec + (size_t)i * kRecDoubles;
+    int stv[kStatSlots];
+    std::memcpy(stv, rec, sizeof(stv));
+    zolo_info_t& inf = info[i];
+    inf.r = sch[i].r;
+    inf.iters = sch[i].iters;
+    inf.ell[0] = sch[i].ell[0];
+    for (int k = 0; k < sch[i].iters; ++k) {
+      inf.used_qr[k] = opts[i].force_qr == 1 ? 1 : (opts[i].force_qr == 0 ? 0 : sch[i].use_qr[k]);
+      inf.ell[k + 1] = sch[i].ell[k + 1];
+      const double* nk = rec + 4 + 2 * k;
+      inf.delta[k] = nk[1] > 0.0 ? std::sqrt(nk[0] / nk[1]) : 0.0;
+    }
+    int e = 0;
+    if (stv[kStatCholFail]) {
+      // redo this matrix on the single-matrix path, which falls back to the QR form
+      zolo_info_t again;
+      e = zolo_pd(h, A[i], m[i], n[i], lda[i], Qp[i], ldq[i], H[i], ldh[i], &opts[i], &again, stream);
+      const double ms = inf.ms;
+      inf = again;
+      inf.ms = ms;
+    } else if (stv[kStatNonFinite]) {
+      e = ZOLO_ENONFINITE;
+    } else if (timeout && opts[i].prec == ZOLO_SPLIT_BF16) {
+      e = ZOLO_ETIMEOUT;
+    }
+    inf.status = e;
+    if (e && !worst) worst = e;
+  }
+  cudaEventRecord(h->e1, st);
+  if (cudaEventSynchronize(h->e1) == cudaSuccess) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->e0, h->e1);
+    for (int i = 0; i < count; ++i) info[i].ms = ms;
+  }
+  return worst;
 }
 
 const char* zolo_strerror(int code) {

@@ -187,7 +187,7 @@ struct SmemLayout {
 };
 
 template <int BN, int S>
-__global__ void __maxnreg__(112)
+__global__ void __launch_bounds__(kThreads, 1)
 split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                   const SplitEpi p) {
   using L = SmemLayout<BN, S>;
@@ -330,15 +330,15 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
 #pragma unroll
       for (int a = 0; a < kAcc; ++a) {
 #pragma unroll
-        for (int g = 0; g < HALF / 16; ++g) {
-          float v[16];
-          tc::tmem_ld16(tmem + lane_off + a * BN + half * HALF + g * 16, v);
+        for (int g = 0; g < HALF / 8; ++g) {
+          float v[8];
+          tc::tmem_ld8(tmem + lane_off + a * BN + half * HALF + g * 8, v);
           if (a == 0) {
 #pragma unroll
-            for (int i = 0; i < 16; ++i) i2[g * 16 + i] += __float2int_rn(v[i] * 4096.0f);
+            for (int i = 0; i < 8; ++i) i2[g * 8 + i] += __float2int_rn(v[i] * 4096.0f);
           } else {
 #pragma unroll
-            for (int i = 0; i < 16; ++i) pair_add(hr[g * 16 + i], lr[g * 16 + i], v[i]);
+            for (int i = 0; i < 8; ++i) pair_add(hr[g * 8 + i], lr[g * 8 + i], v[i]);
           }
         }
       }
@@ -539,6 +539,14 @@ cudaError_t gemm_split(const GemmArgs& g, SplitWork& w, cudaStream_t st) {
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+void split_prepare() {
+  cudaFuncSetAttribute(split_gemm_kernel<64, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       SmemLayout<64, 8>::kAlloc);
+  cudaFuncSetAttribute(split_gemm_kernel<64, 9>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       SmemLayout<64, 9>::kAlloc);
+  encode_fn();
 }
 
 thread_local SplitWork* t_split = nullptr;

@@ -72,7 +72,9 @@ void reset_locked() {
 ProfScope::ProfScope(int cls, cudaStream_t st, double flops, double bytes)
     : cls_(cls), st_(st), flops_(flops), bytes_(bytes) {
   g_launches.fetch_add(1, std::memory_order_relaxed);
-  if (g_on.load(std::memory_order_relaxed)) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (g_on.load(std::memory_order_relaxed) && cudaStreamIsCapturing(st, &cs) == cudaSuccess &&
+      cs == cudaStreamCaptureStatusNone) {
     std::lock_guard<std::mutex> lk(g_mu);
     a_ = take_event();
     cudaEventRecord(static_cast<cudaEvent_t>(a_), st_);
@@ -87,6 +89,10 @@ ProfScope::~ProfScope() {
   g_pending.push_back({cls_, static_cast<cudaEvent_t>(a_), b, flops_, bytes_});
   if (g_pending.size() > 100000) resolve_locked();
 }
+
+void add_launches(int64_t n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+
+bool profiling_enabled() { return g_on.load(std::memory_order_relaxed); }
 
 }  // namespace zolo
 

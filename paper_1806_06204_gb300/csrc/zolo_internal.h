@@ -60,6 +60,11 @@ class ProfScope {
   void* a_ = nullptr;
 };
 
+// Launch bookkeeping for graphs: kernels recorded at capture time are counted
+// when the graph is launched.
+void add_launches(int64_t n);
+bool profiling_enabled();
+
 // ----------------------------------------------------------------- device flags
 // A small device array of int counters written by kernels and read once at the
 // end of a call.
@@ -113,6 +118,8 @@ size_t split_slice_elems(int64_t M, int64_t N, int64_t K, int batch, int S);
 // The engine every contraction of the current call goes through: FP64 (DFMA)
 // when no split workspace is installed, the split tensor-core path otherwise.
 void set_split_engine(SplitWork* w);
+// Sets the kernels' launch attributes ahead of a stream capture.
+void split_prepare();
 cudaError_t gemm_any(const GemmArgs& g, cudaStream_t st);
 
 // --------------------------------------------------------------- elementwise
