@@ -158,6 +158,26 @@ int zolo_dgemm(zolo_handle_t handle, int transA, int transB, int64_t m, int64_t 
                double alpha, const double* A, int64_t lda, const double* B, int64_t ldb,
                double beta, double* C, int64_t ldc, int prec, int slices, void* stream);
 
+/* Allocation-free variant of zolo_dgemm with prec = ZOLO_SPLIT_BF16, for callers
+   that cannot allocate device memory where they call it (their memory belongs
+   to an external allocator or is reserved up front, or they must not call
+   cudaMalloc/cudaFree while they run).  No counterpart in the paper.  It needs
+   no handle and allocates nothing: the slice planes, exponents and error flag
+   live in a 16 MiB file-scope device array that every GPU loading the library
+   holds until the process exits.  Sizes whose slices do not fit are refused
+   with ZOLO_ENOMEM before any device work: slices * (ceil128(rows) +
+   ceil64(cols)) * ceil64(k) * 2 bytes must stay within 16 MiB - 64.25 KiB,
+   with (rows, cols) = (n, m) when m < 128 and n > m, else (m, n) (so
+   m = n = k = 512 fits with 8 slices, 1024 x 1024 x 512 does not).  The
+   first call on a device looks up the array's device address; make it before
+   any stream capture.  All calls share the array: calls that overlap on the
+   GPU race and must be serialised by the caller.  Matrices are device
+   pointers as in zolo_dgemm; `slices` = 8 or 9 (0 = 8).  Synchronises the
+   stream before returning. */
+int zolo_dgemm_noalloc(int transA, int transB, int64_t m, int64_t n, int64_t k, double alpha,
+                       const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
+                       double* C, int64_t ldc, int slices, void* stream);
+
 /* Short text for a return code. */
 const char* zolo_strerror(int code);
 

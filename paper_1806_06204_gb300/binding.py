@@ -74,6 +74,8 @@ def _load():
     lib.zolo_strerror.restype = ctypes.c_char_p
     lib.zolo_dgemm.argtypes = [P, I, I, I64, I64, I64, D, P, I64, P, I64, D, P, I64, I, I, P]
     lib.zolo_dgemm.restype = I
+    lib.zolo_dgemm_noalloc.argtypes = [I, I, I64, I64, I64, D, P, I64, P, I64, D, P, I64, I, P]
+    lib.zolo_dgemm_noalloc.restype = I
     lib.zolo_pd_batched.argtypes = [P, I, P, P, P, P, P, P, P, P, ctypes.POINTER(ZoloOpts),
                                     ctypes.POINTER(ZoloInfo), P]
     lib.zolo_pd_batched.restype = I
@@ -91,7 +93,7 @@ LIB = _load()
 EXPORTED = ["zolo_opts_default", "zolo_create", "zolo_destroy", "zolo_coefficients",
             "zolo_schedule", "zolo_pd", "zolo_svd", "zolo_pd_host", "zolo_svd_host",
             "zolo_strerror", "zolo_kernel_launches", "zolo_profile", "zolo_profile_read",
-            "zolo_dgemm", "zolo_pd_batched"]
+            "zolo_dgemm", "zolo_dgemm_noalloc", "zolo_pd_batched"]
 
 
 def kernel_launches() -> int:
@@ -338,3 +340,22 @@ def zolo_dgemm(handle: Handle, A, B, C=None, alpha=1.0, beta=0.0, transA=False, 
     if e and check:
         raise ZoloError(e, "zolo_dgemm")
     return C
+
+
+def zolo_dgemm_noalloc(A, B, C, alpha=1.0, beta=0.0, transA=False, transB=False, slices: int = 0,
+                       stream=None, check=True):
+    """Split-precision C = alpha op(A) op(B) + beta C using only the library's fixed
+    device scratch (no allocation inside the call); C must be given."""
+    _colmajor(A, "A")
+    _colmajor(B, "B")
+    _colmajor(C, "C")
+    m = A.shape[1] if transA else A.shape[0]
+    k = A.shape[0] if transA else A.shape[1]
+    n = B.shape[0] if transB else B.shape[1]
+    e = LIB.zolo_dgemm_noalloc(int(transA), int(transB), m, n, k, alpha,
+                               ctypes.c_void_p(A.data_ptr()), _ld(A), ctypes.c_void_p(B.data_ptr()),
+                               _ld(B), beta, ctypes.c_void_p(C.data_ptr()), _ld(C), slices,
+                               _stream(stream))
+    if e and check:
+        raise ZoloError(e, "zolo_dgemm_noalloc")
+    return e
