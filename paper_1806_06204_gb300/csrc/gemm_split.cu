@@ -1,21 +1,22 @@
 // Split-precision FP64 GEMM on the BF16 tensor cores (tcgen05 + TMEM + TMA),
 // the Ozaki scheme: every FP64 operand row (of op(A)) / column (of op(B)) is
-// scaled by a power of two 2^e so that its entries lie in (-1, 1), and cut into
-// S signed 6-bit digits by truncation,
-//     x 2^-e = sum_{s=1..S} d_s 2^{-6s} + O(2^{-6S}),   |d_s| <= 63,
-// stored pre-scaled (d_s 2^{-6s}) as BF16, which holds them exactly.  A product
-// is then sum over pairs (s, t), s + t <= S + 1, of BF16 x BF16 GEMMs whose
-// FP32 accumulation is exact as long as each sum stays below 2^24 units of its
-// last place: with |d| <= 63 a level (fixed s + t) of p pairs over k terms needs
-// p k 2^12 <= 2^24.  Levels 2..7 (p <= 6) therefore accumulate exactly in their
-// own TMEM accumulator over K-chunks of 512; the levels >= 8 share one FP32
-// accumulator.  That one is rounded at every MMA (about 500 additions per
-// chunk), but its terms lie 2^-36 below the leading level, so the accumulated
-// rounding stays near 2^-51 of the result.  (Merging from level 6 on instead
-// leaves ~2^-38: a single FP32 accumulator over ~1700 MMAs is not enough.)
-// The epilogue adds the seven accumulators in FP64 after every chunk and
-// applies 2^(e_i + f_j), alpha and beta.
-// Accuracy: |C - AB| <~ K 2^-6S max|A_i.| max|B_.j| (normwise ~2^-48 for S = 8).
+// scaled by a power of two 2^e so that its entries lie in (-1/2, 1/2), rounded
+// to the fixed-point integer N = round(x 2^(6S - e)) and written in S balanced
+// base-64 digits,
+//     x 2^-e = sum_{s=1..S} d_s 2^{-6s} (+ rounding below 2^{-6S-1}),   |d_s| <= 32,
+// each stored pre-scaled (d_s 2^{-6s}) as BF16, which holds it exactly.  A
+// product is the sum over digit pairs (s, t) with s + t <= S + 1 of BF16 x BF16
+// GEMMs.  Balanced digits make the dropped pairs and the rounding zero-mean
+// (truncated digits bias every term of a Gram diagonal the same way) and keep
+// |d_s d_t| <= 2^10, so a level (fixed s + t) of p pairs summed over k terms
+// stays below p k 2^10 units of its last place: exact in FP32 while that is
+// <= 2^24.  Levels 2..8 (p <= 7) therefore accumulate exactly in their own TMEM
+// accumulator over K-chunks of 2048; the levels >= 9 share one FP32
+// accumulator, whose rounding lies 2^-42 below the leading level.  After every
+// chunk the epilogue adds the exact levels as integers (an int64 in units of
+// 2^-48) and the merged one as a float, and at the end applies 2^(e_i + f_j),
+// alpha and beta in FP64.
+// Accuracy: |C - AB| <~ sqrt(K) 2^-6S max|A_i.| max|B_.j| (S = 9: FP64 grade).
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -34,8 +35,8 @@ namespace {
 constexpr int kBeta = 6;
 constexpr int kTileM = 128;
 constexpr int kBK = 64;            // one 128-byte swizzle row of BF16
-constexpr int kChunkK = 512;       // exact-accumulation span of the level sums
-constexpr int kAcc = 7;            // TMEM accumulators: levels 2..7 exact, levels >= 8 merged
+constexpr int kChunkK = 2048;      // exact-accumulation span of the level sums
+constexpr int kAcc = 8;            // TMEM accumulators: levels 2..8 exact, levels >= 9 merged
 constexpr int kARing = 4;
 constexpr int kEpiWarps = 16;      // four per TMEM lane quarter, each owning a quarter of the columns
 constexpr int kThreads = 64 + 32 * kEpiWarps;   // warp 0 TMA, warp 1 MMA, the rest epilogue
@@ -45,12 +46,13 @@ constexpr int kThreads = 64 + 32 * kEpiWarps;   // warp 0 TMA, warp 1 MMA, the r
 // Row i of op(X) (rows x K):  trans = 0: X[i + k ldx] (rows contiguous),
 //                             trans = 1: X[k + i ldx] (row contiguous along k).
 
-// e_i with max_k |op(X)_ik| < 2^e_i (0 for a zero row).  Integer arithmetic on
-// the FP64 bit patterns (|x| orders like its magnitude bits); no FP64 pipe work.
+// e_i with max_k |op(X)_ik| < 2^(e_i - 1) (0 for a zero row).  Integer
+// arithmetic on the FP64 bit patterns (|x| orders like its magnitude bits); no
+// FP64 pipe work.
 __device__ __forceinline__ int exp_above(unsigned long long mag) {
   if (mag == 0) return 0;
   const int ef = (int)(mag >> 52);
-  return ef ? ef - 1022 : -1022;   // normal: |x| < 2^(ef-1022); subnormal: < 2^-1022
+  return ef ? ef - 1021 : -1021;   // normal: |x| < 2^(ef-1022); subnormal: < 2^-1022
 }
 
 __global__ void row_exp_kernel(const double* __restrict__ X, int64_t ldx, int64_t strideX, int trans,
@@ -88,20 +90,21 @@ __global__ void row_exp_kernel(const double* __restrict__ X, int64_t ldx, int64_
   }
 }
 
-// F = floor(|x| 2^(6S - e)) < 2^(6S) from the bit pattern (|x| < 2^e); the S
-// base-64 digits of F, each times 2^-6s and with the sign of x, are the slices.
+// N = round(x 2^(6S - e)) from the bit pattern (|x| < 2^(e-1), so |N| <= 2^(6S-1));
+// ties round away from zero.
 template <int S>
-__device__ __forceinline__ unsigned long long fixed_point(double x, int e, bool* neg) {
+__device__ __forceinline__ long long fixed_point(double x, int e) {
   const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
-  *neg = (bits >> 63) != 0;
   const unsigned long long mag = bits & 0x7FFFFFFFFFFFFFFFull;
   if (mag == 0) return 0;
   const int ef = (int)(mag >> 52);
   const unsigned long long M = (mag & ((1ull << 52) - 1)) | (ef ? (1ull << 52) : 0ull);
   const int E = ef ? ef - 1075 : -1074;          // |x| = M 2^E
-  const int k = E - e + 6 * S;
-  if (k >= 0) return k < 11 ? M << k : 0;        // |x| < 2^e keeps M 2^k below 2^(6S)
-  return -k < 64 ? M >> (-k) : 0;
+  const int k = E - e + 6 * S;                   // |x| < 2^(e-1) keeps k <= 6S - 54
+  unsigned long long F;
+  if (k >= 0) F = k < 11 ? M << k : 0;
+  else F = -k < 63 ? (M + (1ull << (-k - 1))) >> (-k) : 0;
+  return (bits >> 63) ? -(long long)F : (long long)F;
 }
 
 // S slices of op(X), each rows_pad x K_pad BF16, K contiguous; batch entry b at
@@ -135,30 +138,29 @@ __global__ void slice_kernel(const double* __restrict__ X, int64_t ldx, int64_t 
   for (int r = ty; r < 32; r += 8) {
     const int i = i0 + r, k = k0 + tx;
     if (i >= rows_pad || k >= K_pad) continue;
-    bool neg = false;
-    const unsigned long long F = (i < rows) ? fixed_point<S>(tile[r][tx], eb[i], &neg) : 0ull;
+    long long N = (i < rows) ? fixed_point<S>(tile[r][tx], eb[i]) : 0ll;
     __nv_bfloat16* o = ob + (size_t)i * K_pad + k;
+    // balanced digits from the least significant one up; the leading digit takes
+    // what is left, |d_1| <= 32 because |N| <= 2^(6S-1)
+    int d[S];
+#pragma unroll
+    for (int s = S; s >= 2; --s) {
+      int v = (int)(N & 63);
+      v = v >= 32 ? v - 64 : v;
+      d[s - 1] = v;
+      N = (N - v) >> kBeta;
+    }
+    d[0] = (int)N;
 #pragma unroll
     for (int s = 1; s <= S; ++s) {
-      const int d = (int)((F >> (kBeta * (S - s))) & 63ull);
       // d 2^-6s is exact in FP32 and in BF16 (at most six significant bits)
-      const float v = (float)d * __int_as_float((127 - kBeta * s) << 23);
-      o[(s - 1) * plane] = __float2bfloat16_rn(neg ? -v : v);
+      const float v = (float)d[s - 1] * __int_as_float((127 - kBeta * s) << 23);
+      o[(s - 1) * plane] = __float2bfloat16_rn(v);
     }
   }
 }
 
 // ----------------------------------------------------------------- GEMM
-// (h, l) += x for a float pair h + l: TwoSum(h, x), then renormalise.
-__device__ __forceinline__ void pair_add(float& h, float& l, float x) {
-  const float s1 = h + x;
-  const float bb = s1 - h;
-  const float e = (h - (s1 - bb)) + (x - bb);
-  const float lt = l + e;
-  h = s1 + lt;
-  l = lt - (h - s1);
-}
-
 struct SplitEpi {
   double* C;                // output (column-major), per-batch stride
   int64_t ldc, strideC;
@@ -301,24 +303,23 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     }
     tc::mma_commit(tdone);   // arrives once every MMA issued above has completed
   } else if (warp >= 2) {
-    // ---------------- epilogue: drain chunks into float-pair accumulators
-    // Level 2 is an integer multiple of 2^-12: times 2^12 it is an integer of
-    // magnitude below 512 * 63^2 < 2^21 per chunk, so an int32 sums it exactly
-    // over any K used here.  The lower levels go into a float pair (hr, lr)
-    // whose rounding (2^-48 of values at least 2^-6 below level 2) is
-    // negligible.  FP64 is used only when a batch entry's result is scaled and
-    // written.
+    // ---------------- epilogue: drain chunks into integer accumulators
+    // Level L (2..8) of a chunk is an integer multiple of 2^-6L below 2^24 of
+    // those units, so it is added exactly to an int64 counting units of 2^-48
+    // (per chunk below 2^57.1: exact for K up to about 120000).  The merged
+    // levels >= 9 go into a float, 2^-42 below the leading level.  FP64 is used
+    // only when a batch entry's result is scaled and written.
     constexpr int HALF = BN / (kEpiWarps / 4);     // columns of this warp
     const int q = warp & 3;
     const int half = (warp - 2) >> 2;              // which column slice
     const int row = m0 + q * 32 + lane;            // tile row
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-    int i2[HALF];
-    float hr[HALF], lr[HALF];
+    long long iacc[HALF];
+    float fm[HALF];
 #pragma unroll
     for (int j = 0; j < HALF; ++j) {
-      i2[j] = 0;
-      hr[j] = lr[j] = 0.f;
+      iacc[j] = 0;
+      fm[j] = 0.f;
     }
     bool ok = true;
     const int z = p.reduce ? 0 : blockIdx.z;
@@ -333,12 +334,16 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         for (int g = 0; g < HALF / 8; ++g) {
           float v[8];
           tc::tmem_ld8(tmem + lane_off + a * BN + half * HALF + g * 8, v);
-          if (a == 0) {
+          if (a < kAcc - 1) {
+            const int L = a + 2;
+            // times 2^6L: an exact integer below 2^24
+            const float up = __int_as_float((127 + kBeta * L) << 23);
 #pragma unroll
-            for (int i = 0; i < 8; ++i) i2[g * 8 + i] += __float2int_rn(v[i] * 4096.0f);
+            for (int i = 0; i < 8; ++i)
+              iacc[g * 8 + i] += (long long)__float2int_rn(v[i] * up) << (48 - kBeta * L);
           } else {
 #pragma unroll
-            for (int i = 0; i < 8; ++i) pair_add(hr[g * 8 + i], lr[g * 8 + i], v[i]);
+            for (int i = 0; i < 8; ++i) fm[g * 8 + i] += v[i];
           }
         }
       }
@@ -358,7 +363,7 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
           const int col = n0 + half * HALF + j;
           const int ci = p.swap ? col : row, cj = p.swap ? row : col;
           if (row < (p.swap ? p.N : p.M) && col < (p.swap ? p.M : p.N)) {
-            const double t = (double)i2[j] * (1.0 / 4096.0) + ((double)hr[j] + (double)lr[j]);
+            const double t = (double)iacc[j] * 0x1p-48 + (double)fm[j];
             double v = al * ldexp(t, ei + __ldg(ebb + j));
             if (first) {
               if (Cin && p.beta != 0.0) v = fma(p.beta, Cin[ci + (int64_t)cj * p.ldcin], v);
@@ -367,8 +372,8 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
             }
             C[ci + (int64_t)cj * p.ldc] = v;
           }
-          i2[j] = 0;
-          hr[j] = lr[j] = 0.f;
+          iacc[j] = 0;
+          fm[j] = 0.f;
         }
       }
     }
