@@ -48,6 +48,10 @@ WORKLOADS = {
                          desc="Zolo-PD of one 16384x4096 matrix, sigma uniform in [1e-6, 1], r=6"),
     "pd1024": dict(kind="pd", m=1024, n=1024, kappa=1e8, r=6, sample_n=256,
                    desc="Zolo-PD of one 1024x1024 matrix, kappa 1e8, r=6"),
+    "batch512": dict(kind="batch", count=512, m=1024, n=1024, kappa=1e12, r=0,
+                     desc="Zolo-PD of a batch of 512 square matrices, n uniform in {64,...,1024}, "
+                          "sigma geometric over kappa log-uniform in [1e2, 1e12], r chosen per "
+                          "matrix, one zolo_pd_batched call (graph-captured, replayed)"),
 }
 
 
@@ -171,9 +175,37 @@ def blas_threads():
     return os.cpu_count()
 
 
+def batch_oracle_sample(w, budget_s=12.0):
+    """Time the CPU oracle on the leading matrices of the batch until about
+    budget_s seconds have passed; scaled to the whole batch by the flop model."""
+    from oracle import zolo_oracle as zo
+    from paper_1806_06204_gb300 import synth
+    ns, kap = synth.batch_sizes_and_kappas(w["count"])
+    done_f, tot_f, dt, k = 0.0, 0.0, 0.0, 0
+    for i, (n, kp) in enumerate(zip(ns, kap)):
+        r = zo.choose_r(1.0 / kp)
+        it = zo.ell_schedule(1.0 / kp, r)
+        used_qr = [zo.uses_qr(zo.zolotarev_coeffs(l, r), l) for l in it[:-1]]
+        tot_f += pd_model_flops(n, n, r, used_qr)
+        if dt < budget_s and n <= 256:
+            sm = synth.make_matrix(n, n, synth.geometric_sigma(n, kp), 4000 + 1 + i)
+            t0 = time.perf_counter()
+            zo.zolo_pd(sm.A, 1.0, float(sm.sigma[-1]), r=r)
+            dt += time.perf_counter() - t0
+            done_f += pd_model_flops(n, n, r, used_qr)
+            k += 1
+    scale = tot_f / done_f
+    desc = (f"oracle zolo_pd on the {k} matrices of the batch with n <= 256 met first "
+            f"({dt:.1f} s), scaled by the Zolo-PD flop model x{scale:.1f} to all {w['count']}")
+    return w["count"] / (dt * scale), dt, desc
+
+
 def run_reference(args, w, rank):
     if rank != 0:
         return
+    if w["kind"] == "batch":
+        global oracle_sample
+        oracle_sample = lambda w, seed=None: batch_oracle_sample(w)
     for _ in range(args.warmup):
         oracle_sample(w)
     vals, tot = [], 0.0
@@ -193,6 +225,171 @@ def run_reference(args, w, rank):
             "e2e": {"value": value, "unit": "matrices/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def roofline(kstats, timed_ms):
+    """Roofline entry of the dominant kernel class (by device time)."""
+    dom_name, dom = max(((k, v) for k, v in kstats.items() if v["launches"] > 0),
+                        key=lambda kv: kv[1]["ms"])
+    achieved = dom["flops"] / (dom["ms"] / 1000.0) / 1e12
+    bound = {"combine": "hbm", "slice": "hbm", "gemm_split": "tensor"}.get(dom_name, "alu")
+    if bound == "tensor":
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        peak = peaks["bf16_tflops_sustained"]
+        # tensor flops actually issued: one BF16 product per kept slice pair
+        # (s + t <= 10 of nine slices: 45 of them)
+        issued = dom["flops"] * 45 / (dom["ms"] / 1000.0) / 1e12
+        roof = {"bound": "tensor", "kernel": dom_name, "achieved": issued, "peak": peak,
+                "unit": "TFLOP/s", "frac": issued / peak, "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained",
+                "fp64_equivalent_tflops": achieved}
+    elif bound == "alu":
+        roof = {"bound": "alu", "kernel": dom_name, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "derived: 152 SMs x 4 FP64 flops/clk x 2.07 GHz"}
+    else:
+        peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+        gbs = dom["bytes"] / (dom["ms"] / 1000.0) / 1e9
+        roof = {"bound": "hbm", "kernel": dom_name, "achieved": gbs, "peak": peak, "unit": "GB/s",
+                "frac": gbs / peak, "traffic": None}
+    roof["launches"] = dom["launches"]
+    roof["avg_launch_ms"] = dom["ms"] / dom["launches"]
+    roof["share_of_step"] = dom["ms"] / timed_ms
+    return roof
+
+
+def run_batch(args, w, rank, world, dist, local):
+    """The uneven batch through zolo_pd_batched: value = matrices/s over all ranks."""
+    import numpy as np
+    import torch
+    from paper_1806_06204_gb300 import binding as zb, synth
+    split = args.prec == "split"
+    mats = synth.batch(w["count"], seed=4000 + 100000 * rank)
+    As = [torch.from_numpy(sm.A).cuda() for sm in mats]
+    os_ = [zb.opts(beta=float(sm.sigma[-1]), alpha=1.0, r=0,
+                   prec=zb.ZOLO_SPLIT_BF16 if split else zb.ZOLO_FP64, ns_steps=1 if split else 0)
+           for sm in mats]
+    Qps = [zb.empty_colmajor(a.shape[0], a.shape[1]) for a in As]
+    Hs = [zb.empty_colmajor(a.shape[1], a.shape[1]) for a in As]
+    h = zb.Handle(local)
+
+    def step():
+        _, _, infos, st = zb.zolo_pd_batched(h, As, os_, Qps=Qps, Hs=Hs)
+        return infos
+
+    for _ in range(args.warmup):
+        infos = step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    launches0 = zb.kernel_launches()
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            infos = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    launches = zb.kernel_launches() - launches0
+    ms_step = e0.elapsed_time(e1) / args.steps
+    if dist:
+        t = torch.tensor([ms_step], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = world * w["count"] / (ms_step / 1000.0)
+    flops = sum(pd_model_flops(a.shape[0], a.shape[1], i.r, i.used_qr) for a, i in zip(As, infos))
+
+    # per-kernel device times: one more step with event-bracketed launches (a
+    # replayed graph cannot be bracketed kernel by kernel)
+    zb.profile(True)
+    e2 = torch.cuda.Event(enable_timing=True)
+    e3 = torch.cuda.Event(enable_timing=True)
+    e2.record(stream)
+    step()
+    e3.record(stream)
+    torch.cuda.synchronize()
+    kstats = zb.profile_read()
+    zb.profile(False)
+    roof = roofline(kstats, e2.elapsed_time(e3))
+    roof["measured"] = "one extra step with per-launch CUDA events (no graph)"
+
+    # accuracy of every result, checked on the device with torch
+    bwd, orth = 0.0, 0.0
+    for a, q, hh in zip(As, Qps, Hs):
+        n = a.shape[1]
+        bwd = max(bwd, float(torch.linalg.norm(a - q @ hh) / torch.linalg.norm(a)))
+        I = torch.eye(n, dtype=torch.float64, device="cuda")
+        orth = max(orth, float(torch.linalg.norm(q.T @ q - I) / math.sqrt(n)))
+    acc = {"max_bwd_err": bwd, "max_orth_Qp": orth,
+           "statuses_nonzero": sum(1 for i in infos if i.status)}
+
+    e2e = None
+    if not args.no_e2e:
+        # host (pinned) inputs copied in and both factors copied back inside the timed region
+        Ah = [torch.from_numpy(sm.A.T.copy()).pin_memory().t() for sm in mats]
+        Qh = [torch.empty((a.shape[1], a.shape[0]), dtype=torch.float64).pin_memory().t() for a in As]
+        Hh = [torch.empty((a.shape[1], a.shape[1]), dtype=torch.float64).pin_memory().t() for a in As]
+        Ad = [zb.empty_colmajor(a.shape[0], a.shape[1]) for a in As]
+
+        def host_step():
+            for d, src in zip(Ad, Ah):
+                d.copy_(src, non_blocking=True)
+            zb.zolo_pd_batched(h, Ad, os_, Qps=Qps, Hs=Hs)
+            for dst, q in zip(Qh, Qps):
+                dst.copy_(q, non_blocking=True)
+            for dst, hh in zip(Hh, Hs):
+                dst.copy_(hh, non_blocking=True)
+            torch.cuda.synchronize()
+
+        host_step()
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            host_step()
+        barrier()
+        e2e_s = (time.perf_counter() - t0) / args.steps
+        if dist:
+            t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        nb = sum(a.numel() for a in As) * 8
+        e2e = {"value": world * w["count"] / e2e_s, "unit": "matrices/s", "h2d_bytes_per_step": nb,
+               "d2h_bytes_per_step": nb + sum(x.numel() for x in Hs) * 8}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, dt, desc = batch_oracle_sample(w)
+        cpu = {"value": v, "unit": "matrices/s", "cores": blas_threads(), "kind": "oracle",
+               "sample": desc}
+    if rank == 0:
+        ns = [a.shape[1] for a in As]
+        line = {"metric": METRIC, "value": value, "unit": "matrices/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if not split else "bf16x9-slices->f64",
+                "data": "synthetic",
+                "config": {"workload": args.workload, "desc": w["desc"], "count": w["count"],
+                           "n_min": min(ns), "n_max": max(ns), "prec": args.prec,
+                           "r_hist": {str(r): sum(1 for i in infos if i.r == r)
+                                      for r in sorted({i.r for i in infos})},
+                           "l2": "inputs larger than L2 (1.6 GB of A per step; no flush)",
+                           "parallelism": "replicas" if world > 1 else "single"},
+                "eff_tflops": world * flops / (ms_step / 1000.0) / 1e12,
+                "pd_model_flops": flops, "accuracy": acc, "roofline": roof,
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "kernel_ms": {k: round(v["ms"], 3) for k, v in kstats.items() if v["launches"]},
+                "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    h.close()
 
 
 def main():
@@ -234,6 +431,11 @@ def main():
     from paper_1806_06204_gb300 import binding as zb
 
     torch.cuda.set_device(local)
+    if w["kind"] == "batch":
+        run_batch(args, w, rank, world, dist, local)
+        if dist:
+            dist.destroy_process_group()
+        return
     sm = make_input(w, seed=2000 + rank)
     A = torch.from_numpy(sm.A).cuda()
     h = zb.Handle(local)
@@ -284,31 +486,7 @@ def main():
     acc = accuracy(w, sm, outs)
 
     # roofline of the dominant kernel class (by device time inside the timed region)
-    dom_name, dom = max(((k, v) for k, v in kstats.items() if v["launches"] > 0),
-                        key=lambda kv: kv[1]["ms"])
-    achieved = dom["flops"] / (dom["ms"] / 1000.0) / 1e12
-    bound = {"combine": "hbm", "slice": "hbm", "gemm_split": "tensor"}.get(dom_name, "alu")
-    if bound == "tensor":
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-        peak = peaks["bf16_tflops_sustained"]
-        # tensor flops actually issued: one BF16 product per slice pair (S(S+1)/2 of them)
-        issued = dom["flops"] * 36 / (dom["ms"] / 1000.0) / 1e12
-        roof = {"bound": "tensor", "kernel": dom_name, "achieved": issued, "peak": peak,
-                "unit": "TFLOP/s", "frac": issued / peak, "traffic": None,
-                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained",
-                "fp64_equivalent_tflops": dom["flops"] / (dom["ms"] / 1000.0) / 1e12}
-    elif bound == "alu":
-        roof = {"bound": "alu", "kernel": dom_name, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "derived: 152 SMs x 4 FP64 flops/clk x 2.07 GHz"}
-    else:
-        peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
-        gbs = dom["bytes"] / (dom["ms"] / 1000.0) / 1e9
-        roof = {"bound": "hbm", "kernel": dom_name, "achieved": gbs, "peak": peak, "unit": "GB/s",
-                "frac": gbs / peak, "traffic": None}
-    roof["launches"] = dom["launches"]
-    roof["avg_launch_ms"] = dom["ms"] / dom["launches"]
-    roof["share_of_step"] = dom["ms"] / (ms_step * args.steps)
+    roof = roofline(kstats, ms_step * args.steps)
 
     # end to end through the host-buffer entry point
     e2e = None

@@ -121,13 +121,18 @@ size_t layout(void* base, int64_t m, int64_t n, int r, bool svd, PdBufs* b) {
     const int64_t npan = (n + kQrNB - 1) / kQrNB;
     t.qr.strideW = (m + n) * n;
     t.qr.W = q.take<double>(r * t.qr.strideW);
-    t.qr.strideV = (m + kQrNB) * n;
+    const int64_t nblk = (n + kQrBlock - 1) / kQrBlock;
+    t.qr.strideV = (m + kQrBlock) * n;
     t.qr.V = q.take<double>(r * t.qr.strideV);
     t.qr.strideT = npan * kQrNB * kQrNB;
     t.qr.T = q.take<double>(r * t.qr.strideT);
-    t.qr.strideW1 = kQrNB * n;
+    t.qr.strideTb = nblk * kQrBlock * kQrBlock;
+    t.qr.Tb = q.take<double>(r * t.qr.strideTb);
+    t.qr.strideG = kQrBlock * kQrBlock;
+    t.qr.G = q.take<double>(r * t.qr.strideG);
+    t.qr.strideW1 = kQrBlock * n;
     t.qr.W1 = q.take<double>(r * t.qr.strideW1);
-    t.qr.strideW2 = kQrNB * n;
+    t.qr.strideW2 = kQrBlock * n;
     t.qr.W2 = q.take<double>(r * t.qr.strideW2);
     c.off = std::max(c.off, q.off);
   }
@@ -983,6 +988,7 @@ int zolo_pd_batched(zolo_handle_t h, int count, const double* const* A, const in
   // with per-kernel profiling on, the work is queued directly (events cannot
   // bracket the nodes of a graph)
   const bool use_graph = !profiling_enabled();
+  if (!use_graph) exec = nullptr;
   uint64_t graph_launches = 0;
   for (BatchGraph& g : h->graphs)
     if (g.exec == exec) graph_launches = g.launches;

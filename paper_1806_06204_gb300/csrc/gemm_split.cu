@@ -20,6 +20,7 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -55,38 +56,101 @@ __device__ __forceinline__ int exp_above(unsigned long long mag) {
   return ef ? ef - 1021 : -1021;   // normal: |x| < 2^(ef-1022); subnormal: < 2^-1022
 }
 
+// With ek != nullptr, element (i, k) counts as x 2^(esign ek[k]) (the inner-index
+// equilibration): e_i bounds the shifted row.
 __global__ void row_exp_kernel(const double* __restrict__ X, int64_t ldx, int64_t strideX, int trans,
-                               int rows, int K, int* __restrict__ e_out, int rows_pad) {
-  __shared__ unsigned long long red[8][33];
+                               int rows, int K, int* __restrict__ e_out, int rows_pad,
+                               const int* __restrict__ ek, int esign, int K_pad) {
+  __shared__ long long red[8][33];
   const double* Xb = X + blockIdx.z * strideX;
+  const int* ekb = ek ? ek + blockIdx.z * K_pad : nullptr;
   const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
   const unsigned long long kMag = 0x7FFFFFFFFFFFFFFFull;
-  unsigned long long mx = 0;
+  // without shifts: the largest magnitude pattern; with shifts: the largest
+  // shifted exponent bound (both reduce with max)
+  long long mx = ek ? LLONG_MIN : 0;
+  auto take = [&](double x, int k) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x) & kMag;
+    if (!ekb) {
+      mx = (long long)b > mx ? (long long)b : mx;
+    } else if (b != 0) {
+      const long long e = exp_above(b) + esign * ekb[k];
+      mx = e > mx ? e : mx;
+    }
+  };
+  auto finish = [&](long long v) -> int {
+    if (!ekb) return exp_above((unsigned long long)v);
+    return v == LLONG_MIN ? 0 : (int)v;
+  };
   if (!trans) {   // 32 rows per block along tx, k split over ty
     const int i = blockIdx.x * 32 + tx;
     if (i < rows)
-      for (int k = ty; k < K; k += 8) {
-        const unsigned long long b = (unsigned long long)__double_as_longlong(Xb[i + (int64_t)k * ldx]) & kMag;
-        mx = b > mx ? b : mx;
-      }
+      for (int k = ty; k < K; k += 8) take(Xb[i + (int64_t)k * ldx], k);
     red[ty][tx] = mx;
     __syncthreads();
     if (ty == 0) {
       for (int y = 1; y < 8; ++y) mx = red[y][tx] > mx ? red[y][tx] : mx;
-      if (i < rows_pad) e_out[blockIdx.z * rows_pad + i] = exp_above(mx);
+      if (i < rows_pad) e_out[blockIdx.z * rows_pad + i] = finish(mx);
     }
   } else {        // 8 rows per block, one warp per row, lanes along k
     const int i = blockIdx.x * 8 + ty;
     if (i < rows)
-      for (int k = tx; k < K; k += 32) {
+      for (int k = tx; k < K; k += 32) take(Xb[k + (int64_t)i * ldx], k);
+    for (int o = 16; o > 0; o >>= 1) {
+      const long long t = __shfl_xor_sync(0xffffffffu, mx, o);
+      mx = t > mx ? t : mx;
+    }
+    if (tx == 0 && i < rows_pad) e_out[blockIdx.z * rows_pad + i] = finish(mx);
+  }
+}
+
+// ek[k] = the exponent bound of column k of the (rows x K) view of op(X)
+// (0 for a zero column or k >= K): scaling that column by 2^-ek[k] puts its
+// largest magnitude in [1/4, 1/2).
+__global__ void col_exp_kernel(const double* __restrict__ X, int64_t ldx, int64_t strideX, int trans,
+                               int rows, int K, int* __restrict__ ek, int K_pad) {
+  __shared__ unsigned long long red[8][33];
+  const double* Xb = X + blockIdx.z * strideX;
+  const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+  const unsigned long long kMag = 0x7FFFFFFFFFFFFFFFull;
+  const int k0 = blockIdx.x * 32;
+  if (trans) {    // element (i, k) = X[k + i ldx]: threads along k, rows split over ty
+    unsigned long long mx = 0;
+    const int k = k0 + tx;
+    if (k < K)
+      for (int i = ty; i < rows; i += 8) {
         const unsigned long long b = (unsigned long long)__double_as_longlong(Xb[k + (int64_t)i * ldx]) & kMag;
         mx = b > mx ? b : mx;
       }
-    for (int o = 16; o > 0; o >>= 1) {
-      const unsigned long long t = __shfl_xor_sync(0xffffffffu, mx, o);
-      mx = t > mx ? t : mx;
+    red[ty][tx] = mx;
+  } else {        // element (i, k) = X[i + k ldx]: one warp per column, lanes along i
+    for (int kk = ty; kk < 32; kk += 8) {
+      unsigned long long mx = 0;
+      const int k = k0 + kk;
+      if (k < K)
+        for (int i = tx; i < rows; i += 32) {
+          const unsigned long long b = (unsigned long long)__double_as_longlong(Xb[i + (int64_t)k * ldx]) & kMag;
+          mx = b > mx ? b : mx;
+        }
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long t = __shfl_xor_sync(0xffffffffu, mx, o);
+        mx = t > mx ? t : mx;
+      }
+      if (tx == 0) red[0][kk] = mx;   // row 0 collects the columns
     }
-    if (tx == 0 && i < rows_pad) e_out[blockIdx.z * rows_pad + i] = exp_above(mx);
+    __syncthreads();
+    if (ty == 0) {
+      const int k = k0 + tx;
+      if (k < K_pad) ek[blockIdx.z * K_pad + k] = (k < K) ? exp_above(red[0][tx]) : 0;
+    }
+    return;
+  }
+  __syncthreads();
+  if (ty == 0) {
+    unsigned long long mx = red[0][tx];
+    for (int y = 1; y < 8; ++y) mx = red[y][tx] > mx ? red[y][tx] : mx;
+    const int k = k0 + tx;
+    if (k < K_pad) ek[blockIdx.z * K_pad + k] = (k < K) ? exp_above(mx) : 0;
   }
 }
 
@@ -114,7 +178,8 @@ __device__ __forceinline__ long long fixed_point(double x, int e) {
 template <int S>
 __global__ void slice_kernel(const double* __restrict__ X, int64_t ldx, int64_t strideX, int trans,
                              int rows, int K, const int* __restrict__ e_in,
-                             __nv_bfloat16* __restrict__ out, int rows_pad, int K_pad) {
+                             __nv_bfloat16* __restrict__ out, int rows_pad, int K_pad,
+                             const int* __restrict__ ek, int esign) {
   __shared__ double tile[32][33];
   const double* Xb = X + blockIdx.z * strideX;
   const int* eb = e_in + blockIdx.z * rows_pad;
@@ -138,7 +203,9 @@ __global__ void slice_kernel(const double* __restrict__ X, int64_t ldx, int64_t 
   for (int r = ty; r < 32; r += 8) {
     const int i = i0 + r, k = k0 + tx;
     if (i >= rows_pad || k >= K_pad) continue;
-    long long N = (i < rows) ? fixed_point<S>(tile[r][tx], eb[i]) : 0ll;
+    // element x 2^(esign ek[k]) against the row bound 2^(e_i - 1)
+    const int ee = ek ? eb[i] - esign * ek[blockIdx.z * K_pad + k] : eb[i];
+    long long N = (i < rows) ? fixed_point<S>(tile[r][tx], ee) : 0ll;
     __nv_bfloat16* o = ob + (size_t)i * K_pad + k;
     // balanced digits from the least significant one up; the leading digit takes
     // what is left, |d_1| <= 32 because |N| <= 2^(6S-1)
@@ -426,20 +493,20 @@ int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 template <int S>
 cudaError_t slice_operand(const double* X, int64_t ldx, int64_t strideX, int trans, int rows, int K,
                           int batch, int* e, __nv_bfloat16* out, int rows_pad, int K_pad,
-                          cudaStream_t st) {
+                          const int* ek, int esign, cudaStream_t st) {
   {
     ProfScope ps(kProfSlice, st, 0.0, 8.0 * batch * rows * (double)K);
     if (!trans)
       row_exp_kernel<<<dim3((rows_pad + 31) / 32, 1, batch), dim3(32, 8), 0, st>>>(
-          X, ldx, strideX, 0, rows, K, e, rows_pad);
+          X, ldx, strideX, 0, rows, K, e, rows_pad, ek, esign, K_pad);
     else
       row_exp_kernel<<<dim3((rows_pad + 7) / 8, 1, batch), dim3(32, 8), 0, st>>>(
-          X, ldx, strideX, 1, rows, K, e, rows_pad);
+          X, ldx, strideX, 1, rows, K, e, rows_pad, ek, esign, K_pad);
   }
   ProfScope ps(kProfSlice, st, 0.0, (8.0 + 2.0 * S) * batch * rows_pad * (double)K_pad);
   dim3 grid((unsigned)(K_pad / 32), (unsigned)(rows_pad / 32), batch);
   slice_kernel<S><<<grid, dim3(32, 8), 0, st>>>(X, ldx, strideX, trans, rows, K, e, out, rows_pad,
-                                                K_pad);
+                                                K_pad, ek, esign);
   return cudaGetLastError();
 }
 
@@ -451,12 +518,15 @@ cudaError_t run_split(const GemmArgs& g, SplitWork& w, cudaStream_t st) {
   const int Mpad = (int)round_up(M, kTileM), Npad = (int)round_up(N, BN), Kpad = (int)round_up(K, kBK);
   const int nb = g.batch;
   const size_t need_a = (size_t)nb * S * Mpad * Kpad, need_b = (size_t)nb * S * Npad * Kpad;
-  if (need_a + need_b > w.slice_elems || (size_t)nb * (Mpad + Npad) > w.exp_elems)
+  const bool keq = g.k_equilibrate != 0;
+  if (need_a + need_b > w.slice_elems ||
+      (size_t)nb * (Mpad + Npad + (keq ? Kpad : 0)) > w.exp_elems)
     return cudaErrorMemoryAllocation;
   __nv_bfloat16* sa = static_cast<__nv_bfloat16*>(w.slices);
   __nv_bfloat16* sb = sa + need_a;
   int* ea = w.exps;
   int* eb = w.exps + (size_t)nb * Mpad;
+  int* ek = keq ? eb + (size_t)nb * Npad : nullptr;
   cudaError_t err;
   // op(A) rows: M x K.  With swap the tile's A side is op(B)^T (rows = columns of op(B)).
   //   op(A) row i, col k:   transA = 0: A[i + k lda]   transA = 1: A[k + i lda]
@@ -467,9 +537,22 @@ cudaError_t run_split(const GemmArgs& g, SplitWork& w, cudaStream_t st) {
   const int64_t sta = swap ? g.strideB : g.strideA, stb = swap ? g.strideA : g.strideB;
   const int ta = swap ? (g.transB ? 0 : 1) : g.transA;
   const int tb = swap ? g.transA : (g.transB ? 0 : 1);
-  if ((err = slice_operand<S>(Xa, lda, sta, ta, M, K, nb, ea, sa, Mpad, Kpad, st)) != cudaSuccess)
+  // inner-index equilibration: op(B)'s rows k are the columns of the (rows x K)
+  // view of the tile's B side (A side when swapped); they are scaled by 2^-ek[k]
+  // and op(A)'s columns by 2^+ek[k]
+  const int sign_a = swap ? -1 : 1;
+  if (keq) {
+    ProfScope ps(kProfSlice, st, 0.0, 8.0 * nb * (double)N * K);
+    const double* Xo = swap ? Xa : Xb;
+    col_exp_kernel<<<dim3((unsigned)(Kpad / 32), 1, nb), dim3(32, 8), 0, st>>>(
+        Xo, swap ? lda : ldb, swap ? sta : stb, swap ? ta : tb, swap ? M : N, K, ek, Kpad);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  }
+  if ((err = slice_operand<S>(Xa, lda, sta, ta, M, K, nb, ea, sa, Mpad, Kpad, ek, sign_a, st)) !=
+      cudaSuccess)
     return err;
-  if ((err = slice_operand<S>(Xb, ldb, stb, tb, N, K, nb, eb, sb, Npad, Kpad, st)) != cudaSuccess)
+  if ((err = slice_operand<S>(Xb, ldb, stb, tb, N, K, nb, eb, sb, Npad, Kpad, ek, -sign_a, st)) !=
+      cudaSuccess)
     return err;
   CUtensorMap mA, mB;
   if (!make_map(&mA, sa, (int64_t)nb * S * Mpad, Kpad, kTileM) ||
@@ -520,7 +603,8 @@ cudaError_t gemm_split(const GemmArgs& g, SplitWork& w, cudaStream_t st) {
   if (g.K <= 0 || g.batch > kGemmMaxBatch) return gemm_f64(g, st);
   // batch entries per launch that the slice workspace holds
   const size_t per = split_slice_elems(g.M, g.N, g.K, 1, w.slices_s);
-  const int64_t rows = std::max<int64_t>(round_up(std::max(g.M, g.N), kTileM), 64) * 2;
+  const int64_t rows = std::max<int64_t>(round_up(std::max(g.M, g.N), kTileM), 64) * 2 +
+                       (g.k_equilibrate ? round_up(g.K, kBK) : 0);
   int gs = (int)std::min<size_t>(g.batch, w.slice_elems / std::max<size_t>(per, 1));
   gs = (int)std::min<int64_t>(gs, (int64_t)(w.exp_elems / rows));
   if (gs < 1) return cudaErrorMemoryAllocation;

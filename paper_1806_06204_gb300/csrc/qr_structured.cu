@@ -6,9 +6,18 @@
 // block starts diagonal; Householder vector c (column c) is non-zero only on
 // top rows c..m-1 and bottom rows 0..c, i.e. on the CONTIGUOUS stored rows
 // c..m+c: m+1 entries instead of m+n-c (the paper's "at most m+1 nonzero
-// elements").  A panel of NB columns starting at c0 therefore works on the row
-// window [c0, c0 + m + NB), and the compact-WY trailing update (I - V T V^T)
-// touches only that window: every step costs O((m + NB) NB n) whatever n is.
+// elements").  A set of columns [c0, c0 + w) therefore lives in the row window
+// [c0, c0 + m + w), and its compact-WY update (I - V T V^T) touches only that
+// window: every step costs O((m + w) w n) whatever n is.
+//
+// Two levels of blocking.  Panels of NB = 32 columns are factored by one kernel
+// (one CTA, or one 8-CTA cluster, per shift) and applied at once only to the
+// rest of their block of NBb = 128 columns.  The block's reflectors are then
+// merged into one compact-WY factor T_b (from the Gram matrix V_b^T V_b, below)
+// and applied to all later columns with three GEMMs whose inner dimension is the
+// block width: the wide products see the trailing matrix once per 128 columns,
+// not once per 32, and no GEMM dimension is padded up from 32.  The explicit Q
+// applies the same block reflectors in reverse order.
 //
 // Q2 (the bottom block of Q) stays exactly upper triangular: the explicit V
 // holds exact zeros outside each reflector's support, so every product that the
@@ -299,92 +308,170 @@ qr_panel_cluster_kernel(double* W, int64_t strideW, int64_t ldw, int64_t m, int6
   cluster.sync();   // no CTA leaves while another may still read its partials
 }
 
+// T_b of one block: its panel factors on the 32 x 32 diagonal blocks, zero
+// elsewhere (ld NBb).  Grid (ceil(nbb^2 / 256), r).
+__global__ void tb_init_kernel(const double* __restrict__ T, int64_t strideT, double* __restrict__ Tb,
+                               int64_t strideTb, int panel0, int nbb) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nbb * nbb) return;
+  const int i = e % nbb, j = e / nbb;
+  double v = 0.0;
+  if (i / kQrNB == j / kQrNB)
+    v = T[blockIdx.y * strideT + (int64_t)(panel0 + i / kQrNB) * kQrNB * kQrNB + (i % kQrNB) +
+          (j % kQrNB) * kQrNB];
+  Tb[blockIdx.y * strideTb + i + (int64_t)j * kQrBlock] = v;
+}
+
+// One merge level of the block factor: for each pair of neighbouring diagonal
+// blocks [a, a+h) and [a+h, a+h+w) of T_b (already merged up to width h),
+//     T_b[a:a+h, a+h:a+h+w] = -T_11 (V_1^T V_2) T_22,
+// which makes (I - V_1 T_11 V_1^T)(I - V_2 T_22 V_2^T) = I - V T V^T.  One CTA
+// per column j of the right block, per pair and per shift; thread i owns row i.
+__global__ void __launch_bounds__(kQrBlock / 2)
+tb_merge_kernel(const double* __restrict__ G, int64_t strideG, double* __restrict__ Tb,
+                int64_t strideTb, int nbb, int h) {
+  __shared__ double x[kQrBlock / 2];
+  const int j = blockIdx.x, i = threadIdx.x;
+  const int a = blockIdx.y * 2 * h, b0 = a + h;
+  const int w = nbb - b0 < h ? nbb - b0 : h;
+  if (w <= 0 || j >= w) return;
+  const double* Gs = G + blockIdx.z * strideG;
+  double* T = Tb + blockIdx.z * strideTb;
+  constexpr int ld = kQrBlock;
+  if (i < h) {
+    double t = 0.0;
+    for (int k = 0; k <= j; ++k) t = fma(Gs[(a + i) + (int64_t)(b0 + k) * ld], T[(b0 + k) + (int64_t)(b0 + j) * ld], t);
+    x[i] = t;
+  }
+  __syncthreads();
+  if (i < h) {
+    double t = 0.0;
+    for (int k = i; k < h; ++k) t = fma(T[(a + i) + (int64_t)(a + k) * ld], x[k], t);
+    T[(a + i) + (int64_t)(b0 + j) * ld] = -t;
+  }
+}
+
+// C <- (I - V op(T) V^T) C for r shifts, on the row window of C, as
+// W1 = V^T C, W2 = op(T) W1, C -= V W2 (transT = 1 applies Q^T, the
+// factorisation's update; transT = 0 applies Q, the explicit-Q build).
+cudaError_t apply_block(const QrBuffers& b, const double* Vw, int64_t ldv, const double* Tw,
+                        int ldt, int64_t strideT, double* C, int64_t ldw, int64_t rows, int w,
+                        int64_t ncols, int r, int transT, cudaStream_t st) {
+  cudaError_t err;
+  GemmArgs g;
+  g.M = w; g.N = (int)ncols; g.K = (int)rows; g.transA = 1; g.transB = 0;
+  g.A = Vw; g.lda = ldv; g.strideA = b.strideV;
+  g.B = C; g.ldb = ldw; g.strideB = b.strideW;
+  g.Cout = b.W1; g.ldcout = kQrBlock; g.strideCout = b.strideW1;
+  g.batch = r;
+  for (int j = 0; j < r; ++j) g.alpha[j] = 1.0;
+  if ((err = gemm_any(g, st)) != cudaSuccess) return err;
+  GemmArgs h = g;
+  h.K = w; h.transA = transT;
+  h.A = Tw; h.lda = ldt; h.strideA = strideT;
+  h.B = b.W1; h.ldb = kQrBlock; h.strideB = b.strideW1;
+  h.Cout = b.W2; h.strideCout = b.strideW2;
+  if ((err = gemm_any(h, st)) != cudaSuccess) return err;
+  GemmArgs u = g;
+  u.M = (int)rows; u.N = (int)ncols; u.K = w; u.transA = 0; u.transB = 0;
+  u.A = Vw; u.lda = ldv; u.strideA = b.strideV;
+  u.B = b.W2; u.ldb = kQrBlock; u.strideB = b.strideW2;
+  u.Cin = C; u.ldcin = ldw; u.strideCin = b.strideW; u.beta = 1.0;
+  u.Cout = C; u.ldcout = ldw; u.strideCout = b.strideW;
+  for (int j = 0; j < r; ++j) u.alpha[j] = -1.0;
+  // the rows of W2 follow the trailing matrix, whose size decays across the
+  // block's reflectors like the singular values: equilibrate them
+  u.k_equilibrate = 1;
+  return gemm_any(u, st);
+}
+
 }  // namespace
 
 cudaError_t structured_qr_q(const QrBuffers& b, int64_t m, int64_t n, int r, int* status,
                             cudaStream_t st) {
-  constexpr int NB = kQrNB;
+  constexpr int NB = kQrNB, NBb = kQrBlock;
   const int64_t ldw = m + n;
-  const int64_t ldv = m + NB;
+  const int64_t ldv = m + NBb;
   cudaError_t err;
-  const int npanels = (int)((n + NB - 1) / NB);
+  const int nblocks = (int)((n + NBb - 1) / NBb);
+  // every V entry outside the rows a panel writes must be an exact zero
+  if ((err = cudaMemsetAsync(b.V, 0, sizeof(double) * r * b.strideV, st)) != cudaSuccess) return err;
   // ---------------- factorisation (structured GEQRF)
-  for (int p = 0; p < npanels; ++p) {
-    const int64_t c0 = (int64_t)p * NB;
-    const int nbp = (int)(n - c0 < NB ? n - c0 : NB);
+  for (int blk = 0; blk < nblocks; ++blk) {
+    const int64_t c0b = (int64_t)blk * NBb;
+    const int nbb = (int)(n - c0b < NBb ? n - c0b : NBb);
+    for (int p = 0; p * NB < nbb; ++p) {
+      const int64_t c0 = c0b + (int64_t)p * NB;
+      const int nbp = nbb - p * NB < NB ? nbb - p * NB : NB;
+      // V rows are relative to the block start: this panel's window starts p*NB down
+      double* Vpan = b.V + (int64_t)p * NB;
+      {
+        ProfScope ps(kProfPanel, st, 3.0 * r * (double)(m + 1) * nbp * nbp,
+                     8.0 * r * (double)(m + NB) * nbp * 2.0);
+        if (m >= kClusterPanelMinRows)
+          qr_panel_cluster_kernel<NB, kPanelCluster><<<r * kPanelCluster, 256, 0, st>>>(
+              b.W, b.strideW, ldw, m, c0, nbp, Vpan, b.strideV, ldv, b.T, b.strideT, status);
+        else
+          qr_panel_kernel<NB><<<r, kPanelThreads, 0, st>>>(b.W, b.strideW, ldw, m, c0, nbp, Vpan,
+                                                            b.strideV, ldv, b.T, b.strideT, status);
+      }
+      if ((err = cudaGetLastError()) != cudaSuccess) return err;
+      // the rest of this block's columns
+      const int64_t nin = c0b + nbb - (c0 + nbp);
+      if (nin > 0) {
+        const double* Vp = Vpan + c0 * ldv;
+        const double* Tp = b.T + (c0 / NB) * (int64_t)(NB * NB);
+        if ((err = apply_block(b, Vp, ldv, Tp, NB, b.strideT, b.W + c0 + (c0 + nbp) * ldw, ldw,
+                               m + nbp, nbp, nin, r, 1, st)) != cudaSuccess)
+          return err;
+      }
+    }
+    // ---- the block factor T_b: panel factors on the diagonal, merged pairwise
+    const double* Vb = b.V + c0b * ldv;
+    double* Tb = b.Tb + (int64_t)blk * NBb * NBb;
     {
-      ProfScope ps(kProfPanel, st, 3.0 * r * (double)(m + 1) * nbp * nbp,
-                   8.0 * r * (double)(m + NB) * nbp * 2.0);
-      if (m >= kClusterPanelMinRows)
-        qr_panel_cluster_kernel<NB, kPanelCluster><<<r * kPanelCluster, 256, 0, st>>>(
-            b.W, b.strideW, ldw, m, c0, nbp, b.V, b.strideV, ldv, b.T, b.strideT, status);
-      else
-        qr_panel_kernel<NB><<<r, kPanelThreads, 0, st>>>(b.W, b.strideW, ldw, m, c0, nbp, b.V,
-                                                          b.strideV, ldv, b.T, b.strideT, status);
+      ProfScope ps(kProfOther, st);
+      tb_init_kernel<<<dim3((nbb * nbb + 255) / 256, r), 256, 0, st>>>(b.T, b.strideT, Tb,
+                                                                      b.strideTb, (int)(c0b / NB), nbb);
     }
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
-    const int64_t ntr = n - c0 - nbp;
-    if (ntr <= 0) continue;
-    const double* Vp = b.V + c0 * ldv;
-    double* C = b.W + c0 + (c0 + nbp) * ldw;   // window rows [c0, c0+m+nbp), trailing columns
-    const double* Tp = b.T + (int64_t)p * NB * NB;
-    GemmArgs g;
-    // W1 = V^T C
-    g.M = nbp; g.N = (int)ntr; g.K = (int)(m + nbp); g.transA = 1; g.transB = 0;
-    g.A = Vp; g.lda = ldv; g.strideA = b.strideV;
-    g.B = C; g.ldb = ldw; g.strideB = b.strideW;
-    g.Cout = b.W1; g.ldcout = NB; g.strideCout = b.strideW1;
-    g.batch = r;
-    for (int j = 0; j < r; ++j) g.alpha[j] = 1.0;
-    if ((err = gemm_any(g, st)) != cudaSuccess) return err;
-    // W2 = T^T W1
-    GemmArgs h = g;
-    h.K = nbp; h.transA = 1;
-    h.A = Tp; h.lda = NB; h.strideA = b.strideT;
-    h.B = b.W1; h.ldb = NB; h.strideB = b.strideW1;
-    h.Cout = b.W2; h.strideCout = b.strideW2;
-    if ((err = gemm_any(h, st)) != cudaSuccess) return err;
-    // C -= V W2
-    GemmArgs u = g;
-    u.M = (int)(m + nbp); u.N = (int)ntr; u.K = nbp; u.transA = 0; u.transB = 0;
-    u.A = Vp; u.lda = ldv; u.strideA = b.strideV;
-    u.B = b.W2; u.ldb = NB; u.strideB = b.strideW2;
-    u.Cin = C; u.ldcin = ldw; u.strideCin = b.strideW; u.beta = 1.0;
-    u.Cout = C; u.ldcout = ldw; u.strideCout = b.strideW;
-    for (int j = 0; j < r; ++j) u.alpha[j] = -1.0;
-    if ((err = gemm_any(u, st)) != cudaSuccess) return err;
+    if (nbb > NB) {
+      GemmArgs g;   // G = V_b^T V_b
+      g.M = nbb; g.N = nbb; g.K = (int)(m + nbb); g.transA = 1; g.transB = 0;
+      g.A = Vb; g.lda = ldv; g.strideA = b.strideV;
+      g.B = Vb; g.ldb = ldv; g.strideB = b.strideV;
+      g.Cout = b.G; g.ldcout = NBb; g.strideCout = b.strideG;
+      g.batch = r;
+      for (int j = 0; j < r; ++j) g.alpha[j] = 1.0;
+      // in FP64 on every path: the off-diagonal blocks of V_b^T V_b are small next
+      // to the columns' norms, and T_b amplifies their error into every update
+      if ((err = gemm_f64(g, st)) != cudaSuccess) return err;
+      for (int h = NB; h < nbb; h *= 2) {
+        const int pairs = (nbb + 2 * h - 1) / (2 * h);
+        {
+          ProfScope ps(kProfOther, st);
+          tb_merge_kernel<<<dim3(h, pairs, r), NBb / 2, 0, st>>>(b.G, b.strideG, Tb, b.strideTb,
+                                                                 nbb, h);
+        }
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+      }
+    }
+    // ---- all later columns, once per block
+    const int64_t ntr = n - c0b - nbb;
+    if (ntr > 0 &&
+        (err = apply_block(b, Vb, ldv, Tb, NBb, b.strideTb, b.W + c0b + (c0b + nbb) * ldw, ldw,
+                           m + nbb, nbb, ntr, r, 1, st)) != cudaSuccess)
+      return err;
   }
   // ---------------- explicit Q (structured ORGQR), overwriting W
   if ((err = init_q_identity(b.W, b.strideW, m, n, r, st)) != cudaSuccess) return err;
-  for (int p = npanels - 1; p >= 0; --p) {
-    const int64_t c0 = (int64_t)p * NB;
-    const int nbp = (int)(n - c0 < NB ? n - c0 : NB);
-    const int64_t ncol = n - c0;
-    const double* Vp = b.V + c0 * ldv;
-    double* C = b.W + c0 + c0 * ldw;
-    const double* Tp = b.T + (int64_t)p * NB * NB;
-    GemmArgs g;
-    g.M = nbp; g.N = (int)ncol; g.K = (int)(m + nbp); g.transA = 1; g.transB = 0;
-    g.A = Vp; g.lda = ldv; g.strideA = b.strideV;
-    g.B = C; g.ldb = ldw; g.strideB = b.strideW;
-    g.Cout = b.W1; g.ldcout = NB; g.strideCout = b.strideW1;
-    g.batch = r;
-    for (int j = 0; j < r; ++j) g.alpha[j] = 1.0;
-    if ((err = gemm_any(g, st)) != cudaSuccess) return err;
-    GemmArgs h = g;   // W2 = T W1
-    h.K = nbp; h.transA = 0;
-    h.A = Tp; h.lda = NB; h.strideA = b.strideT;
-    h.B = b.W1; h.ldb = NB; h.strideB = b.strideW1;
-    h.Cout = b.W2; h.strideCout = b.strideW2;
-    if ((err = gemm_any(h, st)) != cudaSuccess) return err;
-    GemmArgs u = g;   // C -= V W2
-    u.M = (int)(m + nbp); u.N = (int)ncol; u.K = nbp; u.transA = 0; u.transB = 0;
-    u.A = Vp; u.lda = ldv; u.strideA = b.strideV;
-    u.B = b.W2; u.ldb = NB; u.strideB = b.strideW2;
-    u.Cin = C; u.ldcin = ldw; u.strideCin = b.strideW; u.beta = 1.0;
-    u.Cout = C; u.ldcout = ldw; u.strideCout = b.strideW;
-    for (int j = 0; j < r; ++j) u.alpha[j] = -1.0;
-    if ((err = gemm_any(u, st)) != cudaSuccess) return err;
+  for (int blk = nblocks - 1; blk >= 0; --blk) {
+    const int64_t c0b = (int64_t)blk * NBb;
+    const int nbb = (int)(n - c0b < NBb ? n - c0b : NBb);
+    if ((err = apply_block(b, b.V + c0b * ldv, ldv, b.Tb + (int64_t)blk * NBb * NBb, NBb,
+                           b.strideTb, b.W + c0b + c0b * ldw, ldw, m + nbb, nbb, n - c0b, r, 0,
+                           st)) != cudaSuccess)
+      return err;
   }
   return cudaSuccess;
 }

@@ -96,6 +96,12 @@ struct GemmArgs {
   int reduce = 0;
   int b_lower = 0;
   int c_upper = 0;
+  // split path only: rescale the inner index by exact powers of two so that every
+  // row of op(B) has its largest magnitude in [1/4, 1/2), moving the factors into
+  // op(A)'s columns (the product is unchanged).  For products whose op(B) rows
+  // differ by orders of magnitude, where one scale per output column would cost
+  // the small rows their precision.
+  int k_equilibrate = 0;
 };
 cudaError_t gemm_f64(const GemmArgs& g, cudaStream_t st);
 // algorithmic flops of one call (structural zeros excluded)
@@ -151,13 +157,17 @@ cudaError_t frob_norm2(const double* A, int64_t lda, int64_t m, int64_t n, doubl
                        double* out, cudaStream_t st);
 
 // ------------------------------------------------------------ structured QR
-constexpr int kQrNB = 32;
+constexpr int kQrNB = 32;      // panel width (columns factored by one panel kernel)
+constexpr int kQrBlock = 128;  // block width (columns per trailing update / block reflector)
 struct QrBuffers {
   double* W;   int64_t strideW;   // stacked (m+n) x n per shift, ld m+n
-  double* V;   int64_t strideV;   // explicit reflectors (m+nb) x n per shift, ld m+nb
+  double* V;   int64_t strideV;   // explicit reflectors (m+NBb) x n per shift, ld m+NBb, rows
+                                  // relative to the start of each column's block
   double* T;   int64_t strideT;   // nb x nb triangular factor per panel
-  double* W1;  int64_t strideW1;  // nb x n scratch
-  double* W2;  int64_t strideW2;  // nb x n scratch
+  double* Tb;  int64_t strideTb;  // NBb x NBb triangular factor per block
+  double* G;   int64_t strideG;   // NBb x NBb Gram V_b^T V_b scratch
+  double* W1;  int64_t strideW1;  // NBb x n scratch
+  double* W2;  int64_t strideW2;  // NBb x n scratch
 };
 // Factor [X; sqrt(c_j) I] for j < r and overwrite W_j with the thin Q_j.
 cudaError_t structured_qr_q(const QrBuffers& b, int64_t m, int64_t n, int r, int* status,
