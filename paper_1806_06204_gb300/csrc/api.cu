@@ -130,6 +130,8 @@ size_t layout(void* base, int64_t m, int64_t n, int r, bool svd, PdBufs* b) {
     t.qr.Tb = q.take<double>(r * t.qr.strideTb);
     t.qr.strideG = kQrBlock * kQrBlock;
     t.qr.G = q.take<double>(r * t.qr.strideG);
+    t.qr.elemsP = qr_partial_elems(m, r);
+    t.qr.P = q.take<double>(t.qr.elemsP);
     t.qr.strideW1 = kQrBlock * n;
     t.qr.W1 = q.take<double>(r * t.qr.strideW1);
     t.qr.strideW2 = kQrBlock * n;

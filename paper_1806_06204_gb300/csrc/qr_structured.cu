@@ -351,6 +351,88 @@ tb_merge_kernel(const double* __restrict__ G, int64_t strideG, double* __restric
   }
 }
 
+// ------------------------------------------------------- skinny products
+// C_t = A[:, i0:i0+mt]^T B[:, j0:j0+nt] over K rows, for up to three tiles t
+// with mt <= 64, nt <= 96: the products whose output is a few thousand entries
+// and whose inner dimension is the whole row window (m + w).  One GEMM tile per
+// shift would leave most SMs idle for the length of K, so K is cut into chunks
+// of kTsRows rows: each CTA stages one chunk of the columns it needs in shared
+// memory and writes its partial tile; a second kernel sums the partials chunk
+// by chunk in order (deterministic, FP64).
+constexpr int kTsRows = 64;
+constexpr int kTsThreads = 256;
+constexpr int kTsMaxTile = 64 * 96;   // entries of one tile
+struct TsTiles {
+  int n;
+  int i0[3], j0[3], mt[3], nt[3];
+};
+
+__global__ void __launch_bounds__(kTsThreads)
+ts_partial_kernel(const double* __restrict__ A, int64_t lda, int64_t strideA,
+                  const double* __restrict__ B, int64_t ldb, int64_t strideB, int64_t K,
+                  TsTiles tl, double* __restrict__ P) {
+  __shared__ double sA[kTsRows][65];
+  __shared__ double sB[kTsRows][97];
+  const int chunk = blockIdx.x, t = blockIdx.y, z = blockIdx.z;
+  const int mt = tl.mt[t], nt = tl.nt[t];
+  const double* Az = A + z * strideA + (int64_t)tl.i0[t] * lda;
+  const double* Bz = B + z * strideB + (int64_t)tl.j0[t] * ldb;
+  const int64_t k0 = (int64_t)chunk * kTsRows;
+  const int kc = K - k0 < kTsRows ? (int)(K - k0) : kTsRows;
+  for (int e = threadIdx.x; e < kTsRows * mt; e += kTsThreads) {
+    const int k = e % kTsRows, i = e / kTsRows;
+    sA[k][i] = k < kc ? Az[k0 + k + (int64_t)i * lda] : 0.0;
+  }
+  for (int e = threadIdx.x; e < kTsRows * nt; e += kTsThreads) {
+    const int k = e % kTsRows, j = e / kTsRows;
+    sB[k][j] = k < kc ? Bz[k0 + k + (int64_t)j * ldb] : 0.0;
+  }
+  __syncthreads();
+  double* Pz = P + (((int64_t)chunk * gridDim.z + z) * gridDim.y + t) * kTsMaxTile;
+  for (int e = threadIdx.x; e < mt * nt; e += kTsThreads) {
+    const int i = e % mt, j = e / mt;
+    double acc = 0.0;
+#pragma unroll 8
+    for (int k = 0; k < kTsRows; ++k) acc = fma(sA[k][i], sB[k][j], acc);
+    Pz[e] = acc;
+  }
+}
+
+__global__ void ts_reduce_kernel(const double* __restrict__ P, int nchunks, TsTiles tl,
+                                 double* __restrict__ C, int64_t ldc, int64_t strideC) {
+  const int t = blockIdx.y, z = blockIdx.z;
+  const int mt = tl.mt[t], nt = tl.nt[t];
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= mt * nt) return;
+  double s = 0.0;
+  for (int c = 0; c < nchunks; ++c)
+    s += P[(((int64_t)c * gridDim.z + z) * gridDim.y + t) * kTsMaxTile + e];
+  C[z * strideC + (tl.i0[t] + e % mt) + (int64_t)(tl.j0[t] + e / mt) * ldc] = s;
+}
+
+// C[i0.., j0..] = A[:, i0..]^T B[:, j0..] for the tiles of tl, r shifts (strides
+// per shift), K rows; P holds the partials.
+cudaError_t ts_product(const double* A, int64_t lda, int64_t strideA, const double* B, int64_t ldb,
+                       int64_t strideB, int64_t K, const TsTiles& tl, double* C, int64_t ldc,
+                       int64_t strideC, int r, double* P, int64_t elemsP, cudaStream_t st) {
+  const int nchunks = (int)((K + kTsRows - 1) / kTsRows);
+  if ((int64_t)nchunks * r * tl.n * kTsMaxTile > elemsP) return cudaErrorInvalidValue;
+  for (int t = 0; t < tl.n; ++t)
+    if (tl.mt[t] > 64 || tl.nt[t] > 96 || tl.mt[t] < 1 || tl.nt[t] < 1) return cudaErrorInvalidValue;
+  double fl = 0.0;
+  for (int t = 0; t < tl.n; ++t) fl += 2.0 * tl.mt[t] * tl.nt[t] * (double)K * r;
+  {
+    ProfScope ps(kProfGemm, st, fl, 0.0);
+    ts_partial_kernel<<<dim3(nchunks, tl.n, r), kTsThreads, 0, st>>>(A, lda, strideA, B, ldb,
+                                                                     strideB, K, tl, P);
+  }
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  ProfScope ps(kProfOther, st);
+  ts_reduce_kernel<<<dim3(kTsMaxTile / 256, tl.n, r), 256, 0, st>>>(P, nchunks, tl, C, ldc, strideC);
+  return cudaGetLastError();
+}
+
 // C <- (I - V op(T) V^T) C for r shifts, on the row window of C, as
 // W1 = V^T C, W2 = op(T) W1, C -= V W2 (transT = 1 applies Q^T, the
 // factorisation's update; transT = 0 applies Q, the explicit-Q build).
@@ -365,7 +447,15 @@ cudaError_t apply_block(const QrBuffers& b, const double* Vw, int64_t ldv, const
   g.Cout = b.W1; g.ldcout = kQrBlock; g.strideCout = b.strideW1;
   g.batch = r;
   for (int j = 0; j < r; ++j) g.alpha[j] = 1.0;
-  if ((err = gemm_any(g, st)) != cudaSuccess) return err;
+  if (w <= 32 && ncols <= 96) {
+    // a panel's own block: a skinny output over the whole window, split over K
+    TsTiles tl{1, {0}, {0}, {w}, {(int)ncols}};
+    err = ts_product(Vw, ldv, b.strideV, C, ldw, b.strideW, rows, tl, b.W1, kQrBlock, b.strideW1,
+                     r, b.P, b.elemsP, st);
+  } else {
+    err = gemm_any(g, st);
+  }
+  if (err != cudaSuccess) return err;
   GemmArgs h = g;
   h.K = w; h.transA = transT;
   h.A = Tw; h.lda = ldt; h.strideA = strideT;
@@ -386,6 +476,11 @@ cudaError_t apply_block(const QrBuffers& b, const double* Vw, int64_t ldv, const
 }
 
 }  // namespace
+
+int64_t qr_partial_elems(int64_t m, int r) {
+  const int64_t nchunks = (m + kQrBlock + kTsRows - 1) / kTsRows;
+  return nchunks * r * 3 * kTsMaxTile;
+}
 
 cudaError_t structured_qr_q(const QrBuffers& b, int64_t m, int64_t n, int r, int* status,
                             cudaStream_t st) {
@@ -436,16 +531,22 @@ cudaError_t structured_qr_q(const QrBuffers& b, int64_t m, int64_t n, int r, int
     }
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     if (nbb > NB) {
-      GemmArgs g;   // G = V_b^T V_b
-      g.M = nbb; g.N = nbb; g.K = (int)(m + nbb); g.transA = 1; g.transB = 0;
-      g.A = Vb; g.lda = ldv; g.strideA = b.strideV;
-      g.B = Vb; g.ldb = ldv; g.strideB = b.strideV;
-      g.Cout = b.G; g.ldcout = NBb; g.strideCout = b.strideG;
-      g.batch = r;
-      for (int j = 0; j < r; ++j) g.alpha[j] = 1.0;
-      // in FP64 on every path: the off-diagonal blocks of V_b^T V_b are small next
-      // to the columns' norms, and T_b amplifies their error into every update
-      if ((err = gemm_f64(g, st)) != cudaSuccess) return err;
+      // the blocks of G = V_b^T V_b that the merges read: [0,32)x[32,64),
+      // [64,96)x[96,128) and [0,64)x[64,128) (clipped to the block), in FP64 on
+      // every path: they are small next to the columns' norms, and T_b carries
+      // their error into every update
+      static_assert(kQrBlock == 4 * kQrNB, "the merge levels assume four panels per block");
+      TsTiles tl{};
+      auto add = [&](int i0, int j0, int mt, int nt) {
+        nt = nbb - j0 < nt ? nbb - j0 : nt;
+        if (nt > 0) { tl.i0[tl.n] = i0; tl.j0[tl.n] = j0; tl.mt[tl.n] = mt; tl.nt[tl.n] = nt; ++tl.n; }
+      };
+      add(0, 32, 32, 32);
+      add(64, 96, 32, 32);
+      add(0, 64, 64, 64);
+      if ((err = ts_product(Vb, ldv, b.strideV, Vb, ldv, b.strideV, m + nbb, tl, b.G, NBb, b.strideG,
+                            r, b.P, b.elemsP, st)) != cudaSuccess)
+        return err;
       for (int h = NB; h < nbb; h *= 2) {
         const int pairs = (nbb + 2 * h - 1) / (2 * h);
         {

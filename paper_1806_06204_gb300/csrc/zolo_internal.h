@@ -166,9 +166,12 @@ struct QrBuffers {
   double* T;   int64_t strideT;   // nb x nb triangular factor per panel
   double* Tb;  int64_t strideTb;  // NBb x NBb triangular factor per block
   double* G;   int64_t strideG;   // NBb x NBb Gram V_b^T V_b scratch
+  double* P;   int64_t elemsP;    // split-K partial products of the skinny products
   double* W1;  int64_t strideW1;  // NBb x n scratch
   double* W2;  int64_t strideW2;  // NBb x n scratch
 };
+// Doubles of QrBuffers::P for an m-row problem with r shifts.
+int64_t qr_partial_elems(int64_t m, int r);
 // Factor [X; sqrt(c_j) I] for j < r and overwrite W_j with the thin Q_j.
 cudaError_t structured_qr_q(const QrBuffers& b, int64_t m, int64_t n, int r, int* status,
                             cudaStream_t st);
