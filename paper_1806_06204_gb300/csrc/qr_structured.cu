@@ -31,128 +31,26 @@
 namespace zolo {
 namespace {
 
-constexpr int kPanelThreads = 512;
 constexpr int kPanelCluster = 8;            // CTAs per shift in the cluster panel
 constexpr int64_t kClusterPanelMinRows = 512;
 
-// One CTA per shift j.  Factors panel columns [c0, c0 + nbp) of W_j in place
-// (R on and above the diagonal, Householder vectors below it, as LAPACK), writes
-// the explicit reflectors (unit diagonal, exact zeros elsewhere) to V_j's
-// columns [c0, c0 + nbp) with rows relative to c0, and the upper-triangular
-// compact-WY factor T (H_0 ... H_{nbp-1} = I - V T V^T) to T_j's panel slot.
-template <int NB>
-__global__ void __launch_bounds__(kPanelThreads)
-qr_panel_kernel(double* W, int64_t strideW, int64_t ldw, int64_t m, int64_t c0, int nbp, double* V,
-                int64_t strideV, int64_t ldv, double* T, int64_t strideT, int* status) {
-  __shared__ double red[kPanelThreads / 32][NB];
-  __shared__ double dots[NB];
-  __shared__ double Ts[NB][NB + 1];
-  __shared__ double s_tau, s_scal, s_beta;
-
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  constexpr int kWarps = kPanelThreads / 32;
-  double* Wj = W + blockIdx.x * strideW;
-  double* Vp = V + blockIdx.x * strideV + c0 * ldv;
-  double* Tp = T + blockIdx.x * strideT + (c0 / NB) * (int64_t)(NB * NB);
-
-  for (int e = tid; e < NB * (NB + 1); e += blockDim.x) (&Ts[0][0])[e] = 0.0;
-
-  for (int i = 0; i < nbp; ++i) {
-    const int64_t c = c0 + i;
-    double* col = Wj + c * ldw;
-    // ---- 1. norm of the tail x[c+1 .. m+c]
-    double ss = 0.0;
-    for (int64_t r = c + 1 + tid; r <= m + c; r += kPanelThreads) {
-      const double v = col[r];
-      ss = fma(v, v, ss);
-    }
-    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-    __syncthreads();
-    if (lane == 0) red[warp][0] = ss;
-    __syncthreads();
-    if (tid == 0) {
-      double s = 0.0;
-      for (int w = 0; w < kWarps; ++w) s += red[w][0];
-      const double alpha = col[c];
-      double beta, tau, scal;
-      if (s == 0.0) {
-        beta = alpha; tau = 0.0; scal = 0.0;
-      } else {
-        beta = -copysign(sqrt(fma(alpha, alpha, s)), alpha);
-        tau = (beta - alpha) / beta;
-        scal = 1.0 / (alpha - beta);
-      }
-      if (!isfinite(beta) || !isfinite(tau)) atomicOr(status + kStatNonFinite, 1);
-      s_beta = beta; s_tau = tau; s_scal = scal;
-    }
-    __syncthreads();
-    const double tau = s_tau, scal = s_scal;
-    // ---- 2. v = x / (alpha - beta), explicit copy into V (window rows c0 .. c0+m+NB-1)
-    double* Vcol = Vp + (int64_t)i * ldv;
-    for (int64_t rel = tid; rel < m + NB; rel += kPanelThreads) {
-      const int64_t r = c0 + rel;
-      double v;
-      if (r < c || r > m + c) {
-        v = 0.0;
-      } else if (r == c) {
-        v = 1.0;
-      } else {
-        v = col[r] * scal;
-        col[r] = v;
-      }
-      Vcol[rel] = v;
-    }
-    __syncthreads();
-    if (tid == 0) col[c] = s_beta;
-    // ---- 3. dots of v with the later panel columns (for the update) and with
-    //         the earlier reflectors (for T), in one pass over the support
-    double acc[NB];
+// Reduce-scatter of 32 per-lane partial sums across a warp: on return lane q
+// holds the warp's total of value q.  Each step keeps the half of the values
+// selected by one lane bit and adds the partner's copy of that half: 16 + 8 +
+// 4 + 2 + 1 = 31 adds per lane, where one butterfly per value costs 5 x 32 (the
+// FP64 adds, not the shuffles, bound the panel on this part).
+__device__ __forceinline__ double warp_reduce_scatter32(double (&a)[32], int lane) {
 #pragma unroll
-    for (int q = 0; q < NB; ++q) acc[q] = 0.0;
-    for (int64_t r = c + tid; r <= m + c; r += kPanelThreads) {
-      const double v = Vcol[r - c0];
+  for (int h = 16; h >= 1; h >>= 1) {
+    const bool up = (lane & h) != 0;
 #pragma unroll
-      for (int q = 0; q < NB; ++q) {
-        if (q < nbp && q != i) {
-          const double o = q > i ? Wj[r + (c0 + q) * ldw] : Vp[(r - c0) + (int64_t)q * ldv];
-          acc[q] = fma(v, o, acc[q]);
-        }
-      }
+    for (int j = 0; j < h; ++j) {
+      const double send = up ? a[j] : a[j + h];
+      const double keep = up ? a[j + h] : a[j];
+      a[j] = keep + __shfl_xor_sync(0xffffffffu, send, h);
     }
-#pragma unroll
-    for (int q = 0; q < NB; ++q) {
-      double v = acc[q];
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) red[warp][q] = v;
-    }
-    __syncthreads();
-    if (tid < NB) {
-      double s = 0.0;
-      for (int w = 0; w < kWarps; ++w) s += red[w][tid];
-      dots[tid] = s;
-    }
-    __syncthreads();
-    // ---- 4. apply H_i to the later panel columns: W[:, q] -= tau * dots[q] * v
-    for (int64_t r = c + tid; r <= m + c; r += kPanelThreads) {
-      const double v = Vcol[r - c0];
-#pragma unroll
-      for (int q = 0; q < NB; ++q) {
-        if (q > i && q < nbp) {
-          double* p = Wj + r + (c0 + q) * ldw;
-          *p = fma(-tau * dots[q], v, *p);
-        }
-      }
-    }
-    // ---- 5. T(0:i, i) = -tau T(0:i, 0:i) V^T v_i,  T(i, i) = tau
-    if (tid < i) {
-      double s = 0.0;
-      for (int p = tid; p < i; ++p) s = fma(Ts[tid][p], dots[p], s);
-      Ts[tid][i] = -tau * s;
-    }
-    if (tid == 0) Ts[i][i] = tau;
-    __syncthreads();
   }
-  for (int e = tid; e < NB * NB; e += kPanelThreads) Tp[e] = Ts[e % NB][e / NB];
+  return a[0];
 }
 
 // Cluster form of the panel factorisation: CG CTAs per shift (one thread-block
@@ -264,12 +162,8 @@ qr_panel_cluster_kernel(double* W, int64_t strideW, int64_t ldw, int64_t m, int6
         }
       }
     }
-#pragma unroll
-    for (int q = 0; q < NB; ++q) {
-      double v = acc[q];
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) red[warp][q] = v;
-    }
+    static_assert(NB == 32, "one dot product per lane");
+    red[warp][lane] = warp_reduce_scatter32(acc, lane);
     __syncthreads();
     if (tid < NB) {
       double t = 0.0;
@@ -349,6 +243,167 @@ tb_merge_kernel(const double* __restrict__ G, int64_t strideG, double* __restric
     for (int k = i; k < h; ++k) t = fma(T[(a + i) + (int64_t)(a + k) * ld], x[k], t);
     T[(a + i) + (int64_t)(b0 + j) * ld] = -t;
   }
+}
+
+// Shared-memory form of the panel factorisation: each of the CG CTAs of a
+// shift (one cluster; CG = 1 is a single CTA) loads its rows of the panel's 32
+// columns into shared memory once, factors them there, and writes W, V and T
+// back at the end.  The per-column steps are those of the cluster kernel above
+// (norm and dot-product partials exchanged through distributed shared memory in
+// rank order, so every CTA forms the same beta, tau and dots); only the panel's
+// storage moves from L2 to shared memory, which removes the L2 round trips of
+// the ~80 accesses per row and column.  The reflector's unit diagonal is kept
+// implicit (the diagonal slot holds beta once it is formed), so no second copy
+// of V is needed.  Rows per CTA: ceil((m + NB) / CG) <= kSmemPanelRows.
+constexpr int kSmemPanelRows = 768;
+
+template <int NB, int CG>
+__global__ void __cluster_dims__(CG, 1, 1) __launch_bounds__(256)
+qr_panel_smem_kernel(double* W, int64_t strideW, int64_t ldw, int64_t m, int64_t c0, int nbp,
+                     double* V, int64_t strideV, int64_t ldv, double* T, int64_t strideT,
+                     int* status) {
+  namespace cgrp = cooperative_groups;
+  cgrp::cluster_group cluster = cgrp::this_cluster();
+  constexpr int kT = 256, kWarps = kT / 32;
+  extern __shared__ double Ws[];              // NB columns x Rs rows, column-major
+  __shared__ double part[2][NB + 2];          // [0, NB): dots, NB: norm^2, NB+1: alpha
+  __shared__ double red[kWarps][NB + 2];
+  __shared__ double dots[NB];
+  __shared__ double Ts[NB][NB + 1];
+  __shared__ double s_tau, s_scal, s_beta;
+
+  const int rank = (int)cluster.block_rank();
+  const int shift = blockIdx.x / CG;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double* Wj = W + shift * strideW;
+  double* Vp = V + shift * strideV + c0 * ldv;
+  double* Tp = T + shift * strideT + (c0 / NB) * (int64_t)(NB * NB);
+  const int64_t height = m + NB;
+  const int Rs = (int)((height + CG - 1) / CG);
+  const int64_t lo = c0 + (int64_t)rank * Rs;             // my window rows [lo, hi)
+  const int64_t hi = lo + Rs < c0 + height ? lo + Rs : c0 + height;
+  const int64_t rows_w = ldw;                             // rows that exist in W (m + n)
+  const int nr = hi > lo ? (int)(hi - lo) : 0;
+
+  for (int q = 0; q < NB; ++q)
+    for (int rr = tid; rr < Rs; rr += kT) {
+      const int64_t r = lo + rr;
+      Ws[q * Rs + rr] = (q < nbp && rr < nr && r < rows_w) ? Wj[r + (c0 + q) * ldw] : 0.0;
+    }
+  for (int e = tid; e < NB * (NB + 1); e += kT) (&Ts[0][0])[e] = 0.0;
+  __syncthreads();
+
+  for (int i = 0; i < nbp; ++i) {
+    const int64_t c = c0 + i;
+    const int buf = i & 1;
+    double* col = Ws + i * Rs;
+    const int64_t r0 = lo > c ? lo : c;                  // my part of the support [c, m + c]
+    const int64_t r1 = hi < m + c + 1 ? hi : m + c + 1;
+    // ---- 1. partial norm of the tail (rows > c) and alpha from the owner of row c
+    double ss = 0.0;
+    for (int64_t r = (r0 > c + 1 ? r0 : c + 1) + tid; r < r1; r += kT) {
+      const double v = col[r - lo];
+      ss = fma(v, v, ss);
+    }
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    if (lane == 0) red[warp][0] = ss;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < kWarps; ++w) t += red[w][0];
+      part[buf][NB] = t;
+      part[buf][NB + 1] = (c >= lo && c < hi) ? col[c - lo] : 0.0;
+    }
+    cluster.sync();
+    if (tid == 0) {
+      double sum = 0.0, alpha = 0.0;
+      for (int rk = 0; rk < CG; ++rk) {
+        const double* rp = cluster.map_shared_rank(&part[buf][0], rk);
+        sum += rp[NB];
+        alpha += rp[NB + 1];
+      }
+      double beta, tau, scal;
+      if (sum == 0.0) {
+        beta = alpha; tau = 0.0; scal = 0.0;
+      } else {
+        beta = -copysign(sqrt(fma(alpha, alpha, sum)), alpha);
+        tau = (beta - alpha) / beta;
+        scal = 1.0 / (alpha - beta);
+      }
+      if (rank == 0 && (!isfinite(beta) || !isfinite(tau))) atomicOr(status + kStatNonFinite, 1);
+      s_beta = beta; s_tau = tau; s_scal = scal;
+    }
+    __syncthreads();
+    const double tau = s_tau, scal = s_scal;
+    // ---- 2. my rows of v below the diagonal; the diagonal slot takes beta
+    //         (v's unit diagonal is implicit from here on)
+    for (int64_t r = (r0 > c + 1 ? r0 : c + 1) + tid; r < r1; r += kT) col[r - lo] *= scal;
+    if (tid == 0 && c >= lo && c < hi) col[c - lo] = s_beta;
+    __syncthreads();
+    // ---- 3. partial dots of v with the later panel columns and the earlier reflectors
+    double acc[NB];
+#pragma unroll
+    for (int q = 0; q < NB; ++q) acc[q] = 0.0;
+    for (int64_t r = r0 + tid; r < r1; r += kT) {
+      const double v = (r == c) ? 1.0 : col[r - lo];
+#pragma unroll
+      for (int q = 0; q < NB; ++q) {
+        if (q < nbp && q != i) {
+          // earlier reflector q: support rows [c0+q, m+c0+q]; r >= c > c0+q
+          const double o = (q > i || r <= m + c0 + q) ? Ws[q * Rs + (r - lo)] : 0.0;
+          acc[q] = fma(v, o, acc[q]);
+        }
+      }
+    }
+    static_assert(NB == 32, "one dot product per lane");
+    red[warp][lane] = warp_reduce_scatter32(acc, lane);
+    __syncthreads();
+    if (tid < NB) {
+      double t = 0.0;
+      for (int w = 0; w < kWarps; ++w) t += red[w][tid];
+      part[buf][tid] = t;
+    }
+    cluster.sync();
+    if (tid < NB) {
+      double t = 0.0;
+      for (int rk = 0; rk < CG; ++rk) t += cluster.map_shared_rank(&part[buf][0], rk)[tid];
+      dots[tid] = t;
+    }
+    __syncthreads();
+    // ---- 4. my rows of the later panel columns: W[:, q] -= tau * dots[q] * v
+    for (int64_t r = r0 + tid; r < r1; r += kT) {
+      const double v = (r == c) ? 1.0 : col[r - lo];
+#pragma unroll
+      for (int q = 0; q < NB; ++q) {
+        if (q > i && q < nbp) {
+          double* pq = Ws + q * Rs + (r - lo);
+          *pq = fma(-tau * dots[q], v, *pq);
+        }
+      }
+    }
+    // ---- 5. T(0:i, i) = -tau T(0:i, 0:i) V^T v_i (same in every CTA)
+    if (tid < i) {
+      double t = 0.0;
+      for (int pc = tid; pc < i; ++pc) t = fma(Ts[tid][pc], dots[pc], t);
+      Ts[tid][i] = -tau * t;
+    }
+    if (tid == 0) Ts[i][i] = tau;
+    __syncthreads();
+  }
+  // ---- write back: W (R above the diagonal, beta on it, v below), the explicit
+  //      reflectors (unit diagonal, exact zeros outside each support) and T
+  for (int q = 0; q < nbp; ++q) {
+    const int64_t cq = c0 + q;
+    for (int rr = tid; rr < nr; rr += kT) {
+      const int64_t r = lo + rr;
+      const double w = Ws[q * Rs + rr];
+      if (r < rows_w) Wj[r + cq * ldw] = w;
+      Vp[(r - c0) + (int64_t)q * ldv] = (r < cq || r > m + cq) ? 0.0 : (r == cq ? 1.0 : w);
+    }
+  }
+  if (rank == 0)
+    for (int e = tid; e < NB * NB; e += kT) Tp[e] = Ts[e % NB][e / NB];
+  cluster.sync();   // no CTA leaves while another may still read its partials
 }
 
 // ------------------------------------------------------- skinny products
@@ -485,6 +540,14 @@ int64_t qr_partial_elems(int64_t m, int r) {
 cudaError_t structured_qr_q(const QrBuffers& b, int64_t m, int64_t n, int r, int* status,
                             cudaStream_t st) {
   constexpr int NB = kQrNB, NBb = kQrBlock;
+  static const bool smem_ready = [] {
+    const int bytes = (int)(sizeof(double) * NB * kSmemPanelRows);
+    return cudaFuncSetAttribute(qr_panel_smem_kernel<NB, 1>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess &&
+           cudaFuncSetAttribute(qr_panel_smem_kernel<NB, kPanelCluster>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess;
+  }();
+  if (!smem_ready) return cudaErrorInvalidConfiguration;
   const int64_t ldw = m + n;
   const int64_t ldv = m + NBb;
   cudaError_t err;
@@ -503,12 +566,17 @@ cudaError_t structured_qr_q(const QrBuffers& b, int64_t m, int64_t n, int r, int
       {
         ProfScope ps(kProfPanel, st, 3.0 * r * (double)(m + 1) * nbp * nbp,
                      8.0 * r * (double)(m + NB) * nbp * 2.0);
-        if (m >= kClusterPanelMinRows)
-          qr_panel_cluster_kernel<NB, kPanelCluster><<<r * kPanelCluster, 256, 0, st>>>(
+        const int64_t rows8 = (m + NB + kPanelCluster - 1) / kPanelCluster;
+        if (m + NB <= kSmemPanelRows && m < kClusterPanelMinRows)
+          qr_panel_smem_kernel<NB, 1><<<r, 256, sizeof(double) * NB * (m + NB), st>>>(
+              b.W, b.strideW, ldw, m, c0, nbp, Vpan, b.strideV, ldv, b.T, b.strideT, status);
+        else if (rows8 <= kSmemPanelRows)
+          qr_panel_smem_kernel<NB, kPanelCluster><<<r * kPanelCluster, 256,
+                                                    sizeof(double) * NB * rows8, st>>>(
               b.W, b.strideW, ldw, m, c0, nbp, Vpan, b.strideV, ldv, b.T, b.strideT, status);
         else
-          qr_panel_kernel<NB><<<r, kPanelThreads, 0, st>>>(b.W, b.strideW, ldw, m, c0, nbp, Vpan,
-                                                            b.strideV, ldv, b.T, b.strideT, status);
+          qr_panel_cluster_kernel<NB, kPanelCluster><<<r * kPanelCluster, 256, 0, st>>>(
+              b.W, b.strideW, ldw, m, c0, nbp, Vpan, b.strideV, ldv, b.T, b.strideT, status);
       }
       if ((err = cudaGetLastError()) != cudaSuccess) return err;
       // the rest of this block's columns
