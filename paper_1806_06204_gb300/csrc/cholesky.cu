@@ -5,8 +5,12 @@
 // Blocked right-looking Cholesky: the NB x NB diagonal block is factored in
 // shared memory by one CTA per shift, which also inverts it; the row panel is
 // R_kk^{-T} Z_k,rest and the trailing update a SYRK, both on the FP64 GEMM.
-// The triangular solves go block column by block column, each step a GEMM
-// update followed by a product with the inverted diagonal block.
+// The triangular solves are recursive: halve the columns, solve one half,
+// update the other with one GEMM whose inner dimension is the half's width,
+// solve it; 64-column leaves are products with the inverted diagonal block.
+// Every column of the right-hand side is read by O(log n) GEMMs (the
+// block-column-by-block-column form reads the solved part once per block, which
+// on the split path re-slices it n/64 times).
 #include <cmath>
 
 #include "zolo_internal.h"
@@ -116,70 +120,134 @@ cudaError_t cholesky_upper_batched(const CholBuffers& b, int64_t n, int r, int* 
   return cudaSuccess;
 }
 
+namespace {
+
+// dst_j[:, 0:w] = src_j[:, 0:w] for r matrices of m rows (column-major).
+__global__ void copy_cols_kernel(const double* __restrict__ src, int64_t lds, int64_t strideS,
+                                 double* __restrict__ dst, int64_t ldd, int64_t strideD, int64_t m,
+                                 int w) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m * w) return;
+  const int64_t i = e % m, c = e / m;
+  dst[blockIdx.y * strideD + i + c * ldd] = src[blockIdx.y * strideS + i + c * lds];
+}
+
+cudaError_t copy_cols(const double* src, int64_t lds, int64_t strideS, double* dst, int64_t ldd,
+                      int64_t strideD, int64_t m, int w, int r, cudaStream_t st) {
+  ProfScope ps(kProfOther, st, 0.0, 16.0 * m * w * r);
+  copy_cols_kernel<<<dim3((unsigned)((m * w + 255) / 256), r), 256, 0, st>>>(src, lds, strideS, dst,
+                                                                             ldd, strideD, m, w);
+  return cudaGetLastError();
+}
+
+struct TrsmCtx {
+  const CholBuffers* b;
+  double* Y; int64_t strideY;
+  double* tmp; int64_t strideTmp;
+  int64_t m, n;
+  int r;
+  cudaStream_t st;
+};
+
+// split point of [j0, j0 + w): a multiple of NB near the middle
+int64_t half_of(int w) {
+  const int nb = kCholNB;
+  const int blocks = (w + nb - 1) / nb;
+  return (int64_t)((blocks + 1) / 2) * nb;
+}
+
+// Y[:, j0:j0+w] R[j0:j0+w, j0:j0+w] = rhs[:, j0:j0+w]; rhs is X (shared by the
+// shifts, stride strideR = 0) at the top and Y itself once updated.
+cudaError_t fwd(const TrsmCtx& c, const double* rhs, int64_t ldr, int64_t strideR, int64_t j0, int w) {
+  cudaError_t err;
+  const CholBuffers& b = *c.b;
+  if (w <= kCholNB) {
+    const double* A = rhs + j0 * ldr;
+    int64_t lda = ldr, strideA = strideR;
+    if (rhs == c.Y) {   // in place: the product reads its own output, so copy first
+      if ((err = copy_cols(rhs + j0 * ldr, ldr, strideR, c.tmp, c.m, c.strideTmp, c.m, w, c.r, c.st)) !=
+          cudaSuccess)
+        return err;
+      A = c.tmp; lda = c.m; strideA = c.strideTmp;
+    }
+    GemmArgs h;   // Y_j = rhs_j Rinv_jj
+    h.M = (int)c.m; h.N = w; h.K = w; h.transA = 0; h.transB = 0;
+    h.A = A; h.lda = lda; h.strideA = strideA;
+    h.B = b.Rinv + (j0 / kCholNB) * (int64_t)(kCholNB * kCholNB); h.ldb = kCholNB;
+    h.strideB = b.strideRinv;
+    h.Cout = c.Y + j0 * c.m; h.ldcout = c.m; h.strideCout = c.strideY;
+    h.batch = c.r;
+    for (int j = 0; j < c.r; ++j) h.alpha[j] = 1.0;
+    return gemm_any(h, c.st);
+  }
+  const int64_t h1 = half_of(w);
+  const int w2 = (int)(w - h1);
+  if ((err = fwd(c, rhs, ldr, strideR, j0, (int)h1)) != cudaSuccess) return err;
+  GemmArgs g;   // Y_2 = rhs_2 - Y_1 R_12
+  g.M = (int)c.m; g.N = w2; g.K = (int)h1; g.transA = 0; g.transB = 0;
+  g.A = c.Y + j0 * c.m; g.lda = c.m; g.strideA = c.strideY;
+  g.B = b.Z + j0 + (j0 + h1) * c.n; g.ldb = c.n; g.strideB = b.strideZ;
+  g.Cin = rhs + (j0 + h1) * ldr; g.ldcin = ldr; g.strideCin = strideR; g.beta = 1.0;
+  g.Cout = c.Y + (j0 + h1) * c.m; g.ldcout = c.m; g.strideCout = c.strideY;
+  g.batch = c.r;
+  for (int j = 0; j < c.r; ++j) g.alpha[j] = -1.0;
+  if ((err = gemm_any(g, c.st)) != cudaSuccess) return err;
+  return fwd(c, c.Y, c.m, c.strideY, j0 + h1, w2);
+}
+
+// W[:, j0:j0+w] R[j0:j0+w, j0:j0+w]^T = Y[:, j0:j0+w], W overwriting Y.
+cudaError_t bwd(const TrsmCtx& c, int64_t j0, int w) {
+  cudaError_t err;
+  const CholBuffers& b = *c.b;
+  if (w <= kCholNB) {
+    if ((err = copy_cols(c.Y + j0 * c.m, c.m, c.strideY, c.tmp, c.m, c.strideTmp, c.m, w, c.r, c.st)) !=
+        cudaSuccess)
+      return err;
+    GemmArgs h;   // W_j = Y_j Rinv_jj^T
+    h.M = (int)c.m; h.N = w; h.K = w; h.transA = 0; h.transB = 1;
+    h.A = c.tmp; h.lda = c.m; h.strideA = c.strideTmp;
+    h.B = b.Rinv + (j0 / kCholNB) * (int64_t)(kCholNB * kCholNB); h.ldb = kCholNB;
+    h.strideB = b.strideRinv;
+    h.Cout = c.Y + j0 * c.m; h.ldcout = c.m; h.strideCout = c.strideY;
+    h.batch = c.r;
+    for (int j = 0; j < c.r; ++j) h.alpha[j] = 1.0;
+    return gemm_any(h, c.st);
+  }
+  const int64_t h1 = half_of(w);
+  const int w2 = (int)(w - h1);
+  if ((err = bwd(c, j0 + h1, w2)) != cudaSuccess) return err;
+  GemmArgs g;   // Y_1 -= W_2 R_12^T
+  g.M = (int)c.m; g.N = (int)h1; g.K = w2; g.transA = 0; g.transB = 1;
+  g.A = c.Y + (j0 + h1) * c.m; g.lda = c.m; g.strideA = c.strideY;
+  g.B = b.Z + j0 + (j0 + h1) * c.n; g.ldb = c.n; g.strideB = b.strideZ;
+  g.Cin = c.Y + j0 * c.m; g.ldcin = c.m; g.strideCin = c.strideY; g.beta = 1.0;
+  g.Cout = c.Y + j0 * c.m; g.ldcout = c.m; g.strideCout = c.strideY;
+  g.batch = c.r;
+  for (int j = 0; j < c.r; ++j) g.alpha[j] = -1.0;
+  if ((err = gemm_any(g, c.st)) != cudaSuccess) return err;
+  return bwd(c, j0, (int)h1);
+}
+
+}  // namespace
+
 cudaError_t trsm_right_upper_batched(const double* X, int64_t ldx, const CholBuffers& b, double* Y,
                                      int64_t strideY, double* tmp, int64_t strideTmp, int64_t m,
                                      int64_t n, int r, cudaStream_t st) {
-  constexpr int NB = kCholNB;
-  cudaError_t err;
-  const int nblk = (int)((n + NB - 1) / NB);
-  // Y R = X, block column by block column
-  for (int jb = 0; jb < nblk; ++jb) {
-    const int64_t j0 = (int64_t)jb * NB;
-    const int nbj = (int)(n - j0 < NB ? n - j0 : NB);
-    GemmArgs g;   // tmp = X_j - Y_{<j} R_{<j, j}
-    g.M = (int)m; g.N = nbj; g.K = (int)j0; g.transA = 0; g.transB = 0;
-    g.A = Y; g.lda = m; g.strideA = strideY;
-    g.B = b.Z + j0 * n; g.ldb = n; g.strideB = b.strideZ;
-    g.Cin = X + j0 * ldx; g.ldcin = ldx; g.strideCin = 0; g.beta = 1.0;
-    g.Cout = tmp; g.ldcout = m; g.strideCout = strideTmp;
-    g.batch = r;
-    for (int j = 0; j < r; ++j) g.alpha[j] = -1.0;
-    if ((err = gemm_any(g, st)) != cudaSuccess) return err;
-    GemmArgs h;   // Y_j = tmp Rinv_jj
-    h.M = (int)m; h.N = nbj; h.K = nbj; h.transA = 0; h.transB = 0;
-    h.A = tmp; h.lda = m; h.strideA = strideTmp;
-    h.B = b.Rinv + jb * (int64_t)(NB * NB); h.ldb = NB; h.strideB = b.strideRinv;
-    h.Cout = Y + j0 * m; h.ldcout = m; h.strideCout = strideY;
-    h.batch = r;
-    for (int j = 0; j < r; ++j) h.alpha[j] = 1.0;
-    if ((err = gemm_any(h, st)) != cudaSuccess) return err;
-  }
-  return cudaSuccess;
+  if (n <= 0 || m <= 0) return cudaSuccess;
+  TrsmCtx c{&b, Y, strideY, tmp, strideTmp, m, n, r, st};
+  return fwd(c, X, ldx, 0, 0, (int)n);
 }
 
 cudaError_t trsm_pair_batched(const double* X, int64_t ldx, const CholBuffers& b, double* Y,
                               int64_t strideY, double* tmp, int64_t strideTmp, int64_t m,
                               int64_t n, int r, cudaStream_t st) {
-  constexpr int NB = kCholNB;
+  if (n <= 0 || m <= 0) return cudaSuccess;
   cudaError_t err;
-  const int nblk = (int)((n + NB - 1) / NB);
   if ((err = trsm_right_upper_batched(X, ldx, b, Y, strideY, tmp, strideTmp, m, n, r, st)) !=
       cudaSuccess)
     return err;
-  // backward: W R^T = Y, last block column first, W overwriting Y
-  for (int jb = nblk - 1; jb >= 0; --jb) {
-    const int64_t j0 = (int64_t)jb * NB;
-    const int nbj = (int)(n - j0 < NB ? n - j0 : NB);
-    const int64_t rest = n - j0 - nbj;
-    GemmArgs g;   // tmp = Y_j - W_{>j} (R_{j, >j})^T
-    g.M = (int)m; g.N = nbj; g.K = (int)rest; g.transA = 0; g.transB = 1;
-    g.A = Y + (j0 + nbj) * m; g.lda = m; g.strideA = strideY;
-    g.B = b.Z + j0 + (j0 + nbj) * n; g.ldb = n; g.strideB = b.strideZ;
-    g.Cin = Y + j0 * m; g.ldcin = m; g.strideCin = strideY; g.beta = 1.0;
-    g.Cout = tmp; g.ldcout = m; g.strideCout = strideTmp;
-    g.batch = r;
-    for (int j = 0; j < r; ++j) g.alpha[j] = -1.0;
-    if ((err = gemm_any(g, st)) != cudaSuccess) return err;
-    GemmArgs h;   // W_j = tmp Rinv_jj^T
-    h.M = (int)m; h.N = nbj; h.K = nbj; h.transA = 0; h.transB = 1;
-    h.A = tmp; h.lda = m; h.strideA = strideTmp;
-    h.B = b.Rinv + jb * (int64_t)(NB * NB); h.ldb = NB; h.strideB = b.strideRinv;
-    h.Cout = Y + j0 * m; h.ldcout = m; h.strideCout = strideY;
-    h.batch = r;
-    for (int j = 0; j < r; ++j) h.alpha[j] = 1.0;
-    if ((err = gemm_any(h, st)) != cudaSuccess) return err;
-  }
-  return cudaSuccess;
+  TrsmCtx c{&b, Y, strideY, tmp, strideTmp, m, n, r, st};
+  return bwd(c, 0, (int)n);
 }
 
 }  // namespace zolo

@@ -13,9 +13,9 @@
 // <= 2^24.  Levels 2..8 (p <= 7) therefore accumulate exactly in their own TMEM
 // accumulator over K-chunks of 2048; the levels >= 9 share one FP32
 // accumulator, whose rounding lies 2^-42 below the leading level.  After every
-// chunk the epilogue adds the exact levels as integers (an int64 in units of
-// 2^-48) and the merged one as a float, and at the end applies 2^(e_i + f_j),
-// alpha and beta in FP64.
+// chunk the epilogue adds the exact levels to an int64 counting units of 2^-48
+// and the merged one to a float; at the end it joins them with one FMA and
+// applies 2^(e_i + f_j) through the exponent field, alpha and beta in FP64.
 // Accuracy: |C - AB| <~ sqrt(K) 2^-6S max|A_i.| max|B_.j| (S = 9: FP64 grade).
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -228,6 +228,17 @@ __global__ void slice_kernel(const double* __restrict__ X, int64_t ldx, int64_t 
 }
 
 // ----------------------------------------------------------------- GEMM
+// x 2^k, exact: an integer add on the exponent field while the result stays a
+// normal number (ldexp otherwise; zero stays zero).
+__device__ __forceinline__ double pow2_scale(double x, int k) {
+  const long long b = __double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FF);
+  if (e == 0) return x == 0.0 ? x : ldexp(x, k);
+  const int ne = e + k;
+  if (ne <= 0 || ne >= 0x7FF) return ldexp(x, k);
+  return __longlong_as_double(b + ((long long)k << 52));
+}
+
 struct SplitEpi {
   double* C;                // output (column-major), per-batch stride
   int64_t ldc, strideC;
@@ -375,7 +386,8 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     // those units, so it is added exactly to an int64 counting units of 2^-48
     // (per chunk below 2^57.1: exact for K up to about 120000).  The merged
     // levels >= 9 go into a float, 2^-42 below the leading level.  FP64 is used
-    // only when a batch entry's result is scaled and written.
+    // only when a batch entry's result is written (two conversions, one FMA, the
+    // beta term; the power-of-two scale goes into the exponent field).
     constexpr int HALF = BN / (kEpiWarps / 4);     // columns of this warp
     const int q = warp & 3;
     const int half = (warp - 2) >> 2;              // which column slice
@@ -409,6 +421,8 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
             for (int i = 0; i < 8; ++i)
               iacc[g * 8 + i] += (long long)__float2int_rn(v[i] * up) << (48 - kBeta * L);
           } else {
+            // merged levels >= 9 stay in a float (2^-24 of a value 2^-30 below the
+            // leading level: rounding them to the int64's unit would cost 2^-49)
 #pragma unroll
             for (int i = 0; i < 8; ++i) fm[g * 8 + i] += v[i];
           }
@@ -430,8 +444,11 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
           const int col = n0 + half * HALF + j;
           const int ci = p.swap ? col : row, cj = p.swap ? row : col;
           if (row < (p.swap ? p.N : p.M) && col < (p.swap ? p.M : p.N)) {
-            const double t = (double)iacc[j] * 0x1p-48 + (double)fm[j];
-            double v = al * ldexp(t, ei + __ldg(ebb + j));
+            // one conversion; the power of two 2^(e_i + f_j - 48) goes into the
+            // exponent field (FP64 arithmetic is scarce on this part)
+            double v = pow2_scale(fma((double)fm[j], 0x1p48, (double)iacc[j]), ei + __ldg(ebb + j) - 48);
+            if (al == -1.0) v = __longlong_as_double(__double_as_longlong(v) ^ (long long)0x8000000000000000ull);
+            else if (al != 1.0) v *= al;
             if (first) {
               if (Cin && p.beta != 0.0) v = fma(p.beta, Cin[ci + (int64_t)cj * p.ldcin], v);
             } else {
