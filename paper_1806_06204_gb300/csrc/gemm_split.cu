@@ -39,6 +39,7 @@ constexpr int kBK = 64;            // one 128-byte swizzle row of BF16
 constexpr int kChunkK = 2048;      // exact-accumulation span of the level sums
 constexpr int kAcc = 8;            // TMEM accumulators: levels 2..8 exact, levels >= 9 merged
 constexpr int kARing = 4;
+constexpr int kGroupM = 8;         // tile rows per CTA group (L2 reuse of the A slices)
 constexpr int kEpiWarps = 16;      // four per TMEM lane quarter, each owning a quarter of the columns
 constexpr int kThreads = 64 + 32 * kEpiWarps;   // warp 0 TMA, warp 1 MMA, the rest epilogue
 
@@ -286,7 +287,19 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
   uint32_t* tslot = (uint32_t*)(bar + L::kBars);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * kTileM, n0 = blockIdx.x * BN;
+  // CTAs in groups of kGroupM tile rows: one wave covers kGroupM rows of A
+  // tiles (kept in L2) while B streams, instead of all of B for two rows
+  int tm, tn;
+  {
+    const int num_n = gridDim.x, num_m = gridDim.y;
+    const int pid = blockIdx.y * num_n + blockIdx.x;
+    const int first_m = pid / (kGroupM * num_n) * kGroupM;
+    const int gm = num_m - first_m < kGroupM ? num_m - first_m : kGroupM;
+    const int idx = pid - first_m * num_n;
+    tm = first_m + idx % gm;
+    tn = idx / gm;
+  }
+  const int m0 = tm * kTileM, n0 = tn * BN;
   const int nkb = (p.K + kBK - 1) / kBK;
   const int nchunk_k = (nkb + (kChunkK / kBK) - 1) / (kChunkK / kBK);
   const int b_first = p.reduce ? 0 : blockIdx.z;
@@ -342,7 +355,13 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
+    // One thread issues 180 MMAs per K block: the descriptors are formed once
+    // and advanced by adding to their start-address field (address >> 4, 14
+    // bits; shared addresses stay below 256 KB so no carry leaves the field),
+    // and the slice-pair loops are unrolled.
     const uint32_t idesc = tc::idesc_bf16_f32(kTileM, BN);
+    const uint64_t adesc0 = tc::sdesc_k128(tc::smem_u32(sA));
+    const uint64_t bdesc0 = tc::sdesc_k128(tc::smem_u32(sB));
     int kbg = 0, ia = 0;
     bool ok = true;
     for (int c = 0; c < nchunks && ok; ++c) {
@@ -355,22 +374,24 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         const int sb = kbg & 1;
         if (!(ok = tc::mbar_wait(&bfull[sb], (kbg >> 1) & 1, err))) break;
         tc::tc_fence_after();
-        const uint32_t b0 = tc::smem_u32(sB + sb * L::kBStage);
-        for (int s = 0; s < S; ++s, ++ia) {
+        const uint64_t bd = bdesc0 + (uint64_t)((sb * L::kBStage) >> 4);
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
           const int sa = ia % kARing;
           if (!(ok = tc::mbar_wait(&afull[sa], (ia / kARing) & 1, err))) break;
+          ++ia;
           tc::tc_fence_after();
-          const uint32_t a0 = tc::smem_u32(sA + sa * L::kATile);
-          for (int t = 0; s + t <= S - 1; ++t) {   // level (s+1)+(t+1) <= S+1
+          const uint64_t ad = adesc0 + (uint64_t)((sa * L::kATile) >> 4);
+#pragma unroll
+          for (int t = 0; t < S - s; ++t) {        // level (s+1)+(t+1) <= S+1
             const int lvl = s + t;                 // 0 -> level 2
             const int acc = lvl < kAcc - 1 ? lvl : kAcc - 1;
             const uint32_t d = tmem + acc * BN;
+            const uint64_t bt = bd + (uint64_t)((t * L::kBTile) >> 4);
+            const uint32_t first = (fresh >> acc) & 1u;
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-              const uint32_t accumulate = ((fresh >> acc) & 1) && kk == 0 ? 0u : 1u;
-              tc::mma_bf16(d, tc::sdesc_k128(a0 + kk * 32), tc::sdesc_k128(b0 + t * L::kBTile + kk * 32),
-                           idesc, accumulate);
-            }
+            for (int kk = 0; kk < 4; ++kk)
+              tc::mma_bf16(d, ad + 2 * kk, bt + 2 * kk, idesc, (first && kk == 0) ? 0u : 1u);
             fresh &= ~(1u << acc);
           }
           tc::mma_commit(&aempty[sa]);

@@ -46,22 +46,38 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait: about a second of polling at most, then *err is set.
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait: two seconds at most (by the global timer), then *err is set.
+// The error flag (set by a CTA that gave up) and the timer are looked at once
+// every 256 polls: a global load per poll from every waiting warp would take L2
+// bandwidth from the TMA loads.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
-  for (long long i = 0; i < (1ll << 24); ++i) {
+  const uint64_t t0 = global_ns();
+  for (uint32_t i = 0;; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (*(volatile int*)err) return false;
+    if ((i & 255u) == 255u) {
+      if (*(volatile int*)err) return false;
+      if (global_ns() - t0 > 2000000000ull) break;
+    }
   }
   atomicExch(err, 1);
   return false;
 }
 
-// Bounded wait that ignores the error flag: used on exit paths to let copies or
-// MMAs already in flight finish before their shared memory / TMEM is released.
+// Bounded wait that ignores the error flag (half a second at most): used on exit
+// paths to let copies or MMAs already in flight finish before their shared
+// memory / TMEM is released.
 __device__ __forceinline__ bool mbar_wait_drain(uint64_t* bar, uint32_t parity) {
-  for (long long i = 0; i < (1ll << 22); ++i)
+  const uint64_t t0 = global_ns();
+  for (uint32_t i = 0;; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
-  return false;
+    if ((i & 255u) == 255u && global_ns() - t0 > 500000000ull) return false;
+  }
 }
 
 // ---------------------------------------------------------------- TMA
