@@ -172,59 +172,77 @@ __device__ __forceinline__ long long fixed_point(double x, int e) {
   return (bits >> 63) ? -(long long)F : (long long)F;
 }
 
+// The S slice values d_s 2^-6s of x against the row bound 2^(ee - 1): balanced
+// digits from the least significant one up; the leading digit takes what is
+// left, |d_1| <= 32 because |N| <= 2^(6S-1).  Each is exact in FP32 and BF16
+// (at most six significant bits).
+template <int S>
+__device__ __forceinline__ void slice_values(double x, int ee, float* v) {
+  long long N = fixed_point<S>(x, ee);
+#pragma unroll
+  for (int s = S; s >= 2; --s) {
+    int d = (int)(N & 63);
+    d = d >= 32 ? d - 64 : d;
+    v[s - 1] = (float)d * __int_as_float((127 - kBeta * s) << 23);
+    N = (N - d) >> kBeta;
+  }
+  v[0] = (float)N * __int_as_float((127 - kBeta) << 23);
+}
+
 // S slices of op(X), each rows_pad x K_pad BF16, K contiguous; batch entry b at
 // out + b * S * rows_pad * K_pad, slice s (1-based) at + (s-1) * rows_pad * K_pad.
-// 32 x 32 tiles through shared memory so that both the read (along X's
-// contiguous dimension) and the write (along K) are coalesced.
+// 32 x 64 tiles through shared memory: the read runs along X's contiguous
+// dimension, and each thread writes two neighbouring K entries per plane so
+// that a warp stores whole 128-byte lines.
 template <int S>
-__global__ void slice_kernel(const double* __restrict__ X, int64_t ldx, int64_t strideX, int trans,
-                             int rows, int K, const int* __restrict__ e_in,
-                             __nv_bfloat16* __restrict__ out, int rows_pad, int K_pad,
-                             const int* __restrict__ ek, int esign) {
-  __shared__ double tile[32][33];
+__global__ void __launch_bounds__(256)
+slice_kernel(const double* __restrict__ X, int64_t ldx, int64_t strideX, int trans,
+             int rows, int K, const int* __restrict__ e_in,
+             __nv_bfloat16* __restrict__ out, int rows_pad, int K_pad,
+             const int* __restrict__ ek, int esign) {
+  __shared__ double tile[32][65];                 // [row][k]
   const double* Xb = X + blockIdx.z * strideX;
   const int* eb = e_in + blockIdx.z * rows_pad;
+  const int* ekb = ek ? ek + blockIdx.z * K_pad : nullptr;
   const size_t plane = (size_t)rows_pad * K_pad;
   __nv_bfloat16* ob = out + (size_t)blockIdx.z * S * plane;
-  const int i0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+  const int i0 = blockIdx.y * 32, k0 = blockIdx.x * 64;
   const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
-  for (int r = ty; r < 32; r += 8) {
-    double v = 0.0;
-    if (!trans) {   // tx runs along i
-      const int i = i0 + tx, k = k0 + r;
-      if (i < rows && k < K) v = Xb[i + (int64_t)k * ldx];
-      tile[tx][r] = v;
-    } else {        // tx runs along k
-      const int i = i0 + r, k = k0 + tx;
-      if (i < rows && k < K) v = Xb[k + (int64_t)i * ldx];
-      tile[r][tx] = v;
+  if (!trans) {     // rows contiguous: tx runs along i
+    const int i = i0 + tx;
+    for (int r = ty; r < 64; r += 8) {
+      const int k = k0 + r;
+      tile[tx][r] = (i < rows && k < K) ? Xb[i + (int64_t)k * ldx] : 0.0;
+    }
+  } else {          // K contiguous: tx runs along k
+    for (int r = ty; r < 32; r += 8) {
+      const int i = i0 + r;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int k = k0 + h * 32 + tx;
+        tile[r][h * 32 + tx] = (i < rows && k < K) ? Xb[k + (int64_t)i * ldx] : 0.0;
+      }
     }
   }
   __syncthreads();
+  const int kl = 2 * tx, k = k0 + kl;             // this thread's two K entries
   for (int r = ty; r < 32; r += 8) {
-    const int i = i0 + r, k = k0 + tx;
-    if (i >= rows_pad || k >= K_pad) continue;
-    // element x 2^(esign ek[k]) against the row bound 2^(e_i - 1)
-    const int ee = ek ? eb[i] - esign * ek[blockIdx.z * K_pad + k] : eb[i];
-    long long N = (i < rows) ? fixed_point<S>(tile[r][tx], ee) : 0ll;
-    __nv_bfloat16* o = ob + (size_t)i * K_pad + k;
-    // balanced digits from the least significant one up; the leading digit takes
-    // what is left, |d_1| <= 32 because |N| <= 2^(6S-1)
-    int d[S];
+    const int i = i0 + r;
+    if (i >= rows_pad) continue;
+    float va[S], vb[S];
+    if (i < rows) {
+      // element x 2^(esign ek[k]) against the row bound 2^(e_i - 1)
+      const int ea = ekb ? eb[i] - esign * ekb[k] : eb[i];
+      const int eb2 = ekb ? eb[i] - esign * ekb[k + 1] : eb[i];
+      slice_values<S>(tile[r][kl], ea, va);
+      slice_values<S>(tile[r][kl + 1], eb2, vb);
+    } else {
 #pragma unroll
-    for (int s = S; s >= 2; --s) {
-      int v = (int)(N & 63);
-      v = v >= 32 ? v - 64 : v;
-      d[s - 1] = v;
-      N = (N - v) >> kBeta;
+      for (int s = 0; s < S; ++s) va[s] = vb[s] = 0.f;
     }
-    d[0] = (int)N;
+    __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(ob + (size_t)i * K_pad + k);
 #pragma unroll
-    for (int s = 1; s <= S; ++s) {
-      // d 2^-6s is exact in FP32 and in BF16 (at most six significant bits)
-      const float v = (float)d[s - 1] * __int_as_float((127 - kBeta * s) << 23);
-      o[(s - 1) * plane] = __float2bfloat16_rn(v);
-    }
+    for (int s = 0; s < S; ++s) o[s * (plane / 2)] = __floats2bfloat162_rn(va[s], vb[s]);
   }
 }
 
@@ -542,7 +560,7 @@ cudaError_t slice_operand(const double* X, int64_t ldx, int64_t strideX, int tra
           X, ldx, strideX, 1, rows, K, e, rows_pad, ek, esign, K_pad);
   }
   ProfScope ps(kProfSlice, st, 0.0, (8.0 + 2.0 * S) * batch * rows_pad * (double)K_pad);
-  dim3 grid((unsigned)(K_pad / 32), (unsigned)(rows_pad / 32), batch);
+  dim3 grid((unsigned)(K_pad / 64), (unsigned)(rows_pad / 32), batch);
   slice_kernel<S><<<grid, dim3(32, 8), 0, st>>>(X, ldx, strideX, trans, rows, K, e, out, rows_pad,
                                                 K_pad, ek, esign);
   return cudaGetLastError();
