@@ -11,9 +11,9 @@
 //
 // Mixed precision.  FP32 runs 58x faster than FP64 on this part, so the sweeps
 // that only need to bring the columns close to orthogonal run in FP32 on a copy
-// X32 = R^T with the rotations accumulated in Z32 (one cooperative launch per
-// sweep: the n-1 rounds of the round-robin ordering are separated by a bounded
-// grid barrier).  Z is then made orthonormal in FP64 (Cholesky QR), X = R^T Z is
+// X32 = R^T with the rotations accumulated in Z32, as block Jacobi on 16-column
+// blocks (one cooperative launch per sweep, rounds separated by a bounded grid
+// barrier).  Z is then made orthonormal in FP64 (Cholesky QR), X = R^T Z is
 // formed in FP64, and FP64 sweeps (one launch per round, one CTA per column
 // pair) finish from cosines ~1e-5 in a few quadratically convergent sweeps.
 // FP32 sweeps stop when no cosine exceeds 8e-6 (25 sweeps at most).  FP64 sweeps
@@ -116,64 +116,203 @@ __device__ bool grid_barrier(unsigned* count, unsigned* gen, int* err) {
   return *(volatile int*)err == 0;
 }
 
-// One FP32 sweep: every round of the round-robin ordering, pairs distributed over
-// the blocks; rotations applied to X32 and accumulated into Z32.
+// One FP32 sweep of block Jacobi: the columns are grouped in blocks of kJB,
+// the blocks paired by the round-robin ordering, and each CTA takes one block
+// pair per round: it forms the Gram matrix G = C^T C of the pair's 2 kJB
+// columns (one pass over the rows, staged through shared memory), runs
+// kJInner cyclic Jacobi sweeps on G in shared memory (the rotation from the
+// 2x2 Gram entries of a column pair is the one-sided rotation of those two
+// columns; J^T G J keeps G current), and applies the accumulated rotation Q to
+// the pair's columns of X32 and Z32 in one more pass.  Each column is read a
+// few times per visit instead of once per rotation.  Rounds are separated by a
+// bounded grid barrier.  A rotation is counted when |g_pq| > tol sqrt(g_pp g_qq).
+constexpr int kJB = 16;                // columns per block
+constexpr int kJW = 2 * kJB;           // columns of a block pair
+constexpr int kJRows = 256;            // rows per staged chunk (one per thread when loading)
+constexpr int kJLd = kJRows + 1;       // chunk leading dimension: conflict-free column and row walks
+constexpr int kJInner = 2;             // Jacobi sweeps on G per visit
+
 __global__ void __launch_bounds__(kJacThreads)
-jacobi32_sweep_kernel(float* X, float* Z, int64_t ld, int64_t m, int n_even, int n_real, float tol,
-                      int* status, unsigned* bar, int* err) {
-  __shared__ float red[3][kJacThreads / 32];
-  __shared__ float s_c, s_s;
+jacobi32_block_sweep_kernel(float* X, float* Z, int64_t ld, int64_t m, int nb_even, int n_real,
+                            float tol, int* status, unsigned* bar, int* err) {
+  static_assert(kJacThreads == 256 && kJW == 32 && kJRows == kJacThreads, "thread mapping below");
+  __shared__ float Ct[kJW * kJLd];             // chunk, column-major: Ct[j * kJLd + r]
+  __shared__ float G[kJW][kJW + 1];
+  __shared__ float Qm[kJW][kJW + 1];
+  __shared__ __align__(16) float Q4[kJW][kJW]; // Q for the vectorised product
+  __shared__ float s_c[kJB], s_s[kJB];
+  __shared__ int s_a[kJB], s_b[kJB];
   __shared__ int s_rot;
-  const int npairs = n_even / 2;
-  for (int round = 0; round < n_even - 1; ++round) {
-    for (int i = blockIdx.x; i < npairs; i += gridDim.x) {
-      auto elem = [&](int pos) { return pos == 0 ? 0 : 1 + (pos - 1 + round) % (n_even - 1); };
-      int p = elem(i), q = elem(n_even - 1 - i);
-      if (p > q) { const int t = p; p = q; q = t; }
-      if (q >= n_real) continue;
-      float* xp = X + p * ld;
-      float* xq = X + q * ld;
-      float a = 0.f, b = 0.f, g = 0.f;
-      for (int64_t r = threadIdx.x; r < m; r += kJacThreads) {
-        const float u = xp[r], v = xq[r];
-        a = fmaf(u, u, a);
-        b = fmaf(v, v, b);
-        g = fmaf(u, v, g);
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, o);
-        b += __shfl_xor_sync(0xffffffffu, b, o);
-        g += __shfl_xor_sync(0xffffffffu, g, o);
-      }
-      const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-      if (l == 0) { red[0][w] = a; red[1][w] = b; red[2][w] = g; }
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        float sa = 0.f, sb = 0.f, sg = 0.f;
-        for (int k = 0; k < kJacThreads / 32; ++k) { sa += red[0][k]; sb += red[1][k]; sg += red[2][k]; }
-        int rot = (sg != 0.f) && (fabsf(sg) > tol * sqrtf(sa) * sqrtf(sb));
-        float c = 1.f, sn = 0.f;
-        if (rot) {
-          const float zeta = (sb - sa) / (2.f * sg);
-          const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
-          c = 1.f / sqrtf(fmaf(t, t, 1.f));
-          sn = c * t;
-          atomicAdd(status + kStatJacobiRot, 1);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int npairs = nb_even / 2;
+  for (int round = 0; round < nb_even - 1; ++round) {
+    for (int pi = blockIdx.x; pi < npairs; pi += gridDim.x) {
+      auto elem = [&](int pos) { return pos == 0 ? 0 : 1 + (pos - 1 + round) % (nb_even - 1); };
+      int P = elem(pi), Qb = elem(nb_even - 1 - pi);
+      if (P > Qb) { const int t = P; P = Qb; Qb = t; }
+      auto col = [&](int j) { return j < kJB ? P * kJB + j : Qb * kJB + (j - kJB); };
+      // chunk loader: thread = row, all 32 columns (coalesced along each column).
+      // The next chunk is fetched into registers while the current one is used.
+      float pf[kJW];
+      auto fetch = [&](const float* M, int64_t r0) {
+        const int64_t r = r0 + tid;
+#pragma unroll
+        for (int j = 0; j < kJW; ++j) {
+          const int c = col(j);
+          pf[j] = (c < n_real && r < m) ? M[(int64_t)c * ld + r] : 0.f;
         }
-        s_c = c; s_s = sn; s_rot = rot;
+      };
+      auto stage = [&]() {
+#pragma unroll
+        for (int j = 0; j < kJW; ++j) Ct[j * kJLd + tid] = pf[j];
+      };
+      // ---- 1. Gram G = C^T C: 16 row groups; thread owns the 8x8 block (bi, bj)
+      //         of G over the rows r = g (mod 16) of each chunk
+      {
+        const int g = tid >> 4, t = tid & 15, bi = t >> 2, bj = t & 3;
+        float acc[8][8];
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+          for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+        fetch(X, 0);
+        for (int64_t r0 = 0; r0 < m; r0 += kJRows) {
+          stage();
+          __syncthreads();
+          if (r0 + kJRows < m) fetch(X, r0 + kJRows);
+          for (int r = g; r < kJRows; r += 16) {
+            float va[8], vb[8];
+#pragma unroll
+            for (int a = 0; a < 8; ++a) va[a] = Ct[(8 * bi + a) * kJLd + r];
+#pragma unroll
+            for (int b = 0; b < 8; ++b) vb[b] = Ct[(8 * bj + b) * kJLd + r];
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+#pragma unroll
+              for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(va[a], vb[b], acc[a][b]);
+          }
+          __syncthreads();
+        }
+        // groups 2w and 2w+1 share warp w (lanes l and l ^ 16): fold them, then
+        // sum the 8 warps' partials through the chunk buffer
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+          for (int b = 0; b < 8; ++b) acc[a][b] += __shfl_xor_sync(0xffffffffu, acc[a][b], 16);
+        if (lane < 16)
+#pragma unroll
+          for (int a = 0; a < 8; ++a)
+#pragma unroll
+            for (int b = 0; b < 8; ++b) Ct[warp * kJW * kJW + (8 * bi + a) * kJW + (8 * bj + b)] = acc[a][b];
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int e = tid + kJacThreads * u, i = e >> 5, jj = e & 31;
+          float sum = 0.f;
+#pragma unroll
+          for (int w = 0; w < kJacThreads / 32; ++w) sum += Ct[w * kJW * kJW + e];
+          G[i][jj] = sum;
+          Qm[i][jj] = i == jj ? 1.f : 0.f;
+        }
       }
+      if (tid == 0) s_rot = 0;
       __syncthreads();
-      if (s_rot) {
-        const float c = s_c, sn = s_s;
-        float* zp = Z + p * ld;
-        float* zq = Z + q * ld;
-        for (int64_t r = threadIdx.x; r < m; r += kJacThreads) {
-          const float u = xp[r], v = xq[r];
-          xp[r] = c * u - sn * v;
-          xq[r] = fmaf(sn, u, c * v);
-          const float y = zp[r], z = zq[r];
-          zp[r] = c * y - sn * z;
-          zq[r] = fmaf(sn, y, c * z);
+      // ---- 2. cyclic Jacobi on G (round-robin over the 32 indices, 16 disjoint
+      //         rotations per step); Q accumulates the rotations
+      for (int sw = 0; sw < kJInner; ++sw) {
+        for (int step = 0; step < kJW - 1; ++step) {
+          if (tid < kJB) {
+            auto e2 = [&](int pos) { return pos == 0 ? 0 : 1 + (pos - 1 + step) % (kJW - 1); };
+            int a = e2(tid), b = e2(kJW - 1 - tid);
+            if (a > b) { const int t = a; a = b; b = t; }
+            const float ga = G[a][a], gb = G[b][b], gab = G[a][b];
+            float c = 1.f, sn = 0.f;
+            if (col(b) < n_real && gab != 0.f && fabsf(gab) > tol * sqrtf(ga) * sqrtf(gb)) {
+              const float zeta = (gb - ga) / (2.f * gab);
+              const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
+              c = 1.f / sqrtf(fmaf(t, t, 1.f));
+              sn = c * t;
+              atomicAdd(&s_rot, 1);
+            }
+            s_a[tid] = a; s_b[tid] = b; s_c[tid] = c; s_s[tid] = sn;
+          }
+          __syncthreads();
+          // rows a, b of G (J^T G): 16 rotations x 32 entries, two per thread
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int e = tid + kJacThreads * u, t = e >> 5, k = e & 31;
+            const int a = s_a[t], b = s_b[t];
+            const float c = s_c[t], sn = s_s[t];
+            const float x = G[a][k], y = G[b][k];
+            G[a][k] = c * x - sn * y;
+            G[b][k] = fmaf(sn, x, c * y);
+          }
+          __syncthreads();
+          // columns a, b of G and of Q (G J, Q J)
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int e = tid + kJacThreads * u, t = e >> 5, k = e & 31;
+            const int a = s_a[t], b = s_b[t];
+            const float c = s_c[t], sn = s_s[t];
+            const float x = G[k][a], y = G[k][b];
+            G[k][a] = c * x - sn * y;
+            G[k][b] = fmaf(sn, x, c * y);
+            const float qx = Qm[k][a], qy = Qm[k][b];
+            Qm[k][a] = c * qx - sn * qy;
+            Qm[k][b] = fmaf(sn, qx, c * qy);
+          }
+          __syncthreads();
+        }
+      }
+      const int nrot = s_rot;
+      if (tid == 0 && nrot) atomicAdd(status + kStatJacobiRot, nrot);
+      // ---- 3. X and Z columns of the pair times Q (skipped when nothing rotated):
+      //         thread computes rows 8 rt .. 8 rt + 7, columns 4 ct .. 4 ct + 3
+      if (nrot) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int e = tid + kJacThreads * u;
+          Q4[e >> 5][e & 31] = Qm[e >> 5][e & 31];
+        }
+        const int rt = tid >> 3, ct = tid & 7;
+        for (int which = 0; which < 2; ++which) {
+          float* M = which ? Z : X;
+          fetch(M, 0);
+          for (int64_t r0 = 0; r0 < m; r0 += kJRows) {
+            stage();
+            __syncthreads();
+            if (r0 + kJRows < m) fetch(M, r0 + kJRows);
+            float o[8][4];
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+#pragma unroll
+              for (int b = 0; b < 4; ++b) o[a][b] = 0.f;
+#pragma unroll 4
+            for (int k = 0; k < kJW; ++k) {
+              const float4 q = *reinterpret_cast<const float4*>(&Q4[k][4 * ct]);
+#pragma unroll
+              for (int a = 0; a < 8; ++a) {
+                const float cv = Ct[k * kJLd + 8 * rt + a];
+                o[a][0] = fmaf(cv, q.x, o[a][0]);
+                o[a][1] = fmaf(cv, q.y, o[a][1]);
+                o[a][2] = fmaf(cv, q.z, o[a][2]);
+                o[a][3] = fmaf(cv, q.w, o[a][3]);
+              }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+#pragma unroll
+              for (int b = 0; b < 4; ++b) Ct[(4 * ct + b) * kJLd + 8 * rt + a] = o[a][b];
+            __syncthreads();
+            const int64_t r = r0 + tid;
+#pragma unroll 8
+            for (int j = 0; j < kJW; ++j) {
+              const int c = col(j);
+              if (c < n_real && r < m) M[(int64_t)c * ld + r] = Ct[j * kJLd + tid];
+            }
+            __syncthreads();
+          }
         }
       }
       __syncthreads();
@@ -362,10 +501,12 @@ int eig_sym_jacobi(const double* H, int64_t ldh, int64_t n, double* V, int64_t l
     int occ = 0, dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, jacobi32_sweep_kernel, kJacThreads, 0) !=
-            cudaSuccess)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, jacobi32_block_sweep_kernel, kJacThreads,
+                                                      0) != cudaSuccess)
       return 1;
-    const int grid = (int)std::min<int64_t>(n_even / 2, (int64_t)std::max(1, occ) * sms);
+    const int nb = (int)((n + kJB - 1) / kJB);
+    const int nb_even = nb + (nb & 1);
+    const int grid = (int)std::min<int64_t>(nb_even / 2, (int64_t)std::max(1, occ) * sms);
     const float tol32 = 8e-6f;
     for (int sw = 0; sw < 25; ++sw) {
       if (cudaMemsetAsync(w.status + kStatJacobiRot, 0, sizeof(int), st) != cudaSuccess) return 1;
@@ -373,16 +514,18 @@ int eig_sym_jacobi(const double* H, int64_t ldh, int64_t n, double* V, int64_t l
       float* X32 = w.X32;
       float* Z32 = w.Z32;
       int64_t ld = n, mm = n;
-      int ne = (int)n_even, nr = (int)n;
+      int ne = nb_even, nr = (int)n;
       float tol = tol32;
       int* status = w.status;
       unsigned* bar = w.bar;
       int* err = w.err;
       void* args[] = {&X32, &Z32, &ld, &mm, &ne, &nr, &tol, &status, &bar, &err};
       {
-        ProfScope ps(kProfJacobi32, st, 18.0 * (double)n * (double)n * (double)(n_even - 1) / 2.0);
-        if (cudaLaunchCooperativeKernel((const void*)jacobi32_sweep_kernel, grid, kJacThreads, args,
-                                        0, st) != cudaSuccess)
+        // Gram and two products with Q per block pair: 6 (2 kJB)^2 m flops
+        ProfScope ps(kProfJacobi32, st,
+                     6.0 * kJW * kJW * (double)n * (double)(nb_even / 2) * (double)(nb_even - 1));
+        if (cudaLaunchCooperativeKernel((const void*)jacobi32_block_sweep_kernel, grid, kJacThreads,
+                                        args, 0, st) != cudaSuccess)
           return 1;
       }
       int rot = 0, herr = 0;
