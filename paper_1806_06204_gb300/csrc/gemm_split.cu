@@ -5,8 +5,9 @@
 // base-64 digits,
 //     x 2^-e = sum_{s=1..S} d_s 2^{-6s} (+ rounding below 2^{-6S-1}),   |d_s| <= 32,
 // each stored pre-scaled (d_s 2^{-6s}) as BF16, which holds it exactly.  A
-// product is the sum over digit pairs (s, t) with s + t <= S + 1 of BF16 x BF16
-// GEMMs.  Balanced digits make the dropped pairs and the rounding zero-mean
+// product is the sum over digit pairs (s, t) with s + t <= S + 2 of BF16 x BF16
+// GEMMs (53 for S = 9: the pairs at level S + 2 dominate the error of the ones
+// left out, so keeping them cuts it by about twenty).  Balanced digits make the dropped pairs and the rounding zero-mean
 // (truncated digits bias every term of a Gram diagonal the same way) and keep
 // |d_s d_t| <= 2^10, so a level (fixed s + t) of p pairs summed over k terms
 // stays below p k 2^10 units of its last place: exact in FP32 while that is
@@ -401,7 +402,7 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
           tc::tc_fence_after();
           const uint64_t ad = adesc0 + (uint64_t)((sa * L::kATile) >> 4);
 #pragma unroll
-          for (int t = 0; t < S - s; ++t) {        // level (s+1)+(t+1) <= S+1
+          for (int t = 0; t < (S - s + 1 < S ? S - s + 1 : S); ++t) {   // level (s+1)+(t+1) <= S+2
             const int lvl = s + t;                 // 0 -> level 2
             const int acc = lvl < kAcc - 1 ? lvl : kAcc - 1;
             const uint32_t d = tmem + acc * BN;
@@ -711,7 +712,8 @@ cudaError_t gemm_any(const GemmArgs& g, cudaStream_t st) {
   const double S = t_split->slices_s;
   const double slice_bytes = g.batch * (8.0 + 2.0 * S) * (ra + rb) * kp;
   const double out_bytes = (g.reduce ? 1 : g.batch) * 8.0 * g.M * (double)g.N * (g.beta != 0.0 ? 2 : 1);
-  const double tensor = S * (S + 1) / 2 * 2.0 * ra * rb * kp * g.batch / 0.7e15;
+  const double pairs = S * (S + 1) / 2 + (S - 1);   // s + t <= S + 2
+  const double tensor = pairs * 2.0 * ra * rb * kp * g.batch / 0.7e15;
   const double tsplit = slice_bytes / 4e12 + out_bytes / 5e12 + tensor + 30e-6;
   return tsplit < t64 ? gemm_split(g, *t_split, st) : gemm_f64(g, st);
 }

@@ -80,6 +80,31 @@ def clustered_square(n: int = 16384, cluster: int = 64, seed: int = 5000) -> Syn
     return make_matrix(n, n, s, seed)
 
 
+def clustered_square_device(n: int = 16384, cluster: int = 64, seed: int = 5000) -> SynthMatrix:
+    """The clustered n x n workload drawn on the GPU (torch, seeded generator):
+    the Haar factors of a 16384^2 matrix take minutes in numpy on the host.  Same
+    spectrum as clustered_square; U and V are not kept (A only)."""
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(seed)
+
+    def haar(k):
+        q, r = torch.linalg.qr(torch.randn(k, k, dtype=torch.float64, device="cuda", generator=g))
+        d = torch.sign(torch.diagonal(r))
+        d[d == 0] = 1.0
+        return q * d
+
+    s = np.concatenate([np.geomspace(1.0, 1e-16, n - cluster), np.full(cluster, 1e-3)])
+    s = np.sort(s)[::-1].copy()
+    U = haar(n)
+    V = haar(n)
+    A = (U * torch.from_numpy(s).cuda()) @ V.T
+    del U, V
+    A_host = np.asfortranarray(A.cpu().numpy())
+    del A
+    torch.cuda.empty_cache()
+    return SynthMatrix(A=A_host, U=None, sigma=s, V=None, seed=seed)
+
+
 def batch_sizes_and_kappas(count: int = 512, seed: int = 4000,
                            sizes=tuple(range(64, 1025, 64)),
                            log10_kappa=(2.0, 12.0)):
