@@ -39,10 +39,15 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// One round of the FP64 sweeps: one CTA per column pair.  The squared column
+// norms are tracked in nrm2 (formed afresh at the start of every sweep): a
+// rotation with t = tan(theta) changes them exactly to a - t g and b + t g, so
+// only the cross product g = x_p . x_q is formed here (one FMA per row instead
+// of three; the FP64 pipe is the bound).
 __global__ void __launch_bounds__(kJacThreads)
 jacobi_round_kernel(double* X, int64_t ldx, int64_t m, int n_even, int n_real, int round, double tol,
-                    int* status) {
-  __shared__ double red[3][kJacThreads / 32];
+                    int* status, double* nrm2) {
+  __shared__ double red[kJacThreads / 32];
   __shared__ double s_c, s_s;
   __shared__ int s_rot;
   const int i = blockIdx.x;
@@ -52,20 +57,16 @@ jacobi_round_kernel(double* X, int64_t ldx, int64_t m, int n_even, int n_real, i
   if (q >= n_real) return;
   double* xp = X + p * ldx;
   double* xq = X + q * ldx;
-  double a = 0.0, b = 0.0, g = 0.0;
-  for (int64_t r = threadIdx.x; r < m; r += kJacThreads) {
-    const double u = xp[r], v = xq[r];
-    a = fma(u, u, a);
-    b = fma(v, v, b);
-    g = fma(u, v, g);
-  }
-  a = warp_sum(a); b = warp_sum(b); g = warp_sum(g);
+  double g = 0.0;
+  for (int64_t r = threadIdx.x; r < m; r += kJacThreads) g = fma(xp[r], xq[r], g);
+  g = warp_sum(g);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) { red[0][w] = a; red[1][w] = b; red[2][w] = g; }
+  if (l == 0) red[w] = g;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double sa = 0.0, sb = 0.0, sg = 0.0;
-    for (int k = 0; k < kJacThreads / 32; ++k) { sa += red[0][k]; sb += red[1][k]; sg += red[2][k]; }
+    double sg = 0.0;
+    for (int k = 0; k < kJacThreads / 32; ++k) sg += red[k];
+    const double sa = nrm2[p], sb = nrm2[q];
     const double cosv = (sa > 0.0 && sb > 0.0) ? fabs(sg) / (sqrt(sa) * sqrt(sb)) : 0.0;
     atomicMax(status + kStatJacobiMaxCos, __float_as_int((float)cosv));
     int rot = (sg != 0.0) && (fabs(sg) > tol * sqrt(sa) * sqrt(sb));
@@ -75,6 +76,8 @@ jacobi_round_kernel(double* X, int64_t ldx, int64_t m, int n_even, int n_real, i
       const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
       c = 1.0 / sqrt(fma(t, t, 1.0));
       s = c * t;
+      nrm2[p] = fma(-t, sg, sa);
+      nrm2[q] = fma(t, sg, sb);
       atomicAdd(status + kStatJacobiRot, 1);
     }
     s_c = c; s_s = s; s_rot = rot;
@@ -447,12 +450,12 @@ cudaError_t transpose_lower(const double* R, int64_t ldr, double* X, int64_t ldx
 }
 
 cudaError_t jacobi_round(double* X, int64_t ldx, int64_t m, int64_t n_even, int64_t n_real,
-                         int round, double tol, int* status, cudaStream_t st) {
-  ProfScope ps(kProfJacobi, st, 12.0 * (double)m * (double)(n_even / 2),
+                         int round, double tol, int* status, double* nrm2, cudaStream_t st) {
+  ProfScope ps(kProfJacobi, st, 10.0 * (double)m * (double)(n_even / 2),
                32.0 * (double)m * (double)(n_even / 2));
   jacobi_round_kernel<<<(unsigned)(n_even / 2), kJacThreads, 0, st>>>(X, ldx, m, (int)n_even,
                                                                       (int)n_real, round, tol,
-                                                                      status);
+                                                                      status, nrm2);
   return cudaGetLastError();
 }
 
@@ -571,8 +574,11 @@ int eig_sym_jacobi(const double* H, int64_t ldh, int64_t n, double* V, int64_t l
   int quiet = 0;
   for (int sw = 0; sw < 40 && !converged; ++sw) {
     if (cudaMemsetAsync(w.status + kStatJacobiRot, 0, 2 * sizeof(int), st) != cudaSuccess) return 1;
+    // squared column norms afresh (w.lam is free until the Rayleigh quotients)
+    if (column_dots(X, n, X, n, n, n, w.lam, st) != cudaSuccess) return 1;
     for (int round = 0; round < n_even - 1; ++round)
-      if (jacobi_round(X, n, n, n_even, n, round, tol_strict, w.status, st) != cudaSuccess) return 1;
+      if (jacobi_round(X, n, n, n_even, n, round, tol_strict, w.status, w.lam, st) != cudaSuccess)
+        return 1;
     int rs[2] = {0, 0};
     if (cudaMemcpyAsync(rs, w.status + kStatJacobiRot, sizeof(rs), cudaMemcpyDeviceToHost, st) !=
         cudaSuccess)
