@@ -178,6 +178,18 @@ def oracle_sample(w, seed=None):
     return 1.0 / (dt * scale), dt, desc
 
 
+def max_over_ranks(x, dist):
+    """The largest value of x over all ranks (the slowest rank sets the job's time);
+    x itself without a process group."""
+    if dist is None:
+        return x
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def blas_threads():
     for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
         if os.environ.get(k, "").isdigit():
@@ -310,10 +322,7 @@ def run_batch(args, w, rank, world, dist, local):
         barrier()
     launches = zb.kernel_launches() - launches0
     ms_step = e0.elapsed_time(e1) / args.steps
-    if dist:
-        t = torch.tensor([ms_step], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = max_over_ranks(ms_step, dist)
     value = world * w["count"] / (ms_step / 1000.0)
     flops = sum(pd_model_flops(a.shape[0], a.shape[1], i.r, i.used_qr) for a, i in zip(As, infos))
 
@@ -367,10 +376,7 @@ def run_batch(args, w, rank, world, dist, local):
             host_step()
         barrier()
         e2e_s = (time.perf_counter() - t0) / args.steps
-        if dist:
-            t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks(e2e_s, dist)
         nb = sum(a.numel() for a in As) * 8
         e2e = {"value": world * w["count"] / e2e_s, "unit": "matrices/s", "h2d_bytes_per_step": nb,
                "d2h_bytes_per_step": nb + sum(x.numel() for x in Hs) * 8}
@@ -490,10 +496,7 @@ def main():
     zb.profile(False)
     launches = zb.kernel_launches() - launches0
     ms_step = e0.elapsed_time(e1) / args.steps
-    if dist:
-        t = torch.tensor([ms_step], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = max_over_ranks(ms_step, dist)
     value = world / (ms_step / 1000.0)                # matrices/s over all ranks
     flops = pd_model_flops(m, n, info.r, info.used_qr)
     acc = accuracy(w, sm, outs)
@@ -526,10 +529,7 @@ def main():
         torch.cuda.synchronize()
         barrier()
         e2e_s = (time.perf_counter() - t0) / args.steps
-        if dist:
-            t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks(e2e_s, dist)
         e2e = {"value": world / e2e_s, "unit": "matrices/s", "h2d_bytes_per_step": 8 * m * n,
                "d2h_bytes_per_step": d2h}
 
