@@ -40,6 +40,10 @@ WORKLOADS = {
                          "(kappa 1e12), r=8, QR-form then Cholesky-form iteration, eig(H) included"),
     "pd4096": dict(kind="pd", m=4096, n=4096, kappa=1e12, r=8, sample_n=384,
                    desc="Plain FP64 Zolo-PD of one 4096x4096 matrix, kappa 1e12, r=8"),
+    # r = 1: the Zolotarev step is the dynamically weighted Halley step, i.e. QDWH-PD
+    # on the same kernels (5 iterations at kappa 1e12: 2 QR form, 3 Cholesky form)
+    "qdwh4096": dict(kind="pd", m=4096, n=4096, kappa=1e12, r=1, sample_n=384,
+                     desc="QDWH-PD (Zolo-PD with r=1) of one 4096x4096 matrix, kappa 1e12"),
     "pd256": dict(kind="pd", m=256, n=256, kappa=1e8, r=3, sample_n=256,
                   desc="Plain FP64 Zolo-PD of one 256x256 matrix, kappa 1e8, r=3"),
     "svd256": dict(kind="svd", m=256, n=256, kappa=1e8, r=3, sample_n=256,

@@ -32,6 +32,7 @@ namespace zolo {
 namespace {
 
 constexpr int kJacThreads = 256;
+constexpr int kRoundThreads = 256;   // FP64 rounds (128 measured slower at n = 4096)
 constexpr double kEps = 2.220446049250313e-16;
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -44,10 +45,10 @@ __device__ __forceinline__ double warp_sum(double v) {
 // rotation with t = tan(theta) changes them exactly to a - t g and b + t g, so
 // only the cross product g = x_p . x_q is formed here (one FMA per row instead
 // of three; the FP64 pipe is the bound).
-__global__ void __launch_bounds__(kJacThreads)
+__global__ void __launch_bounds__(kRoundThreads)
 jacobi_round_kernel(double* X, int64_t ldx, int64_t m, int n_even, int n_real, int round, double tol,
                     int* status, double* nrm2) {
-  __shared__ double red[kJacThreads / 32];
+  __shared__ double red[kRoundThreads / 32];
   __shared__ double s_c, s_s;
   __shared__ int s_rot;
   const int i = blockIdx.x;
@@ -58,14 +59,14 @@ jacobi_round_kernel(double* X, int64_t ldx, int64_t m, int n_even, int n_real, i
   double* xp = X + p * ldx;
   double* xq = X + q * ldx;
   double g = 0.0;
-  for (int64_t r = threadIdx.x; r < m; r += kJacThreads) g = fma(xp[r], xq[r], g);
+  for (int64_t r = threadIdx.x; r < m; r += kRoundThreads) g = fma(xp[r], xq[r], g);
   g = warp_sum(g);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   if (l == 0) red[w] = g;
   __syncthreads();
   if (threadIdx.x == 0) {
     double sg = 0.0;
-    for (int k = 0; k < kJacThreads / 32; ++k) sg += red[k];
+    for (int k = 0; k < kRoundThreads / 32; ++k) sg += red[k];
     const double sa = nrm2[p], sb = nrm2[q];
     const double cosv = (sa > 0.0 && sb > 0.0) ? fabs(sg) / (sqrt(sa) * sqrt(sb)) : 0.0;
     atomicMax(status + kStatJacobiMaxCos, __float_as_int((float)cosv));
@@ -85,7 +86,7 @@ jacobi_round_kernel(double* X, int64_t ldx, int64_t m, int n_even, int n_real, i
   __syncthreads();
   if (!s_rot) return;
   const double c = s_c, s = s_s;
-  for (int64_t r = threadIdx.x; r < m; r += kJacThreads) {
+  for (int64_t r = threadIdx.x; r < m; r += kRoundThreads) {
     const double u = xp[r], v = xq[r];
     xp[r] = c * u - s * v;
     xq[r] = fma(s, u, c * v);
@@ -453,7 +454,7 @@ cudaError_t jacobi_round(double* X, int64_t ldx, int64_t m, int64_t n_even, int6
                          int round, double tol, int* status, double* nrm2, cudaStream_t st) {
   ProfScope ps(kProfJacobi, st, 10.0 * (double)m * (double)(n_even / 2),
                32.0 * (double)m * (double)(n_even / 2));
-  jacobi_round_kernel<<<(unsigned)(n_even / 2), kJacThreads, 0, st>>>(X, ldx, m, (int)n_even,
+  jacobi_round_kernel<<<(unsigned)(n_even / 2), kRoundThreads, 0, st>>>(X, ldx, m, (int)n_even,
                                                                       (int)n_real, round, tol,
                                                                       status, nrm2);
   return cudaGetLastError();

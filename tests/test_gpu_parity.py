@@ -92,7 +92,9 @@ def test_one_cholesky_iteration_matches_oracle(zb, handle, m, n, kappa, r):
 # ------------------------------------------------------------------ full PD
 
 @pytest.mark.parametrize("m,n,kappa,r", [(256, 256, 1e8, 3), (300, 120, 1e6, 6), (128, 128, 1e12, 8),
-                                         (77, 77, 1e2, 0), (1, 1, 1.0, 1), (65, 33, 1e4, 0)])
+                                         (77, 77, 1e2, 0), (1, 1, 1.0, 1), (65, 33, 1e4, 0),
+                                         # r = 1 is the dynamically weighted Halley step: QDWH-PD
+                                         (256, 256, 1e8, 1), (120, 80, 1e12, 1)])
 def test_pd_matches_oracle(zb, handle, m, n, kappa, r):
     sm = synth.make_matrix(m, n, synth.geometric_sigma(n, kappa), seed=1000 + m + n)
     beta = float(sm.sigma[-1])
@@ -104,8 +106,10 @@ def test_pd_matches_oracle(zb, handle, m, n, kappa, r):
     check_pd_invariants(sm.A, Qp, H)
     assert np.linalg.norm(H - Ho) <= 1e-13 * np.linalg.norm(Ho)
     assert np.linalg.norm(Qp - Qo) <= polar_tol(sm) * math.sqrt(n)
-    # per-iteration relative changes agree (the a-posteriori quantity of Algorithm 1)
-    assert np.allclose(info.delta, io.delta, rtol=1e-6, atol=1e-13)
+    # per-iteration relative changes agree (the a-posteriori quantity of Algorithm 1);
+    # late, small deltas are carried by the smallest singular directions, whose
+    # iterates differ by about eps * kappa between two correct runs
+    assert np.allclose(info.delta, io.delta, rtol=max(1e-6, 10 * EPS * kappa), atol=1e-13)
 
 
 def test_pd_alpha_from_frobenius_norm(zb, handle):
