@@ -174,6 +174,20 @@ def test_user_stream_and_leading_dimensions(zb, handle):
 
 # ------------------------------------------------------------------ SVD
 
+def test_svd_with_a_cluster_of_equal_singular_values(zb, handle):
+    # 16 equal singular values: the eigensolver's simultaneous step meets large
+    # angles there and must fall back to exact rotations; the cluster's singular
+    # vectors are only defined up to a rotation, so invariants are checked
+    n = 160
+    sig = np.sort(np.r_[np.geomspace(1.0, 1e-6, n - 16), np.full(16, 1e-2)])[::-1].copy()
+    sm = synth.make_matrix(n, n, sig, seed=1177)
+    U, S, V, info = zb.zolo_svd(handle, dev(sm.A), zb.opts(beta=float(sig[-1])))
+    U, S, V = host(U), host(S), host(V)
+    assert np.max(np.abs(S - sm.sigma)) <= 1e-12 * sm.sigma[0]
+    assert zo.svd_residual(sm.A, U, S, V) <= 1e-13 * math.sqrt(n)
+    assert zo.orthogonality(U) <= 1e-13 and zo.orthogonality(V) <= 1e-13
+
+
 @pytest.mark.parametrize("m,n,kappa,r", [(256, 256, 1e8, 3), (150, 90, 1e6, 0), (31, 31, 1e3, 2)])
 def test_svd_matches_oracle(zb, handle, m, n, kappa, r):
     sm = synth.make_matrix(m, n, synth.geometric_sigma(n, kappa), seed=1100 + m)
