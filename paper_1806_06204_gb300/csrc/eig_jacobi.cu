@@ -32,7 +32,6 @@ namespace zolo {
 namespace {
 
 constexpr int kJacThreads = 256;
-constexpr int kRoundThreads = 256;   // FP64 rounds (128 measured slower at n = 4096)
 constexpr double kEps = 2.220446049250313e-16;
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -43,13 +42,18 @@ __device__ __forceinline__ double warp_sum(double v) {
 // One round of the FP64 sweeps: one CTA per column pair.  The squared column
 // norms are tracked in nrm2 (formed afresh at the start of every sweep): a
 // rotation with t = tan(theta) changes them exactly to a - t g and b + t g, so
-// only the cross product g = x_p . x_q is formed here (one FMA per row instead
-// of three; the FP64 pipe is the bound).
-__global__ void __launch_bounds__(kRoundThreads)
+// only the cross product of the pair is formed here.  The rotations are the
+// scaled ("fast") form: column j is held as dsc[j] * x~_j, the cosine goes into
+// the scales (dsc_p <- c dsc_p, dsc_q <- c dsc_q) and each stored column takes
+// one FMA, x~_p -= t (dsc_q / dsc_p) x~_q and x~_q += t (dsc_p / dsc_q) x~_p: three
+// FP64 operations per row and pair instead of five (the FP64 pipe is the bound).
+// Near convergence c = 1 - O(t^2), so the scales stay within rounding of 1 over
+// a sweep; the caller folds them into the columns between sweeps.
+__global__ void __launch_bounds__(kJacThreads)
 jacobi_round_kernel(double* X, int64_t ldx, int64_t m, int n_even, int n_real, int round, double tol,
-                    int* status, double* nrm2) {
-  __shared__ double red[kRoundThreads / 32];
-  __shared__ double s_c, s_s;
+                    int* status, double* nrm2, double* dsc) {
+  __shared__ double red[kJacThreads / 32];
+  __shared__ double s_al, s_be;
   __shared__ int s_rot;
   const int i = blockIdx.x;
   auto elem = [&](int pos) { return pos == 0 ? 0 : 1 + (pos - 1 + round) % (n_even - 1); };
@@ -59,38 +63,47 @@ jacobi_round_kernel(double* X, int64_t ldx, int64_t m, int n_even, int n_real, i
   double* xp = X + p * ldx;
   double* xq = X + q * ldx;
   double g = 0.0;
-  for (int64_t r = threadIdx.x; r < m; r += kRoundThreads) g = fma(xp[r], xq[r], g);
+  for (int64_t r = threadIdx.x; r < m; r += kJacThreads) g = fma(xp[r], xq[r], g);
   g = warp_sum(g);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   if (l == 0) red[w] = g;
   __syncthreads();
   if (threadIdx.x == 0) {
     double sg = 0.0;
-    for (int k = 0; k < kRoundThreads / 32; ++k) sg += red[k];
+    for (int k = 0; k < kJacThreads / 32; ++k) sg += red[k];
+    const double dp = dsc[p], dq = dsc[q];
+    sg *= dp * dq;                                  // cross product of the true columns
     const double sa = nrm2[p], sb = nrm2[q];
     const double cosv = (sa > 0.0 && sb > 0.0) ? fabs(sg) / (sqrt(sa) * sqrt(sb)) : 0.0;
     atomicMax(status + kStatJacobiMaxCos, __float_as_int((float)cosv));
     int rot = (sg != 0.0) && (fabs(sg) > tol * sqrt(sa) * sqrt(sb));
-    double c = 1.0, s = 0.0;
     if (rot) {
       const double zeta = (sb - sa) / (2.0 * sg);
       const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
-      c = 1.0 / sqrt(fma(t, t, 1.0));
-      s = c * t;
+      const double c = 1.0 / sqrt(fma(t, t, 1.0));
       nrm2[p] = fma(-t, sg, sa);
       nrm2[q] = fma(t, sg, sb);
+      dsc[p] = c * dp;
+      dsc[q] = c * dq;
+      s_al = t * (dq / dp);
+      s_be = t * (dp / dq);
       atomicAdd(status + kStatJacobiRot, 1);
     }
-    s_c = c; s_s = s; s_rot = rot;
+    s_rot = rot;
   }
   __syncthreads();
   if (!s_rot) return;
-  const double c = s_c, s = s_s;
-  for (int64_t r = threadIdx.x; r < m; r += kRoundThreads) {
+  const double al = s_al, be = s_be;
+  for (int64_t r = threadIdx.x; r < m; r += kJacThreads) {
     const double u = xp[r], v = xq[r];
-    xp[r] = c * u - s * v;
-    xq[r] = fma(s, u, c * v);
+    xp[r] = fma(-al, v, u);
+    xq[r] = fma(be, u, v);
   }
+}
+
+__global__ void fill_kernel(double* d, int64_t n, double v) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) d[i] = v;
 }
 
 // Bounded grid-wide barrier for a cooperative launch (all blocks co-resident).
@@ -451,12 +464,13 @@ cudaError_t transpose_lower(const double* R, int64_t ldr, double* X, int64_t ldx
 }
 
 cudaError_t jacobi_round(double* X, int64_t ldx, int64_t m, int64_t n_even, int64_t n_real,
-                         int round, double tol, int* status, double* nrm2, cudaStream_t st) {
-  ProfScope ps(kProfJacobi, st, 10.0 * (double)m * (double)(n_even / 2),
+                         int round, double tol, int* status, double* nrm2, double* dsc,
+                         cudaStream_t st) {
+  ProfScope ps(kProfJacobi, st, 6.0 * (double)m * (double)(n_even / 2),
                32.0 * (double)m * (double)(n_even / 2));
-  jacobi_round_kernel<<<(unsigned)(n_even / 2), kRoundThreads, 0, st>>>(X, ldx, m, (int)n_even,
+  jacobi_round_kernel<<<(unsigned)(n_even / 2), kJacThreads, 0, st>>>(X, ldx, m, (int)n_even,
                                                                       (int)n_real, round, tol,
-                                                                      status, nrm2);
+                                                                      status, nrm2, dsc);
   return cudaGetLastError();
 }
 
@@ -575,10 +589,17 @@ int eig_sym_jacobi(const double* H, int64_t ldh, int64_t n, double* V, int64_t l
   int quiet = 0;
   for (int sw = 0; sw < 40 && !converged; ++sw) {
     if (cudaMemsetAsync(w.status + kStatJacobiRot, 0, 2 * sizeof(int), st) != cudaSuccess) return 1;
-    // squared column norms afresh (w.lam is free until the Rayleigh quotients)
+    // fold the previous sweep's column scales in, then the squared column norms
+    // afresh (w.lam and w.tmp are free until the Rayleigh quotients)
+    if (sw > 0 && scale_columns(X, n, n, n, w.tmp, 0, st) != cudaSuccess) return 1;
+    {
+      ProfScope ps(kProfOther, st);
+      fill_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(w.tmp, n, 1.0);
+    }
     if (column_dots(X, n, X, n, n, n, w.lam, st) != cudaSuccess) return 1;
     for (int round = 0; round < n_even - 1; ++round)
-      if (jacobi_round(X, n, n, n_even, n, round, tol_strict, w.status, w.lam, st) != cudaSuccess)
+      if (jacobi_round(X, n, n, n_even, n, round, tol_strict, w.status, w.lam, w.tmp, st) !=
+          cudaSuccess)
         return 1;
     int rs[2] = {0, 0};
     if (cudaMemcpyAsync(rs, w.status + kStatJacobiRot, sizeof(rs), cudaMemcpyDeviceToHost, st) !=
@@ -593,6 +614,7 @@ int eig_sym_jacobi(const double* H, int64_t ldh, int64_t n, double* V, int64_t l
   }
   *sweeps = total_sweeps;
   if (!converged) return 2;
+  if (n > 1 && scale_columns(X, n, n, n, w.tmp, 0, st) != cudaSuccess) return 1;
   // ---- eigenvectors (normalised columns) and Rayleigh quotients
   if (column_norms(X, n, n, n, w.lam, st) != cudaSuccess) return 1;
   if (scale_columns(X, n, n, n, w.lam, 1, st) != cudaSuccess) return 1;

@@ -222,7 +222,7 @@ cudaError_t gather_columns(const double* X, int64_t ldx, double* Y, int64_t ldy,
 cudaError_t transpose_lower(const double* R, int64_t ldr, double* X, int64_t ldx, int64_t n,
                             cudaStream_t st);
 cudaError_t jacobi_round(double* X, int64_t ldx, int64_t m, int64_t n_even, int64_t n_real, int round,
-                         double tol, int* status, double* nrm2, cudaStream_t st);
+                         double tol, int* status, double* nrm2, double* dsc, cudaStream_t st);
 
 #endif  // __CUDACC__
 
