@@ -69,24 +69,38 @@ jacobi_round_kernel(double* X, int64_t ldx, int64_t m, int n_even, int n_real, i
   if (l == 0) red[w] = g;
   __syncthreads();
   if (threadIdx.x == 0) {
+    // One lane's scalar work costs whole FP64 warp instructions on this part, so
+    // only what fixes the rotation exactly is FP64: the cosine test and the angle
+    // are formed in FP32 (an angle off by 1e-7 only slows convergence by that
+    // factor), while c = (1 + t^2)^(-1/2) for the t actually applied, the norm
+    // and scale updates are FP64 (Newton steps from FP32 seeds).
     double sg = 0.0;
     for (int k = 0; k < kJacThreads / 32; ++k) sg += red[k];
     const double dp = dsc[p], dq = dsc[q];
     sg *= dp * dq;                                  // cross product of the true columns
     const double sa = nrm2[p], sb = nrm2[q];
-    const double cosv = (sa > 0.0 && sb > 0.0) ? fabs(sg) / (sqrt(sa) * sqrt(sb)) : 0.0;
-    atomicMax(status + kStatJacobiMaxCos, __float_as_int((float)cosv));
-    int rot = (sg != 0.0) && (fabs(sg) > tol * sqrt(sa) * sqrt(sb));
+    const float fa = (float)sa, fb = (float)sb;     // below float range: left as converged
+    const float cosv = (fa > 0.f && fb > 0.f) ? fabsf((float)sg) * rsqrtf(fa) * rsqrtf(fb) : 0.f;
+    atomicMax(status + kStatJacobiMaxCos, __float_as_int(cosv));
+    const int rot = (sg != 0.0) && (cosv > (float)tol);
     if (rot) {
-      const double zeta = (sb - sa) / (2.0 * sg);
-      const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
-      const double c = 1.0 / sqrt(fma(t, t, 1.0));
+      const float zeta = (float)((sb - sa) / (2.0 * sg));
+      const float az = fabsf(zeta);
+      const float tf = (az > 1e18f ? 0.5f / az : 1.f / (az + sqrtf(fmaf(az, az, 1.f))));
+      const double t = zeta >= 0.f ? (double)tf : -(double)tf;
+      const double x = fma(t, t, 1.0);
+      double c = (double)rsqrtf((float)x);
+      c = c * fma(-0.5 * x * c, c, 1.5);
+      c = c * fma(-0.5 * x * c, c, 1.5);
+      double rp = (double)(1.f / (float)dp), rq = (double)(1.f / (float)dq);
+      rp = rp * fma(-dp, rp, 2.0); rp = rp * fma(-dp, rp, 2.0);
+      rq = rq * fma(-dq, rq, 2.0); rq = rq * fma(-dq, rq, 2.0);
       nrm2[p] = fma(-t, sg, sa);
       nrm2[q] = fma(t, sg, sb);
       dsc[p] = c * dp;
       dsc[q] = c * dq;
-      s_al = t * (dq / dp);
-      s_be = t * (dp / dq);
+      s_al = t * (dq * rp);
+      s_be = t * (dp * rq);
       atomicAdd(status + kStatJacobiRot, 1);
     }
     s_rot = rot;
