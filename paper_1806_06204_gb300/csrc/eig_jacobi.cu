@@ -161,7 +161,7 @@ constexpr int kJB = 16;                // columns per block
 constexpr int kJW = 2 * kJB;           // columns of a block pair
 constexpr int kJRows = 256;            // rows per staged chunk (one per thread when loading)
 constexpr int kJLd = kJRows + 1;       // chunk leading dimension: conflict-free column and row walks
-constexpr int kJInner = 2;             // Jacobi sweeps on G per visit
+constexpr int kJInner = 1;             // Jacobi sweeps on G per visit
 
 __global__ void __launch_bounds__(kJacThreads)
 jacobi32_block_sweep_kernel(float* X, float* Z, int64_t ld, int64_t m, int nb_even, int n_real,
