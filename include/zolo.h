@@ -54,7 +54,13 @@ typedef struct {
                       smallest r needing at most two iterations (Table 1)      */
   double alpha;    /* alpha >= sigma_max(A) (Algorithm 1 step 1); <= 0: use
                       ||A||_F, an upper bound                                  */
-  double beta;     /* 0 < beta <= sigma_min(A) (step 2); l_0 = beta / alpha   */
+  double beta;     /* 0 < beta <= sigma_min(A) (step 2); l_0 = beta / alpha.
+                      <= 0: estimated on the device (not in the paper, which
+                      assumes it known): beta = alpha / ||R^{-1}||_F with R from
+                      a Householder QR of A / alpha, a lower bound of
+                      sigma_min(A) (||R^{-1}||_F >= ||R^{-1}||_2) within a
+                      factor sqrt(n); about 2mn^2 + n^3 more flops.  Not
+                      accepted by zolo_pd_batched.                            */
   int max_iter;    /* cap on iterations, 1..8 (default 6)                    */
   int posteriori;  /* 1: after the a-priori iterations, apply the test of
                       Algorithm 1 step (d) literally and iterate while
@@ -81,7 +87,7 @@ typedef struct {
 
 typedef struct zolo_handle_s* zolo_handle_t;
 
-/* Defaults: r = 0, alpha = 1, beta = 0 (must be set), max_iter = 6,
+/* Defaults: r = 0, alpha = 1, beta = 0 (estimated), max_iter = 6,
    posteriori = 0, ns_steps = 0, prec = ZOLO_FP64, force_qr = -1. */
 void zolo_opts_default(zolo_opts_t* opts);
 

@@ -292,6 +292,17 @@ def thin_q(refl, p: int, n: int) -> np.ndarray:
     return Q
 
 
+def beta_estimate(A: np.ndarray, alpha: float) -> float:
+    """A lower bound of sigma_min(A) from the triangular factor of X0 = A / alpha.
+
+    Not in the paper (its Section 3.2 takes alpha and beta as known).  With
+    X0 = Q R, sigma_min(X0) = 1 / ||R^{-1}||_2 >= 1 / ||R^{-1}||_F, so
+    beta = alpha / ||R^{-1}||_F <= sigma_min(A), loose by at most sqrt(n)."""
+    _, R = householder_qr(np.asarray(A, dtype=np.float64) / alpha)
+    Rinv = solve_right_upper(np.eye(R.shape[0]), R)
+    return float(alpha / np.linalg.norm(Rinv))
+
+
 def cholesky_upper(Z: np.ndarray) -> np.ndarray:
     """Upper R with Z = R^T R (unblocked); raises on a non-positive pivot."""
     n = Z.shape[0]

@@ -324,17 +324,48 @@ int validate(zolo_handle_t h, const void* A, int64_t m, int64_t n, int64_t lda, 
   if (ldq < n) return -9;
   if (o) {
     if (o->r < 0 || o->r > kMaxR || !std::isfinite(o->alpha) || !std::isfinite(o->beta) ||
-        !(o->beta > 0.0) || o->max_iter < 1 || o->max_iter > kMaxIters || o->ns_steps < 0 ||
+        o->max_iter < 1 || o->max_iter > kMaxIters || o->ns_steps < 0 ||
         o->ns_steps > 4 || (o->prec != ZOLO_FP64 && o->prec != ZOLO_SPLIT_BF16) ||
         o->force_qr < -1 || o->force_qr > 1 || (o->alpha > 0.0 && o->beta > o->alpha))
       return -10;
   } else {
-    return -10;   // beta has no default
+    return -10;
   }
   return 0;
 }
 
 // The PD core on device buffers; Qp/H are written (may be internal buffers).
+// beta = alpha / ||R^{-1}||_F with R the triangular factor of a Householder QR
+// of X0 = A / alpha (the structured QR with c = 0, no explicit Q): since
+// ||R^{-1}||_F >= ||R^{-1}||_2 = 1 / sigma_min(X0), a lower bound of
+// sigma_min(A), loose by at most sqrt(n).  R^{-1} comes from the recursive
+// triangular solve with the identity as right-hand side.  Uses the workspace
+// of an r = 1 layout; returns ZOLO_ENONFINITE for a zero pivot.
+int estimate_beta(const double* A, int64_t lda, int64_t m, int64_t n, double alpha, const PdBufs& b,
+                  cudaStream_t st, double* beta) {
+  CK(cudaMemsetAsync(b.status, 0, sizeof(int) * kStatSlots, st));
+  CK(scale_copy(A, lda, b.X, m, m, n, 1.0 / alpha, st));
+  const double zero = 0.0;
+  CK(init_stacked(b.X, m, b.qr.W, b.qr.strideW, m, n, &zero, 1, st));
+  CK(structured_qr_q(b.qr, m, n, 1, b.status, st, false));
+  // R (the upper triangle of W's top n x n block; what lies below is never read)
+  // into X with ld n; the QR region is free from here on
+  CK(copy_matrix(b.qr.W, m + n, b.X, n, n, n, st));
+  CK(tri_inv_diag_blocks(b.X, n, b.ch.Rinv, b.status, st));
+  CK(init_q_identity(b.ch.Z, 0, 0, n, 1, st));
+  CholBuffers cb{b.X, 0, b.ch.Rinv, 0};
+  CK(trsm_right_upper_batched(b.ch.Z, n, cb, b.Y, 0, b.tmp, 0, n, n, 1, st));
+  CK(frob_norm2(b.Y, n, n, n, b.partials, b.norms, st));
+  double nrm2 = 0.0;
+  int hst[kStatSlots];
+  CK(cudaMemcpyAsync(&nrm2, b.norms, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(hst, b.status, sizeof(hst), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (hst[kStatNonFinite] || !(nrm2 > 0.0) || !std::isfinite(nrm2)) return ZOLO_ENONFINITE;
+  *beta = alpha / std::sqrt(nrm2);
+  return 0;
+}
+
 int pd_core(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda, double* Qp,
             int64_t ldq, double* H, int64_t ldh, const zolo_opts_t& o, zolo_info_t* info,
             cudaStream_t st, bool svd, PdBufs* out_bufs) {
@@ -354,7 +385,15 @@ int pd_core(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda,
     alpha = std::sqrt(nrm2);
     if (!(alpha > 0.0) || !std::isfinite(alpha)) return ZOLO_ENONFINITE;
   }
-  const double ell0 = std::min(1.0, o.beta / alpha);
+  double beta = o.beta;
+  if (!(beta > 0.0)) {
+    PdBufs eb;
+    const size_t bytes1 = layout(nullptr, m, n, 1, svd, &eb);
+    if (int e = ensure_ws(h, bytes1)) return e;
+    layout(h->ws, m, n, 1, svd, &eb);
+    if (int e = estimate_beta(A, lda, m, n, alpha, eb, st, &beta)) return e;
+  }
+  const double ell0 = std::min(1.0, beta / alpha);
   Schedule sch;
   if (build_schedule(ell0, r_sched, o.max_iter, &sch) != 0) return -10;
   const int r = sch.r;
@@ -823,7 +862,7 @@ int zolo_pd_batched(zolo_handle_t h, int count, const double* const* A, const in
   for (int i = 0; i < count; ++i) {
     std::memset(&info[i], 0, sizeof(zolo_info_t));
     int e = validate(h, A[i], m[i], n[i], lda[i], Qp[i], ldq[i], H[i], ldh[i], &opts[i]);
-    if (e == 0 && opts[i].posteriori) e = -10;
+    if (e == 0 && (opts[i].posteriori || !(opts[i].beta > 0.0))) e = -10;
     if (e) {
       info[i].status = e;
       return e;

@@ -83,6 +83,48 @@ chol_diag_kernel(double* Z, int64_t strideZ, int64_t n, int64_t k0, int nbk, dou
 
 }  // namespace
 
+namespace {
+
+// Upper-triangular inverse of one NB x NB diagonal block of R (one CTA per
+// block): column k of the inverse by back substitution, one thread per column.
+template <int NB>
+__global__ void __launch_bounds__(NB)
+tri_inv_kernel(const double* __restrict__ R, int64_t n, double* __restrict__ Rinv, int* status) {
+  __shared__ double S[NB][NB + 1];
+  __shared__ double Y[NB][NB + 1];
+  const int64_t k0 = (int64_t)blockIdx.x * NB;
+  const int nbk = n - k0 < NB ? (int)(n - k0) : NB;
+  const int k = threadIdx.x;
+  for (int i = 0; i < NB; ++i) S[i][k] = (i < nbk && k < nbk) ? R[(k0 + i) + (k0 + k) * n] : 0.0;
+  __syncthreads();
+  if (k < nbk) {
+    // Y(:, k) = R^{-1} e_k, rows k down to 0
+    bool bad = !(S[k][k] != 0.0);
+    Y[k][k] = bad ? 0.0 : 1.0 / S[k][k];
+    for (int i = k - 1; i >= 0; --i) {
+      double s = 0.0;
+      for (int l = i + 1; l <= k; ++l) s = fma(S[i][l], Y[l][k], s);
+      bad |= !(S[i][i] != 0.0);
+      Y[i][k] = bad ? 0.0 : -s / S[i][i];
+    }
+    if (bad) atomicOr(status + kStatNonFinite, 1);
+  }
+  __syncthreads();
+  double* Ij = Rinv + (k0 / NB) * (int64_t)(NB * NB);
+  for (int i = 0; i < NB; ++i)
+    Ij[i + k * NB] = (i < nbk && k < nbk && i <= k) ? Y[i][k] : 0.0;
+}
+
+}  // namespace
+
+cudaError_t tri_inv_diag_blocks(const double* R, int64_t n, double* Rinv, int* status,
+                                cudaStream_t st) {
+  ProfScope ps(kProfCholDiag, st);
+  tri_inv_kernel<kCholNB><<<(unsigned)((n + kCholNB - 1) / kCholNB), kCholNB, 0, st>>>(R, n, Rinv,
+                                                                                     status);
+  return cudaGetLastError();
+}
+
 cudaError_t cholesky_upper_batched(const CholBuffers& b, int64_t n, int r, int* status,
                                    cudaStream_t st) {
   constexpr int NB = kCholNB;

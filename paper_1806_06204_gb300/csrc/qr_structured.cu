@@ -538,7 +538,7 @@ int64_t qr_partial_elems(int64_t m, int r) {
 }
 
 cudaError_t structured_qr_q(const QrBuffers& b, int64_t m, int64_t n, int r, int* status,
-                            cudaStream_t st) {
+                            cudaStream_t st, bool explicit_q) {
   constexpr int NB = kQrNB, NBb = kQrBlock;
   static const bool smem_ready = [] {
     const int bytes = (int)(sizeof(double) * NB * kSmemPanelRows);
@@ -632,6 +632,7 @@ cudaError_t structured_qr_q(const QrBuffers& b, int64_t m, int64_t n, int r, int
                            m + nbb, nbb, ntr, r, 1, st)) != cudaSuccess)
       return err;
   }
+  if (!explicit_q) return cudaSuccess;
   // ---------------- explicit Q (structured ORGQR), overwriting W
   if ((err = init_q_identity(b.W, b.strideW, m, n, r, st)) != cudaSuccess) return err;
   for (int blk = nblocks - 1; blk >= 0; --blk) {

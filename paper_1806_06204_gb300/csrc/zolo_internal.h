@@ -172,9 +172,14 @@ struct QrBuffers {
 };
 // Doubles of QrBuffers::P for an m-row problem with r shifts.
 int64_t qr_partial_elems(int64_t m, int r);
-// Factor [X; sqrt(c_j) I] for j < r and overwrite W_j with the thin Q_j.
+// Factor [X; sqrt(c_j) I] for j < r and overwrite W_j with the thin Q_j
+// (explicit_q = false: leave R on and above the diagonal of W_j's top block).
 cudaError_t structured_qr_q(const QrBuffers& b, int64_t m, int64_t n, int r, int* status,
-                            cudaStream_t st);
+                            cudaStream_t st, bool explicit_q = true);
+// Inverses of the NB x NB diagonal blocks of an upper-triangular R (ld n) in the
+// layout cholesky_upper_batched leaves in Rinv; a zero pivot sets status.
+cudaError_t tri_inv_diag_blocks(const double* R, int64_t n, double* Rinv, int* status,
+                                cudaStream_t st);
 
 // ----------------------------------------------------------------- Cholesky
 constexpr int kCholNB = 64;

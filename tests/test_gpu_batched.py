@@ -114,3 +114,7 @@ def test_batched_empty_and_bad_arguments(zb, handle):
     o = zb.opts(beta=0.05, alpha=sm.sigma.max(), posteriori=True)
     _, _, infos, st = zb.zolo_pd_batched(handle, [dev(sm.A)], [o], check=False)
     assert st == -10 and infos[0].status == -10
+    # the batched call takes no beta estimate: beta must be given
+    o = zb.opts(beta=0.0, alpha=sm.sigma.max())
+    _, _, infos, st = zb.zolo_pd_batched(handle, [dev(sm.A)], [o], check=False)
+    assert st == -10 and infos[0].status == -10

@@ -121,6 +121,39 @@ def test_pd_alpha_from_frobenius_norm(zb, handle):
     assert info.ell[0] == pytest.approx(3e-5 / alpha, rel=1e-13)
 
 
+@pytest.mark.parametrize("m,n,kappa", [(256, 256, 1e8), (300, 120, 1e12), (129, 129, 10.0),
+                                       (200, 33, 1e4)])
+def test_beta_estimated_on_device(zb, handle, m, n, kappa):
+    # beta <= 0: the library estimates beta = alpha / ||R^{-1}||_F from a QR of A/alpha;
+    # the closed form is (sum_i sigma_i^{-2})^{-1/2}, between sigma_min/sqrt(n) and sigma_min
+    sm = synth.make_matrix(m, n, synth.geometric_sigma(n, kappa), seed=2000 + m + n)
+    alpha = float(sm.sigma.max())
+    Qp, H, info = zb.zolo_pd(handle, dev(sm.A), zb.opts(beta=0.0, alpha=alpha))
+    assert info.status == 0
+    beta = info.ell[0] * alpha
+    want = zo.beta_estimate(sm.A, alpha)
+    rel = 1e-10 + 100 * EPS * kappa
+    assert beta == pytest.approx(want, rel=rel)
+    s = np.sort(sm.sigma)
+    assert beta == pytest.approx(1.0 / math.sqrt(np.sum(s ** -2.0)), rel=rel)
+    assert s[0] / math.sqrt(n) * (1 - rel) <= beta <= s[0] * (1 + rel)
+    Qp, H = host(Qp), host(H)
+    check_pd_invariants(sm.A, Qp, H)
+    Qo, Ho, io = zo.zolo_pd(sm.A, alpha, want)
+    assert info.r == io.r and info.iters == io.iters
+    assert np.linalg.norm(H - Ho) <= 1e-13 * np.linalg.norm(Ho)
+    assert np.linalg.norm(Qp - Qo) <= polar_tol(sm, alpha) * math.sqrt(n)
+
+
+def test_beta_estimated_with_frobenius_alpha(zb, handle):
+    sm = synth.make_matrix(160, 96, synth.geometric_sigma(96, 1e6), seed=31)
+    A = 5.0 * sm.A
+    Qp, H, info = zb.zolo_pd(handle, dev(A), zb.opts(beta=-1.0, alpha=0.0))
+    alpha = np.linalg.norm(A)
+    assert info.ell[0] * alpha == pytest.approx(zo.beta_estimate(A, alpha), rel=1e-8)
+    check_pd_invariants(A, host(Qp), host(H))
+
+
 def test_posteriori_mode_matches_oracle(zb, handle):
     sm = synth.square_geometric(128, 1e12, seed=8)
     Qp, H, info = zb.zolo_pd(handle, dev(sm.A), zb.opts(beta=1e-12, r=8, posteriori=True))

@@ -89,3 +89,28 @@ def test_hestenes_odd_column_count():
     off = G - np.diag(np.diag(G))
     assert np.abs(off).max() < 1e-13
     assert np.allclose(np.sort(np.linalg.norm(Y, axis=0)), np.sort(np.linalg.svd(X, compute_uv=False)))
+
+
+@pytest.mark.parametrize("m,n,kappa", [(6, 6, 10.0), (40, 25, 1e6), (33, 33, 1e10)])
+def test_beta_estimate_closed_form(m, n, kappa):
+    # With X0 = A/alpha = QR the singular values of R are those of X0, so
+    # ||R^{-1}||_F^2 = sum_i (alpha/sigma_i)^2 and the estimate is
+    # (sum_i sigma_i^{-2})^{-1/2} whatever alpha is: sigma_min/sqrt(n) <= beta <= sigma_min.
+    r = rng(m * n)
+    sig = np.geomspace(1.0, 1.0 / kappa, n) * 3.0
+    U, _ = np.linalg.qr(r.standard_normal((m, n)))
+    V, _ = np.linalg.qr(r.standard_normal((n, n)))
+    A = (U * sig) @ V.T
+    want = 1.0 / math.sqrt(np.sum(sig ** -2.0))
+    for alpha in (sig.max(), 7.0 * sig.max()):
+        got = zo.beta_estimate(A, alpha)
+        assert abs(got - want) <= (1e-12 + 10 * zo.EPS * kappa) * want
+        assert sig.min() / math.sqrt(n) * (1 - 1e-9) <= got <= sig.min() * (1 + 1e-9)
+
+
+def test_beta_estimate_diagonal_and_identity():
+    d = np.array([4.0, -0.5, 2.0, 0.25])
+    assert zo.beta_estimate(np.diag(d), 4.0) == pytest.approx(1.0 / math.sqrt(np.sum(d ** -2.0)),
+                                                              rel=1e-15)
+    # all singular values equal: the estimate is sigma / sqrt(n), the loosest case
+    assert zo.beta_estimate(np.eye(9), 1.0) == pytest.approx(1.0 / 3.0, rel=1e-15)
