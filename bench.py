@@ -48,6 +48,8 @@ WORKLOADS = {
                   desc="Plain FP64 Zolo-PD of one 256x256 matrix, kappa 1e8, r=3"),
     "svd256": dict(kind="svd", m=256, n=256, kappa=1e8, r=3, sample_n=256,
                    desc="Plain FP64 Zolo-SVD of one 256x256 matrix, kappa 1e8, r=3"),
+    "svd1024": dict(kind="svd", m=1024, n=1024, kappa=1e8, r=6, sample_n=256,
+                    desc="Plain FP64 Zolo-SVD of one 1024x1024 matrix, kappa 1e8, r=6"),
     "pd16384x4096": dict(kind="pd", m=16384, n=4096, kappa=1e6, r=6, sample_n=384, tall=True,
                          desc="Zolo-PD of one 16384x4096 matrix, sigma uniform in [1e-6, 1], r=6"),
     "pd1024": dict(kind="pd", m=1024, n=1024, kappa=1e8, r=6, sample_n=256,
@@ -423,6 +425,9 @@ def main():
                     help="split: the iterations' products on the BF16 tensor cores (Ozaki slices)")
     ap.add_argument("--beta-scale", type=float, default=None,
                     help="beta = sigma_min times this (default: the workload's own, else 1)")
+    ap.add_argument("--r", type=int, default=None,
+                    help="override the workload's r; -1 = the r measured fastest on this GPU "
+                         "(tuned during the warm-up steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -463,7 +468,8 @@ def main():
     h = zb.Handle(local)
     split = args.prec == "split"
     beta_scale = args.beta_scale if args.beta_scale is not None else w.get("beta_scale", 1.0)
-    o = zb.opts(beta=float(np.min(sm.sigma)) * beta_scale, alpha=1.0, r=w["r"],
+    r_req = args.r if args.r is not None else w["r"]
+    o = zb.opts(beta=float(np.min(sm.sigma)) * beta_scale, alpha=1.0, r=r_req,
                 prec=zb.ZOLO_SPLIT_BF16 if split else zb.ZOLO_FP64, ns_steps=1 if split else 0)
     m, n = w["m"], w["n"]
 
@@ -550,7 +556,8 @@ def main():
                 "dtype": "f64" if not split else "bf16x9-slices->f64",
                 "data": "synthetic",
                 "config": {"workload": args.workload, "desc": w["desc"], "m": m, "n": n,
-                           "kappa": w["kappa"], "r": info.r, "prec": args.prec,
+                           "kappa": w["kappa"], "r": info.r, "r_requested": r_req,
+                           "prec": args.prec,
                            "beta_over_sigma_min": beta_scale,
                            "l2": "inputs larger than L2 (no flush)",
                            "parallelism": "replicas" if world > 1 else "single"},

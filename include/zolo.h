@@ -30,6 +30,7 @@ extern "C" {
 
 #define ZOLO_MAX_R 8
 #define ZOLO_MAX_ITERS 8
+#define ZOLO_R_TUNED (-1)
 
 enum {
   ZOLO_OK = 0,
@@ -39,7 +40,9 @@ enum {
   ZOLO_ECUDA = 4,      /* a CUDA runtime call failed                            */
   ZOLO_ENOMEM = 5,     /* workspace too small / device allocation failed        */
   ZOLO_EEIG = 6,       /* the Jacobi eigensolver did not converge               */
-  ZOLO_ETIMEOUT = 7    /* a bounded wait inside a tensor-core kernel expired    */
+  ZOLO_ETIMEOUT = 7,   /* a bounded wait inside a tensor-core kernel expired    */
+  ZOLO_EIO = 8,        /* a tuning-cache file could not be written or read      */
+  ZOLO_EINVAL = 9      /* a tuning-cache file is malformed or from another GPU  */
 };
 
 /* Arithmetic of the contractions.  ZOLO_FP64: plain FP64 on the FP64 FMA pipe.
@@ -51,9 +54,13 @@ enum { ZOLO_FP64 = 0, ZOLO_SPLIT_BF16 = 1 };
 
 typedef struct {
   int r;           /* order parameter, 1..8 (Eq. 6: type (2r+1, 2r)); 0 = the
-                      smallest r needing at most two iterations (Table 1)      */
+                      smallest r needing at most two iterations (Table 1);
+                      ZOLO_R_TUNED = the r measured fastest on this GPU for
+                      (m, n, prec, l_0 to the nearest decade), see
+                      zolo_tuned_r                                             */
   double alpha;    /* alpha >= sigma_max(A) (Algorithm 1 step 1); <= 0: use
-                      ||A||_F, an upper bound                                  */
+                      min(||A||_F, sqrt(||A||_1 ||A||_inf)), an upper bound
+                      (one pass over A)                                        */
   double beta;     /* 0 < beta <= sigma_min(A) (step 2); l_0 = beta / alpha.
                       <= 0: estimated on the device (not in the paper, which
                       assumes it known): beta = alpha / ||R^{-1}||_F with R from
@@ -183,6 +190,26 @@ int zolo_dgemm(zolo_handle_t handle, int transA, int transB, int64_t m, int64_t 
 int zolo_dgemm_noalloc(int transA, int transB, int64_t m, int64_t n, int64_t k, double alpha,
                        const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
                        double* C, int64_t ldc, int slices, void* stream);
+
+/* ---- r tuned by measurement (not in the paper, whose r follows Table 1:
+   there the r shifted problems run on r process groups at once; on one GPU
+   they share the chip, so fewer shifts and more iterations can be faster).
+   A zolo_pd / zolo_svd call with opts.r = ZOLO_R_TUNED looks up the handle's
+   cache under the key (m, n, prec, round(-log10 l_0)); on a miss it runs the
+   polar decomposition of its own A once for every r in 1..8 whose a-priori
+   schedule converges within max_iter, times each run with CUDA events, stores
+   the fastest r and then computes the result with it (so a first call costs
+   up to nine decompositions).  zolo_pd_batched uses a cached r for such a
+   matrix and the Table 1 rule (r = 0) when there is none.
+   zolo_tuned_r returns the cached r for a key, or 0.
+   zolo_tune_save / zolo_tune_load write and read the cache as text: a first
+   line naming the device, then one "m n prec decade r" line per key; loading
+   a file written on a device of another name returns ZOLO_EINVAL and keeps
+   the cache as it was.  Both return 0, -1/-2 for a NULL argument, or
+   ZOLO_EIO when the file cannot be written or read. */
+int zolo_tuned_r(zolo_handle_t handle, int64_t m, int64_t n, int prec, double ell0);
+int zolo_tune_save(zolo_handle_t handle, const char* path);
+int zolo_tune_load(zolo_handle_t handle, const char* path);
 
 /* Short text for a return code. */
 const char* zolo_strerror(int code);

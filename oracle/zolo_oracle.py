@@ -292,6 +292,17 @@ def thin_q(refl, p: int, n: int) -> np.ndarray:
     return Q
 
 
+def alpha_bound(A: np.ndarray) -> float:
+    """An upper bound of sigma_max(A) when none is given (Algorithm 1 step 1 takes
+    alpha >= ||A||_2 as known): the smaller of ||A||_F and sqrt(||A||_1 ||A||_inf),
+    both >= ||A||_2 (the second since ||A||_2^2 = ||A^T A||_2 <= ||A^T||_1 ||A||_1)."""
+    A = np.asarray(A, dtype=np.float64)
+    fro = math.sqrt(float(np.sum(A * A)))
+    one = float(np.max(np.sum(np.abs(A), axis=0)))
+    inf = float(np.max(np.sum(np.abs(A), axis=1)))
+    return min(fro, math.sqrt(one) * math.sqrt(inf))
+
+
 def beta_estimate(A: np.ndarray, alpha: float) -> float:
     """A lower bound of sigma_min(A) from the triangular factor of X0 = A / alpha.
 

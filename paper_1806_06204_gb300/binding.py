@@ -19,6 +19,7 @@ ZOLO_MAX_R = 8
 ZOLO_MAX_ITERS = 8
 ZOLO_FP64 = 0
 ZOLO_SPLIT_BF16 = 1
+ZOLO_R_TUNED = -1
 
 ERRORS = {1: "ZOLO_ENONFINITE", 2: "ZOLO_ECHOL", 3: "ZOLO_ENOTCONV", 4: "ZOLO_ECUDA",
           5: "ZOLO_ENOMEM", 6: "ZOLO_EEIG", 7: "ZOLO_ETIMEOUT"}
@@ -79,6 +80,11 @@ def _load():
     lib.zolo_pd_batched.argtypes = [P, I, P, P, P, P, P, P, P, P, ctypes.POINTER(ZoloOpts),
                                     ctypes.POINTER(ZoloInfo), P]
     lib.zolo_pd_batched.restype = I
+    lib.zolo_tuned_r.argtypes = [P, I64, I64, I, D]
+    lib.zolo_tuned_r.restype = I
+    for f in (lib.zolo_tune_save, lib.zolo_tune_load):
+        f.argtypes = [P, ctypes.c_char_p]
+        f.restype = I
     lib.zolo_kernel_launches.argtypes = []
     lib.zolo_kernel_launches.restype = ctypes.c_uint64
     lib.zolo_profile.argtypes = [I]
@@ -93,7 +99,8 @@ LIB = _load()
 EXPORTED = ["zolo_opts_default", "zolo_create", "zolo_destroy", "zolo_coefficients",
             "zolo_schedule", "zolo_pd", "zolo_svd", "zolo_pd_host", "zolo_svd_host",
             "zolo_strerror", "zolo_kernel_launches", "zolo_profile", "zolo_profile_read",
-            "zolo_dgemm", "zolo_dgemm_noalloc", "zolo_pd_batched"]
+            "zolo_dgemm", "zolo_dgemm_noalloc", "zolo_pd_batched", "zolo_tuned_r",
+            "zolo_tune_save", "zolo_tune_load"]
 
 
 def kernel_launches() -> int:
@@ -165,6 +172,22 @@ def schedule(ell0: float, r: int = 0, max_iter: int = 8):
     if k < 0:
         raise ZoloError(k, "zolo_schedule")
     return list(ells[:k + 1]), [bool(x) for x in qr[:k]], ru.value
+
+
+def tuned_r(handle, m: int, n: int, prec: int, ell0: float) -> int:
+    """The r the handle has measured fastest for (m, n, prec, l_0), or 0."""
+    return int(LIB.zolo_tuned_r(handle.ptr, m, n, prec, ell0))
+
+
+def tune_save(handle, path: str) -> None:
+    e = LIB.zolo_tune_save(handle.ptr, path.encode())
+    if e:
+        raise ZoloError(e, "zolo_tune_save")
+
+
+def tune_load(handle, path: str) -> int:
+    """Merge a saved tuning cache into the handle; returns the status (0 or ZOLO_E*)."""
+    return int(LIB.zolo_tune_load(handle.ptr, path.encode()))
 
 
 class Handle:

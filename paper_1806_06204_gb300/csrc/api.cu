@@ -13,13 +13,15 @@
 // together with ||X_{k+1} - X_k||_F and ||X_{k+1}||_F.  H = (Qp^T A + A^T Qp)/2
 // uses the original A (Algorithm 1 step 5).
 #include <algorithm>
+#include <array>
 #include <climits>
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <string>
 #include <vector>
-#include <algorithm>
-#include <cstdint>
 
 #include "../../include/zolo.h"
 #include "zolo_internal.h"
@@ -66,6 +68,8 @@ struct zolo_handle_s {
   size_t exp_elems = 0;
   int* err = nullptr;         // device error flag of the tensor-core kernels
   cudaEvent_t e0 = nullptr, e1 = nullptr;
+  // r measured fastest per (m, n, prec, round(-log10 l_0))
+  std::map<std::array<int64_t, 4>, int> tuned_r;
 };
 
 namespace {
@@ -323,7 +327,7 @@ int validate(zolo_handle_t h, const void* A, int64_t m, int64_t n, int64_t lda, 
   if (!Q) return -8;
   if (ldq < n) return -9;
   if (o) {
-    if (o->r < 0 || o->r > kMaxR || !std::isfinite(o->alpha) || !std::isfinite(o->beta) ||
+    if (o->r < ZOLO_R_TUNED || o->r > kMaxR || !std::isfinite(o->alpha) || !std::isfinite(o->beta) ||
         o->max_iter < 1 || o->max_iter > kMaxIters || o->ns_steps < 0 ||
         o->ns_steps > 4 || (o->prec != ZOLO_FP64 && o->prec != ZOLO_SPLIT_BF16) ||
         o->force_qr < -1 || o->force_qr > 1 || (o->alpha > 0.0 && o->beta > o->alpha))
@@ -366,23 +370,90 @@ int estimate_beta(const double* A, int64_t lda, int64_t m, int64_t n, double alp
   return 0;
 }
 
+// device name with blanks as '_' (the tuning cache file's first line)
+std::string device_tag(int dev) {
+  cudaDeviceProp p;
+  std::string tag = "unknown";
+  if (cudaGetDeviceProperties(&p, dev) == cudaSuccess) tag = p.name;
+  for (char& c : tag)
+    if (c == ' ' || c == '\t' || c == '\n') c = '_';
+  return tag;
+}
+
+std::array<int64_t, 4> tune_key(int64_t m, int64_t n, int prec, double ell0) {
+  return {m, n, prec, (int64_t)std::lround(-std::log10(ell0))};
+}
+
+int pd_core(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda, double* Qp,
+            int64_t ldq, double* H, int64_t ldh, const zolo_opts_t& o, zolo_info_t* info,
+            cudaStream_t st, bool svd, PdBufs* out_bufs);
+
+// r = ZOLO_R_TUNED: the cached r for this key, else every r whose schedule
+// converges within max_iter is run on A itself and timed, and the fastest kept.
+int tune_r(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda, double* Qp,
+           int64_t ldq, double* H, int64_t ldh, const zolo_opts_t& o, double alpha, double beta,
+           double ell0, cudaStream_t st, bool svd, PdBufs* out_bufs, int* r_out) {
+  const auto key = tune_key(m, n, o.prec, ell0);
+  const auto hit = h->tuned_r.find(key);
+  if (hit != h->tuned_r.end()) {
+    *r_out = hit->second;
+    return 0;
+  }
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  if (cudaEventCreate(&t0) != cudaSuccess || cudaEventCreate(&t1) != cudaSuccess) {
+    if (t0) cudaEventDestroy(t0);
+    return ZOLO_ECUDA;
+  }
+  float best = 0.f;
+  int best_r = 0, e = 0;
+  for (int r = 1; r <= kMaxR && !e; ++r) {
+    Schedule s;
+    if (build_schedule(ell0, r, o.max_iter, &s) != 0 || !s.converged) continue;
+    zolo_opts_t oo = o;
+    oo.r = r;
+    oo.alpha = alpha;
+    oo.beta = beta;
+    zolo_info_t ti{};
+    if (cudaEventRecord(t0, st) != cudaSuccess) { e = ZOLO_ECUDA; break; }
+    e = pd_core(h, A, m, n, lda, Qp, ldq, H, ldh, oo, &ti, st, svd, out_bufs);
+    if (e) break;
+    float ms = 0.f;
+    if (cudaEventRecord(t1, st) != cudaSuccess || cudaEventSynchronize(t1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, t0, t1) != cudaSuccess) {
+      e = ZOLO_ECUDA;
+      break;
+    }
+    if (best_r == 0 || ms < best) {
+      best = ms;
+      best_r = r;
+    }
+  }
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  if (e) return e;
+  if (best_r == 0) best_r = kMaxR;   // no schedule converges within max_iter
+  h->tuned_r[key] = best_r;
+  *r_out = best_r;
+  return 0;
+}
+
 int pd_core(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda, double* Qp,
             int64_t ldq, double* H, int64_t ldh, const zolo_opts_t& o, zolo_info_t* info,
             cudaStream_t st, bool svd, PdBufs* out_bufs) {
-  // alpha: caller's bound or ||A||_F
+  // alpha: caller's bound or min(||A||_F, sqrt(||A||_1 ||A||_inf))
   double alpha = o.alpha;
   int r_sched = o.r;
-  // workspace needs r; an upper bound (r <= 8) is taken when r = 0 until alpha is known
   if (alpha <= 0.0) {
     PdBufs tmpb;
     const size_t bytes = layout(nullptr, m, n, 1, svd, &tmpb);
     if (int e = ensure_ws(h, bytes)) return e;
     layout(h->ws, m, n, 1, svd, &tmpb);
-    CK(frob_norm2(A, lda, m, n, tmpb.partials, tmpb.norms, st));
-    double nrm2 = 0.0;
-    CK(cudaMemcpyAsync(&nrm2, tmpb.norms, sizeof(double), cudaMemcpyDeviceToHost, st));
+    // row partial sums in X (m * ceil(n / 256) <= m n), column sums in Xn
+    CK(alpha_bound_sums(A, lda, m, n, tmpb.X, tmpb.Xn, tmpb.partials, tmpb.norms, st));
+    double sums[3];
+    CK(cudaMemcpyAsync(sums, tmpb.norms, sizeof(sums), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    alpha = std::sqrt(nrm2);
+    alpha = alpha_from_sums(sums);
     if (!(alpha > 0.0) || !std::isfinite(alpha)) return ZOLO_ENONFINITE;
   }
   double beta = o.beta;
@@ -394,6 +465,10 @@ int pd_core(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda,
     if (int e = estimate_beta(A, lda, m, n, alpha, eb, st, &beta)) return e;
   }
   const double ell0 = std::min(1.0, beta / alpha);
+  if (r_sched == ZOLO_R_TUNED)
+    if (int e = tune_r(h, A, m, n, lda, Qp, ldq, H, ldh, o, alpha, beta, ell0, st, svd, out_bufs,
+                       &r_sched))
+      return e;
   Schedule sch;
   if (build_schedule(ell0, r_sched, o.max_iter, &sch) != 0) return -10;
   const int r = sch.r;
@@ -689,7 +764,7 @@ int zolo_svd(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda
   // schedule means pd_core never has to grow (and move) the workspace.
   PdBufs b{};
   int e = 0;
-  const int r_size = opts->r == 0 ? kMaxR : opts->r;
+  const int r_size = opts->r <= 0 ? kMaxR : opts->r;
   {
     const size_t bytes = layout(nullptr, m, n, r_size, true, &b);
     if ((e = ensure_ws(h, bytes)) != 0) return info->status = e;
@@ -871,26 +946,37 @@ int zolo_pd_batched(zolo_handle_t h, int count, const double* const* A, const in
   if (cudaSetDevice(h->device) != cudaSuccess) return ZOLO_ECUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaEventRecord(h->e0, st);
-  // ---- bounds and schedules (alpha <= 0: ||A_i||_F, all norms in one pass)
+  // ---- bounds and schedules (alpha <= 0: min(||A_i||_F, sqrt(||A_i||_1 ||A_i||_inf)),
+  // all sums in one pass; the scratch is reused matrix after matrix on one stream)
   std::vector<double> alpha(count);
   std::vector<Schedule> sch(count);
   {
     std::vector<int> need;
+    int64_t part_max = 0, n_max = 0;
     for (int i = 0; i < count; ++i) {
       alpha[i] = opts[i].alpha;
-      if (alpha[i] <= 0.0) need.push_back(i);
+      if (alpha[i] <= 0.0) {
+        need.push_back(i);
+        part_max = std::max(part_max, alpha_bound_part_elems(m[i], n[i]));
+        n_max = std::max(n_max, n[i]);
+      }
     }
     if (!need.empty()) {
       double* tmp = nullptr;
-      if (cudaMalloc(&tmp, sizeof(double) * (2 * need.size() + 2 * 1024)) != cudaSuccess) {
+      const size_t nsum = 3 * need.size();
+      if (cudaMalloc(&tmp, sizeof(double) * (nsum + 2 * 1024 + part_max + n_max)) != cudaSuccess) {
         cudaGetLastError();
         return ZOLO_ENOMEM;
       }
-      std::vector<double> nr(2 * need.size());
+      double* partials = tmp + nsum;
+      double* part = partials + 2 * 1024;
+      double* colsum = part + part_max;
+      std::vector<double> nr(nsum);
       int e = 0;
       for (size_t q = 0; q < need.size() && !e; ++q) {
         const int i = need[q];
-        if (frob_norm2(A[i], lda[i], m[i], n[i], tmp + 2 * need.size(), tmp + 2 * q, st) != cudaSuccess)
+        if (alpha_bound_sums(A[i], lda[i], m[i], n[i], part, colsum, partials, tmp + 3 * q, st) !=
+            cudaSuccess)
           e = ZOLO_ECUDA;
       }
       if (!e && (cudaMemcpyAsync(nr.data(), tmp, sizeof(double) * nr.size(), cudaMemcpyDeviceToHost,
@@ -899,15 +985,20 @@ int zolo_pd_batched(zolo_handle_t h, int count, const double* const* A, const in
         e = ZOLO_ECUDA;
       cudaFree(tmp);
       if (e) return e;
-      for (size_t q = 0; q < need.size(); ++q) alpha[need[q]] = std::sqrt(nr[2 * q]);
+      for (size_t q = 0; q < need.size(); ++q) alpha[need[q]] = alpha_from_sums(&nr[3 * q]);
     }
     for (int i = 0; i < count; ++i) {
       if (!(alpha[i] > 0.0) || !std::isfinite(alpha[i])) {
         info[i].status = ZOLO_ENONFINITE;
         return ZOLO_ENONFINITE;
       }
-      if (build_schedule(std::min(1.0, opts[i].beta / alpha[i]), opts[i].r, opts[i].max_iter,
-                         &sch[i]) != 0) {
+      const double ell0 = std::min(1.0, opts[i].beta / alpha[i]);
+      int ri = opts[i].r;
+      if (ri == ZOLO_R_TUNED) {
+        const auto hit = h->tuned_r.find(tune_key(m[i], n[i], opts[i].prec, ell0));
+        ri = hit != h->tuned_r.end() ? hit->second : 0;
+      }
+      if (build_schedule(ell0, ri, opts[i].max_iter, &sch[i]) != 0) {
         info[i].status = -10;
         return -10;
       }
@@ -1115,6 +1206,57 @@ int zolo_pd_batched(zolo_handle_t h, int count, const double* const* A, const in
   return worst;
 }
 
+int zolo_tuned_r(zolo_handle_t h, int64_t m, int64_t n, int prec, double ell0) {
+  if (!h || !(ell0 > 0.0 && ell0 <= 1.0)) return 0;
+  const auto hit = h->tuned_r.find(tune_key(m, n, prec, ell0));
+  return hit != h->tuned_r.end() ? hit->second : 0;
+}
+
+int zolo_tune_save(zolo_handle_t h, const char* path) {
+  if (!h) return -1;
+  if (!path) return -2;
+  FILE* f = std::fopen(path, "w");
+  if (!f) return ZOLO_EIO;
+  bool ok = std::fprintf(f, "zolo-tune 1 %s\n", device_tag(h->device).c_str()) > 0;
+  for (const auto& kv : h->tuned_r)
+    ok = ok && std::fprintf(f, "%lld %lld %lld %lld %d\n", (long long)kv.first[0],
+                            (long long)kv.first[1], (long long)kv.first[2], (long long)kv.first[3],
+                            kv.second) > 0;
+  ok = (std::fclose(f) == 0) && ok;
+  return ok ? 0 : ZOLO_EIO;
+}
+
+int zolo_tune_load(zolo_handle_t h, const char* path) {
+  if (!h) return -1;
+  if (!path) return -2;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return ZOLO_EIO;
+  char magic[32] = {0}, dev[256] = {0};
+  int version = 0;
+  int rc = 0;
+  if (std::fscanf(f, "%31s %d %255s", magic, &version, dev) != 3 ||
+      std::strcmp(magic, "zolo-tune") != 0 || version != 1 || device_tag(h->device) != dev) {
+    rc = ZOLO_EINVAL;
+  }
+  std::map<std::array<int64_t, 4>, int> got;
+  while (rc == 0) {
+    long long a, b, c, d;
+    int r;
+    const int k = std::fscanf(f, "%lld %lld %lld %lld %d", &a, &b, &c, &d, &r);
+    if (k == EOF) break;
+    if (k != 5 || r < 1 || r > kMaxR || a < 1 || b < 1 || a < b ||
+        (c != ZOLO_FP64 && c != ZOLO_SPLIT_BF16) || d < 0 || d > 400) {
+      rc = ZOLO_EINVAL;
+      break;
+    }
+    got[{a, b, c, d}] = r;
+  }
+  std::fclose(f);
+  if (rc) return rc;
+  for (const auto& kv : got) h->tuned_r[kv.first] = kv.second;
+  return 0;
+}
+
 const char* zolo_strerror(int code) {
   switch (code) {
     case ZOLO_OK: return "success";
@@ -1125,6 +1267,8 @@ const char* zolo_strerror(int code) {
     case ZOLO_ENOMEM: return "device memory allocation failed";
     case ZOLO_EEIG: return "Jacobi eigensolver did not converge";
     case ZOLO_ETIMEOUT: return "a bounded device wait expired (tensor-core pipeline)";
+    case ZOLO_EIO: return "tuning-cache file could not be written or read";
+    case ZOLO_EINVAL: return "tuning-cache file malformed or written on another GPU";
     default: return code < 0 ? "illegal argument" : "unknown error";
   }
 }

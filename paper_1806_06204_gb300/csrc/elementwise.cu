@@ -137,6 +137,66 @@ __global__ void frob_kernel(const double* __restrict__ A, int64_t lda, int64_t m
   }
 }
 
+// Row sums of |A| over a chunk of kAbsChunk columns: part[i + c m] for chunk c.
+constexpr int kAbsChunk = 256;
+
+__global__ void row_abs_partial_kernel(const double* __restrict__ A, int64_t lda, int64_t m,
+                                       int64_t n, double* __restrict__ part) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  const int64_t j0 = (int64_t)blockIdx.y * kAbsChunk;
+  const int64_t j1 = j0 + kAbsChunk < n ? j0 + kAbsChunk : n;
+  double s = 0.0;
+  for (int64_t j = j0; j < j1; ++j) s += fabs(A[i + j * lda]);
+  part[i + (int64_t)blockIdx.y * m] = s;
+}
+
+// One warp per column: colsum[j] = sum_i |A(i, j)|.
+__global__ void col_abs_kernel(const double* __restrict__ A, int64_t lda, int64_t m, int64_t n,
+                               double* __restrict__ colsum) {
+  const int64_t j = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (j >= n) return;
+  const int l = threadIdx.x & 31;
+  double s = 0.0;
+  for (int64_t i = l; i < m; i += 32) s += fabs(A[i + j * lda]);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (l == 0) colsum[j] = s;
+}
+
+__device__ __forceinline__ double block_max(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
+  }
+  return s;   // valid in thread 0
+}
+
+// out[1] = max_j colsum[j] = ||A||_1, out[2] = max_i sum_c part[i + c m] = ||A||_inf.
+__global__ void abs_norms_finish_kernel(const double* __restrict__ part, int64_t m, int nchunk,
+                                        const double* __restrict__ colsum, int64_t n,
+                                        double* __restrict__ out) {
+  __shared__ double red[32];
+  double rmax = 0.0, cmax = 0.0;
+  for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
+    double r = 0.0;
+    for (int c = 0; c < nchunk; ++c) r += part[i + c * m];
+    rmax = fmax(rmax, r);
+  }
+  for (int64_t j = threadIdx.x; j < n; j += blockDim.x) cmax = fmax(cmax, colsum[j]);
+  const double a = block_max(cmax, red);
+  const double b = block_max(rmax, red);
+  if (threadIdx.x == 0) {
+    out[1] = a;
+    out[2] = b;
+  }
+}
+
 __global__ void symmetrize_kernel(const double* __restrict__ M, int64_t ldm, double* __restrict__ H,
                                   int64_t ldh, int64_t n) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * n;
@@ -231,6 +291,36 @@ cudaError_t check_finite(const double* A, int64_t lda, int64_t m, int64_t n, int
   ProfScope ps(kProfOther, st);
   check_finite_kernel<<<grid_for(m * n), kThreads, 0, st>>>(A, lda, m, n, status);
   return cudaGetLastError();
+}
+
+int64_t alpha_bound_part_elems(int64_t m, int64_t n) {
+  return m * ((n + kAbsChunk - 1) / kAbsChunk);
+}
+
+cudaError_t alpha_bound_sums(const double* A, int64_t lda, int64_t m, int64_t n, double* part,
+                             double* colsum, double* partials, double* out, cudaStream_t st) {
+  if (cudaError_t e = frob_norm2(A, lda, m, n, partials, out, st)) return e;
+  const int nchunk = (int)((n + kAbsChunk - 1) / kAbsChunk);
+  {
+    ProfScope ps(kProfOther, st);
+    row_abs_partial_kernel<<<dim3((unsigned)((m + 255) / 256), nchunk), 256, 0, st>>>(A, lda, m, n,
+                                                                                      part);
+  }
+  {
+    ProfScope ps(kProfOther, st);
+    col_abs_kernel<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(A, lda, m, n, colsum);
+  }
+  ProfScope ps(kProfOther, st);
+  abs_norms_finish_kernel<<<1, 1024, 0, st>>>(part, m, nchunk, colsum, n, out);
+  return cudaGetLastError();
+}
+
+double alpha_from_sums(const double* sums) {
+  // ||A||_2 <= ||A||_F and ||A||_2^2 <= ||A||_1 ||A||_inf: the smaller of the two
+  const double fro = std::sqrt(sums[0]);
+  const double holder = std::sqrt(sums[1]) * std::sqrt(sums[2]);
+  if (!std::isfinite(fro)) return fro;
+  return holder < fro ? holder : fro;
 }
 
 cudaError_t frob_norm2(const double* A, int64_t lda, int64_t m, int64_t n, double* partials,

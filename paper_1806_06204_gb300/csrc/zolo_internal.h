@@ -155,6 +155,15 @@ cudaError_t check_finite(const double* A, int64_t lda, int64_t m, int64_t n, int
 // ||A||_F^2 into out[0] (via partials)
 cudaError_t frob_norm2(const double* A, int64_t lda, int64_t m, int64_t n, double* partials,
                        double* out, cudaStream_t st);
+// alpha >= sigma_max(A) when the caller gives none: sums[0] = ||A||_F^2, sums[1] =
+// ||A||_1, sums[2] = ||A||_inf (sums: 3 device doubles, written by
+// alpha_bound_sums; part: alpha_bound_part_elems(m, n) doubles, colsum: n,
+// partials: 2 * 1024), then alpha_from_sums = min(||A||_F, sqrt(||A||_1 ||A||_inf))
+// on the host.
+int64_t alpha_bound_part_elems(int64_t m, int64_t n);
+cudaError_t alpha_bound_sums(const double* A, int64_t lda, int64_t m, int64_t n, double* part,
+                             double* colsum, double* partials, double* sums, cudaStream_t st);
+double alpha_from_sums(const double* sums);
 
 // ------------------------------------------------------------ structured QR
 constexpr int kQrNB = 32;      // panel width (columns factored by one panel kernel)

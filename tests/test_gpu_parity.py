@@ -112,13 +112,27 @@ def test_pd_matches_oracle(zb, handle, m, n, kappa, r):
     assert np.allclose(info.delta, io.delta, rtol=max(1e-6, 10 * EPS * kappa), atol=1e-13)
 
 
-def test_pd_alpha_from_frobenius_norm(zb, handle):
-    sm = synth.square_geometric(96, 1e5, seed=77)
-    A = 3.0 * sm.A
-    Qp, H, info = zb.zolo_pd(handle, dev(A), zb.opts(beta=3e-5, alpha=0.0, r=5))
+@pytest.mark.parametrize("m,n,kind", [(96, 96, "dense"), (300, 40, "dense"), (700, 513, "dense"),
+                                      (96, 96, "diag"), (300, 40, "diag"), (700, 513, "diag")])
+def test_pd_alpha_from_norm_bound(zb, handle, m, n, kind):
+    # alpha <= 0: min(||A||_F, sqrt(||A||_1 ||A||_inf)).  The Frobenius norm is the
+    # smaller for the dense matrices, the Hoelder bound for the nearly diagonal ones;
+    # 700 x 513 spans several 256-column chunks of the row sums and a ragged last one
+    sig = 3.0 * synth.geometric_sigma(n, 1e5)
+    if kind == "dense":
+        A = synth.make_matrix(m, n, sig, seed=77 + n).A
+    else:
+        A = np.zeros((m, n))
+        A[:n, :n] = np.diag(sig)
+        A += 1e-7 / math.sqrt(m) * np.random.default_rng(n).standard_normal((m, n))
+    fro = np.linalg.norm(A)
+    holder = math.sqrt(np.abs(A).sum(axis=0).max() * np.abs(A).sum(axis=1).max())
+    assert (holder < fro) == (kind == "diag")
+    Qp, H, info = zb.zolo_pd(handle, dev(A), zb.opts(beta=1e-5, alpha=0.0, r=5))
     check_pd_invariants(A, host(Qp), host(H))
-    alpha = np.linalg.norm(A)
-    assert info.ell[0] == pytest.approx(3e-5 / alpha, rel=1e-13)
+    alpha = zo.alpha_bound(A)
+    assert alpha >= np.linalg.norm(A, 2)
+    assert info.ell[0] == pytest.approx(1e-5 / alpha, rel=1e-13)
 
 
 @pytest.mark.parametrize("m,n,kappa", [(256, 256, 1e8), (300, 120, 1e12), (129, 129, 10.0),
@@ -145,11 +159,11 @@ def test_beta_estimated_on_device(zb, handle, m, n, kappa):
     assert np.linalg.norm(Qp - Qo) <= polar_tol(sm, alpha) * math.sqrt(n)
 
 
-def test_beta_estimated_with_frobenius_alpha(zb, handle):
+def test_beta_estimated_with_alpha_bound(zb, handle):
     sm = synth.make_matrix(160, 96, synth.geometric_sigma(96, 1e6), seed=31)
     A = 5.0 * sm.A
     Qp, H, info = zb.zolo_pd(handle, dev(A), zb.opts(beta=-1.0, alpha=0.0))
-    alpha = np.linalg.norm(A)
+    alpha = zo.alpha_bound(A)
     assert info.ell[0] * alpha == pytest.approx(zo.beta_estimate(A, alpha), rel=1e-8)
     check_pd_invariants(A, host(Qp), host(H))
 

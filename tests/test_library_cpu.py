@@ -78,7 +78,7 @@ def test_illegal_arguments_rejected_before_device_work(zb):
     assert call(fake, P, 4, 4, 4, P, 3, P, 4, ctypes.byref(o)) == -7
     assert call(fake, P, 4, 4, 4, P, 4, P, 3, ctypes.byref(o)) == -9
     # beta <= 0 asks for the device estimate, so it is legal; -inf is not finite
-    for bad in [dict(beta=float("-inf")), dict(beta=1e-3, r=9), dict(beta=2.0, alpha=1.0),
+    for bad in [dict(beta=float("-inf")), dict(beta=1e-3, r=9), dict(beta=1e-3, r=-2), dict(beta=2.0, alpha=1.0),
                 dict(beta=1e-3, max_iter=0), dict(beta=float("nan"))]:
         ob = zb.opts(**bad)
         assert call(fake, P, 4, 4, 4, P, 4, P, 4, ctypes.byref(ob)) == -10, bad

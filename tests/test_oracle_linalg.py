@@ -114,3 +114,19 @@ def test_beta_estimate_diagonal_and_identity():
                                                               rel=1e-15)
     # all singular values equal: the estimate is sigma / sqrt(n), the loosest case
     assert zo.beta_estimate(np.eye(9), 1.0) == pytest.approx(1.0 / 3.0, rel=1e-15)
+
+
+def test_alpha_bound_exact_cases_and_upper_bound():
+    # diagonal: ||A||_1 = ||A||_inf = max |d_i| = ||A||_2, so the Hoelder bound is exact
+    d = np.array([0.5, -3.0, 2.0])
+    assert zo.alpha_bound(np.diag(d)) == pytest.approx(3.0, rel=1e-15)
+    # all ones, m x n: rank one with ||A||_2 = ||A||_F = sqrt(mn) = sqrt(||A||_1 ||A||_inf)
+    assert zo.alpha_bound(np.ones((6, 4))) == pytest.approx(math.sqrt(24.0), rel=1e-15)
+    # an orthonormal-column matrix: ||A||_2 = 1 while ||A||_F = sqrt(n)
+    Q, _ = np.linalg.qr(rng(3).standard_normal((50, 20)))
+    b = zo.alpha_bound(Q)
+    assert 1.0 - 1e-14 <= b <= math.sqrt(20.0) + 1e-12
+    for seed in range(5):
+        A = rng(seed).standard_normal((30, 17)) * rng(seed + 9).uniform(0.01, 10, 17)
+        assert zo.alpha_bound(A) >= np.linalg.norm(A, 2) * (1 - 1e-14)
+        assert zo.alpha_bound(A) <= np.linalg.norm(A) * (1 + 1e-15)
