@@ -295,7 +295,8 @@ def run_batch(args, w, rank, world, dist, local):
     mats = synth.batch(w["count"], seed=4000 + 100000 * rank)
     As = [torch.from_numpy(sm.A).cuda() for sm in mats]
     os_ = [zb.opts(beta=float(sm.sigma[-1]), alpha=1.0, r=0,
-                   prec=zb.ZOLO_SPLIT_BF16 if split else zb.ZOLO_FP64, ns_steps=1 if split else 0)
+                   prec=zb.ZOLO_SPLIT_BF16 if split else zb.ZOLO_FP64, ns_steps=1 if split else 0,
+                   chol_form=args.chol_form)
            for sm in mats]
     Qps = [zb.empty_colmajor(a.shape[0], a.shape[1]) for a in As]
     Hs = [zb.empty_colmajor(a.shape[1], a.shape[1]) for a in As]
@@ -428,6 +429,9 @@ def main():
     ap.add_argument("--r", type=int, default=None,
                     help="override the workload's r; -1 = the r measured fastest on this GPU "
                          "(tuned during the warm-up steps)")
+    ap.add_argument("--chol-form", type=int, default=0, choices=[0, 1, 2],
+                    help="Cholesky-form iterations: 1 triangular solves, 2 explicit inverse, "
+                         "0 by the flop model")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -470,7 +474,8 @@ def main():
     beta_scale = args.beta_scale if args.beta_scale is not None else w.get("beta_scale", 1.0)
     r_req = args.r if args.r is not None else w["r"]
     o = zb.opts(beta=float(np.min(sm.sigma)) * beta_scale, alpha=1.0, r=r_req,
-                prec=zb.ZOLO_SPLIT_BF16 if split else zb.ZOLO_FP64, ns_steps=1 if split else 0)
+                prec=zb.ZOLO_SPLIT_BF16 if split else zb.ZOLO_FP64, ns_steps=1 if split else 0,
+                chol_form=args.chol_form)
     m, n = w["m"], w["n"]
 
     def step():
@@ -557,6 +562,7 @@ def main():
                 "data": "synthetic",
                 "config": {"workload": args.workload, "desc": w["desc"], "m": m, "n": n,
                            "kappa": w["kappa"], "r": info.r, "r_requested": r_req,
+                           "chol_form": info.chol_form,
                            "prec": args.prec,
                            "beta_over_sigma_min": beta_scale,
                            "l2": "inputs larger than L2 (no flush)",

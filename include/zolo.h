@@ -77,6 +77,16 @@ typedef struct {
   int prec;        /* ZOLO_FP64 or ZOLO_SPLIT_BF16                            */
   int force_qr;    /* -1: QR form while (1+c_1)/(l^2+c_1) > 100, then the
                       Cholesky form; 0: Cholesky form always; 1: QR always     */
+  int chol_form;   /* how a Cholesky-form iteration applies the r factors
+                      Z_j = R_j^T R_j: 1 = the triangular solves of Algorithm 1
+                      (d), T_j = a_j (X R_j^{-1}) R_j^{-T}, 2r solves with m
+                      rows; 2 = the explicit inverse (not in the paper):
+                      W = sum_j a_j R_j^{-1} R_j^{-T} (n-row solves against I
+                      and one batch-reduced product), then X W, one product
+                      with m rows; the same rational function of X^T X, with
+                      kappa(Z_j) <= 100 on this path.  0 = whichever has fewer
+                      modelled flops: the inverse when
+                      r (3/2) n^3 + 2 m n^2 < 0.85 * 2 r m n^2 (tall X, large r) */
 } zolo_opts_t;
 
 typedef struct {
@@ -90,12 +100,16 @@ typedef struct {
                                   form after a non-positive pivot             */
   int eig_sweeps;              /* Jacobi sweeps (zolo_svd only)              */
   double ms;                   /* device time of the call (CUDA events)      */
+  int chol_form;               /* the Cholesky form the call would take (1 =
+                                  triangular solves, 2 = explicit inverse; see
+                                  zolo_opts_t.chol_form)                     */
 } zolo_info_t;
 
 typedef struct zolo_handle_s* zolo_handle_t;
 
 /* Defaults: r = 0, alpha = 1, beta = 0 (estimated), max_iter = 6,
-   posteriori = 0, ns_steps = 0, prec = ZOLO_FP64, force_qr = -1. */
+   posteriori = 0, ns_steps = 0, prec = ZOLO_FP64, force_qr = -1,
+   chol_form = 0. */
 void zolo_opts_default(zolo_opts_t* opts);
 
 /* A handle binds a device and owns the library's workspace cache.

@@ -28,7 +28,8 @@ ERRORS = {1: "ZOLO_ENONFINITE", 2: "ZOLO_ECHOL", 3: "ZOLO_ENOTCONV", 4: "ZOLO_EC
 class ZoloOpts(ctypes.Structure):
     _fields_ = [("r", ctypes.c_int), ("alpha", ctypes.c_double), ("beta", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("posteriori", ctypes.c_int),
-                ("ns_steps", ctypes.c_int), ("prec", ctypes.c_int), ("force_qr", ctypes.c_int)]
+                ("ns_steps", ctypes.c_int), ("prec", ctypes.c_int), ("force_qr", ctypes.c_int),
+                ("chol_form", ctypes.c_int)]
 
 
 class ZoloInfo(ctypes.Structure):
@@ -37,7 +38,7 @@ class ZoloInfo(ctypes.Structure):
                 ("ell", ctypes.c_double * (ZOLO_MAX_ITERS + 1)),
                 ("delta", ctypes.c_double * ZOLO_MAX_ITERS),
                 ("chol_fallbacks", ctypes.c_int), ("eig_sweeps", ctypes.c_int),
-                ("ms", ctypes.c_double)]
+                ("ms", ctypes.c_double), ("chol_form", ctypes.c_int)]
 
 
 class KStat(ctypes.Structure):
@@ -137,20 +138,23 @@ class Info:
     chol_fallbacks: int
     eig_sweeps: int
     ms: float
+    chol_form: int
 
     @staticmethod
     def from_c(ci: ZoloInfo) -> "Info":
         k = ci.iters
         return Info(ci.status, k, ci.r, [bool(x) for x in ci.used_qr[:k]], list(ci.ell[:k + 1]),
-                    list(ci.delta[:k]), ci.chol_fallbacks, ci.eig_sweeps, ci.ms)
+                    list(ci.delta[:k]), ci.chol_fallbacks, ci.eig_sweeps, ci.ms, ci.chol_form)
 
 
 def opts(beta: float, alpha: float = 1.0, r: int = 0, max_iter: int = 6, posteriori: bool = False,
-         ns_steps: int = 0, prec: int = ZOLO_FP64, force_qr: int = -1) -> ZoloOpts:
+         ns_steps: int = 0, prec: int = ZOLO_FP64, force_qr: int = -1,
+         chol_form: int = 0) -> ZoloOpts:
     o = ZoloOpts()
     LIB.zolo_opts_default(ctypes.byref(o))
     o.r, o.alpha, o.beta, o.max_iter = r, alpha, beta, max_iter
     o.posteriori, o.ns_steps, o.prec, o.force_qr = int(posteriori), ns_steps, prec, force_qr
+    o.chol_form = chol_form
     return o
 
 

@@ -197,6 +197,15 @@ __global__ void abs_norms_finish_kernel(const double* __restrict__ part, int64_t
   }
 }
 
+// W(i, j) = W(j, i) for i > j: the lower triangle from the upper one.
+__global__ void mirror_upper_kernel(double* __restrict__ W, int64_t ldw, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e % n, j = e / n;
+    if (i > j) W[i + j * ldw] = W[j + i * ldw];
+  }
+}
+
 __global__ void symmetrize_kernel(const double* __restrict__ M, int64_t ldm, double* __restrict__ H,
                                   int64_t ldh, int64_t n) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * n;
@@ -276,6 +285,12 @@ cudaError_t combine(const double* X, int64_t ldx, double* Xn, int64_t ldxn, int6
   }
   ProfScope ps(kProfOther, st);
   finish_pairs_kernel<<<1, 1024, 0, st>>>(partials, kReduceBlocks, norms);
+  return cudaGetLastError();
+}
+
+cudaError_t mirror_upper(double* W, int64_t ldw, int64_t n, cudaStream_t st) {
+  ProfScope ps(kProfOther, st);
+  mirror_upper_kernel<<<grid_for(n * n), kThreads, 0, st>>>(W, ldw, n);
   return cudaGetLastError();
 }
 

@@ -148,6 +148,8 @@ cudaError_t combine(const double* X, int64_t ldx, double* Xn, int64_t ldxn, int6
                     double mhat, const double* T, int64_t ldt, int64_t strideT, const double* coef,
                     int nt, double* partials, double* norms, int* status, cudaStream_t st);
 // H = (M + M^T) / 2
+// W(i, j) = W(j, i) for i > j (n x n, ld ldw): a symmetric W from its upper triangle
+cudaError_t mirror_upper(double* W, int64_t ldw, int64_t n, cudaStream_t st);
 cudaError_t symmetrize(const double* M, int64_t ldm, double* H, int64_t ldh, int64_t n,
                        cudaStream_t st);
 cudaError_t check_finite(const double* A, int64_t lda, int64_t m, int64_t n, int* status,

@@ -93,6 +93,22 @@ def test_batched_equals_single_calls_bit_for_bit(zb, handle):
         assert np.array_equal(hh.cpu().numpy(), h1.cpu().numpy())
 
 
+def test_batched_inverse_cholesky_form_equals_single_calls(zb, handle):
+    shapes = [(600, 150), (128, 128), (333, 97)]
+    mats = _case(shapes, [1e6, 1e9, 1e3], 400)
+    os = [zb.opts(beta=0.5 / 1e6, alpha=0.0, r=6), zb.opts(beta=0.5 / 1e9, r=8, chol_form=2),
+          zb.opts(beta=0.5 / 1e3, r=4, chol_form=1)]
+    As = [dev(sm.A) for sm in mats]
+    Qps, Hs, infos, st = zb.zolo_pd_batched(handle, As, os)
+    assert st == 0
+    for sm, a, o, q, hh, inf in zip(mats, As, os, Qps, Hs, infos):
+        _check(zb, sm, q, hh, o.beta / (o.alpha if o.alpha > 0 else 1.0))
+        q1, h1, inf1 = zb.zolo_pd(handle, a, o)
+        assert inf.iters == inf1.iters and inf.r == inf1.r
+        assert np.array_equal(q.cpu().numpy(), q1.cpu().numpy())
+        assert np.array_equal(hh.cpu().numpy(), h1.cpu().numpy())
+
+
 def test_batched_split_precision_invariants(zb, handle):
     shapes = [(256, 256), (192, 128), (128, 128)]
     mats = _case(shapes, [1e8, 1e3, 1e14], 300)

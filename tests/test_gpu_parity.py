@@ -77,11 +77,14 @@ def test_one_qr_iteration_matches_oracle(zb, handle, m, n, kappa, r):
     assert err < 1e-13 + 50 * EPS * amp, err
 
 
+@pytest.mark.parametrize("form", [1, 2])
 @pytest.mark.parametrize("m,n,kappa,r", [(64, 64, 5.0, 3), (200, 65, 20.0, 5), (33, 1, 1.5, 1),
-                                         (129, 129, 50.0, 8)])
-def test_one_cholesky_iteration_matches_oracle(zb, handle, m, n, kappa, r):
+                                         (129, 129, 50.0, 8), (300, 130, 30.0, 2)])
+def test_one_cholesky_iteration_matches_oracle(zb, handle, m, n, kappa, r, form):
+    # form 1: the triangular solves of Algorithm 1 (d); form 2: X sum_j a_j Z_j^{-1}
+    # through explicit R_j^{-1} (the same rational function of X^T X)
     sm = synth.make_matrix(m, n, synth.geometric_sigma(n, kappa), seed=2100 + m)
-    o = zb.opts(beta=1.0 / kappa, r=r, max_iter=1, force_qr=0)
+    o = zb.opts(beta=1.0 / kappa, r=r, max_iter=1, force_qr=0, chol_form=form)
     X1, _, info = zb.zolo_pd(handle, dev(sm.A), o)
     co = zo.zolotarev_coeffs(1.0 / kappa, r)
     ref = zo.zolo_step_chol(sm.A, co)
@@ -110,6 +113,22 @@ def test_pd_matches_oracle(zb, handle, m, n, kappa, r):
     # late, small deltas are carried by the smallest singular directions, whose
     # iterates differ by about eps * kappa between two correct runs
     assert np.allclose(info.delta, io.delta, rtol=max(1e-6, 10 * EPS * kappa), atol=1e-13)
+
+
+@pytest.mark.parametrize("m,n,kappa,r,form", [(700, 200, 1e6, 6, 0), (256, 256, 1e12, 8, 2),
+                                              (520, 130, 1e8, 2, 2), (190, 190, 1e4, 3, 1)])
+def test_pd_inverse_cholesky_form_matches_oracle(zb, handle, m, n, kappa, r, form):
+    # 700 x 200 with r = 6: the flop model picks the inverse form by itself
+    sm = synth.make_matrix(m, n, synth.geometric_sigma(n, kappa), seed=3000 + m + n)
+    beta = float(sm.sigma[-1])
+    Qp, H, info = zb.zolo_pd(handle, dev(sm.A), zb.opts(beta=beta, r=r, chol_form=form))
+    Qo, Ho, io = zo.zolo_pd(sm.A, 1.0, beta, r=r)
+    Qp, H = host(Qp), host(H)
+    assert info.iters == io.iters and info.used_qr == io.used_qr and not all(io.used_qr)
+    assert info.chol_form == (form or 2)
+    check_pd_invariants(sm.A, Qp, H)
+    assert np.linalg.norm(H - Ho) <= 1e-13 * np.linalg.norm(Ho)
+    assert np.linalg.norm(Qp - Qo) <= polar_tol(sm) * math.sqrt(n)
 
 
 @pytest.mark.parametrize("m,n,kind", [(96, 96, "dense"), (300, 40, "dense"), (700, 513, "dense"),

@@ -75,12 +75,15 @@ def test_split_integer_products_are_exact(zb, handle):
     assert np.array_equal(C.cpu().numpy(), A @ B)
 
 
-@pytest.mark.parametrize("m,n,kappa,r", [(256, 256, 1e8, 3), (300, 160, 1e6, 6), (384, 384, 1e12, 8)])
-def test_split_pd_meets_invariants_and_matches_oracle(zb, handle, m, n, kappa, r):
+@pytest.mark.parametrize("m,n,kappa,r,form", [(256, 256, 1e8, 3, 1), (300, 160, 1e6, 6, 1),
+                                              (384, 384, 1e12, 8, 1), (384, 384, 1e12, 8, 2),
+                                              (800, 200, 1e6, 6, 0)])
+def test_split_pd_meets_invariants_and_matches_oracle(zb, handle, m, n, kappa, r, form):
+    # form 2 / the 800 x 200 auto case: Cholesky-form iterations through W = sum_j a_j Z_j^{-1}
     sm = synth.make_matrix(m, n, synth.geometric_sigma(n, kappa), seed=3100 + m)
     beta = float(sm.sigma[-1])
     Qp, H, info = zb.zolo_pd(handle, dev(sm.A), zb.opts(beta=beta, r=r, prec=zb.ZOLO_SPLIT_BF16,
-                                                         ns_steps=1))
+                                                         ns_steps=1, chol_form=form))
     Qo, Ho, io = zo.zolo_pd(sm.A, 1.0, beta, r=r, ns_steps=1)
     Qp, H = Qp.cpu().numpy(), H.cpu().numpy()
     assert info.iters == io.iters and info.used_qr == io.used_qr
