@@ -432,6 +432,11 @@ def main():
     ap.add_argument("--chol-form", type=int, default=0, choices=[0, 1, 2],
                     help="Cholesky-form iterations: 1 triangular solves, 2 explicit inverse, "
                          "0 by the flop model")
+    ap.add_argument("--autotune", dest="autotune", action="store_true", default=True,
+                    help="measure the contraction kernels per shape during the warm-up steps "
+                         "(default)")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="built-in kernel rules only")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -470,6 +475,8 @@ def main():
     sm = make_input(w, seed=2000 + rank)
     A = torch.from_numpy(sm.A).cuda()
     h = zb.Handle(local)
+    if args.autotune:
+        zb.autotune(h, True)
     split = args.prec == "split"
     beta_scale = args.beta_scale if args.beta_scale is not None else w.get("beta_scale", 1.0)
     r_req = args.r if args.r is not None else w["r"]
@@ -488,6 +495,8 @@ def main():
     for _ in range(args.warmup):
         outs, info = step()
     torch.cuda.synchronize()
+    if args.autotune:
+        zb.autotune(h, False)   # the timed steps use the kept kernels
 
     def barrier():
         if dist:
@@ -562,7 +571,7 @@ def main():
                 "data": "synthetic",
                 "config": {"workload": args.workload, "desc": w["desc"], "m": m, "n": n,
                            "kappa": w["kappa"], "r": info.r, "r_requested": r_req,
-                           "chol_form": info.chol_form,
+                           "chol_form": info.chol_form, "autotune": bool(args.autotune),
                            "prec": args.prec,
                            "beta_over_sigma_min": beta_scale,
                            "l2": "inputs larger than L2 (no flush)",

@@ -216,11 +216,29 @@ int zolo_dgemm_noalloc(int transA, int transB, int64_t m, int64_t n, int64_t k, 
    up to nine decompositions).  zolo_pd_batched uses a cached r for such a
    matrix and the Table 1 rule (r = 0) when there is none.
    zolo_tuned_r returns the cached r for a key, or 0.
-   zolo_tune_save / zolo_tune_load write and read the cache as text: a first
-   line naming the device, then one "m n prec decade r" line per key; loading
-   a file written on a device of another name returns ZOLO_EINVAL and keeps
-   the cache as it was.  Both return 0, -1/-2 for a NULL argument, or
-   ZOLO_EIO when the file cannot be written or read. */
+
+   ---- Contraction kernels tuned by measurement.  zolo_autotune(h, 1): from
+   then on, every zolo_pd / zolo_svd / zolo_dgemm call on h that meets a
+   contraction shape (M, N, K, batch, transposes, triangular-structure flags,
+   slice count) for the first time runs it once with each candidate kernel
+   (FP64 tiles 64x64, 32x128, 32x64; split-K in 2, 4 or 8 slices with a
+   deterministic reduction; the split tensor-core path when opts.prec asks for
+   it) into a scratch output, timed with CUDA events, and keeps the fastest
+   for that shape; the call's own outputs are written once, by the kept
+   kernel.  zolo_autotune(h, 0) stops measuring; choices already made stay in
+   use.  Without choices the built-in rules apply (the split path where its
+   cost model predicts a gain, else the 64x64 FP64 tile, 32x128 for M <= 32).
+   zolo_pd_batched always uses the built-in rules.  A tuned kernel may sum in
+   another order than the built-in one: results agree to rounding, not bit for
+   bit.  Returns 0, -1 (NULL handle) or -2 (enable not 0/1).
+
+   zolo_tune_save / zolo_tune_load write and read both caches as text: a first
+   line "zolo-tune 2 <device name>", then "r m n prec decade r" lines and
+   "g M N K batch flags slices kernel" lines; loading a file written on a
+   device of another name, or any malformed line, returns ZOLO_EINVAL and
+   keeps the caches as they were.  Both return 0, -1/-2 for a NULL argument,
+   or ZOLO_EIO when the file cannot be written or read. */
+int zolo_autotune(zolo_handle_t handle, int enable);
 int zolo_tuned_r(zolo_handle_t handle, int64_t m, int64_t n, int prec, double ell0);
 int zolo_tune_save(zolo_handle_t handle, const char* path);
 int zolo_tune_load(zolo_handle_t handle, const char* path);

@@ -81,6 +81,8 @@ def _load():
     lib.zolo_pd_batched.argtypes = [P, I, P, P, P, P, P, P, P, P, ctypes.POINTER(ZoloOpts),
                                     ctypes.POINTER(ZoloInfo), P]
     lib.zolo_pd_batched.restype = I
+    lib.zolo_autotune.argtypes = [P, I]
+    lib.zolo_autotune.restype = I
     lib.zolo_tuned_r.argtypes = [P, I64, I64, I, D]
     lib.zolo_tuned_r.restype = I
     for f in (lib.zolo_tune_save, lib.zolo_tune_load):
@@ -101,7 +103,7 @@ EXPORTED = ["zolo_opts_default", "zolo_create", "zolo_destroy", "zolo_coefficien
             "zolo_schedule", "zolo_pd", "zolo_svd", "zolo_pd_host", "zolo_svd_host",
             "zolo_strerror", "zolo_kernel_launches", "zolo_profile", "zolo_profile_read",
             "zolo_dgemm", "zolo_dgemm_noalloc", "zolo_pd_batched", "zolo_tuned_r",
-            "zolo_tune_save", "zolo_tune_load"]
+            "zolo_tune_save", "zolo_tune_load", "zolo_autotune"]
 
 
 def kernel_launches() -> int:
@@ -176,6 +178,13 @@ def schedule(ell0: float, r: int = 0, max_iter: int = 8):
     if k < 0:
         raise ZoloError(k, "zolo_schedule")
     return list(ells[:k + 1]), [bool(x) for x in qr[:k]], ru.value
+
+
+def autotune(handle, enable: bool) -> None:
+    """Measure the contraction kernels of shapes met from now on (see zolo.h)."""
+    e = LIB.zolo_autotune(handle.ptr, int(enable))
+    if e:
+        raise ZoloError(e, "zolo_autotune")
 
 
 def tuned_r(handle, m: int, n: int, prec: int, ell0: float) -> int:

@@ -70,6 +70,8 @@ struct zolo_handle_s {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   // r measured fastest per (m, n, prec, round(-log10 l_0))
   std::map<std::array<int64_t, 4>, int> tuned_r;
+  // contraction kernel measured fastest per shape (zolo_autotune)
+  GemmTuner tuner;
 };
 
 namespace {
@@ -796,6 +798,7 @@ int zolo_pd(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda,
   std::memset(info, 0, sizeof(*info));
   if (cudaSetDevice(h->device) != cudaSuccess) return info->status = ZOLO_ECUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  TunerScope ts(&h->tuner);
   cudaEventRecord(h->e0, st);
   int e = pd_core(h, A, m, n, lda, Qp, ldq, H, ldh, *opts, info, st, false, nullptr);
   cudaEventRecord(h->e1, st);
@@ -817,6 +820,7 @@ int zolo_svd(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda
   std::memset(info, 0, sizeof(*info));
   if (cudaSetDevice(h->device) != cudaSuccess) return info->status = ZOLO_ECUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  TunerScope ts(&h->tuner);
   cudaEventRecord(h->e0, st);
   // Qp and H go to internal buffers carved ahead of the union region; their
   // offsets do not depend on r, and sizing with r = 8 when r is chosen by the
@@ -961,6 +965,7 @@ int zolo_dgemm(zolo_handle_t h, int transA, int transB, int64_t m, int64_t n, in
   if (slices != 0 && slices != 8 && slices != 9) return -16;
   if (cudaSetDevice(h->device) != cudaSuccess) return ZOLO_ECUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  TunerScope ts(&h->tuner);
   GemmArgs g;
   g.M = (int)m; g.N = (int)n; g.K = (int)k; g.transA = transA; g.transB = transB;
   g.A = A; g.lda = lda; g.B = B; g.ldb = ldb;
@@ -993,6 +998,8 @@ int zolo_pd_batched(zolo_handle_t h, int count, const double* const* A, const in
   if (count < 0) return -2;
   if (count == 0) return 0;
   if (!A || !m || !n || !lda || !Qp || !ldq || !H || !ldh || !opts || !info) return -3;
+  // the lanes run concurrently and are graph-captured: built-in kernel rules only
+  TunerScope no_tuner(nullptr);
   for (int i = 0; i < count; ++i) {
     std::memset(&info[i], 0, sizeof(zolo_info_t));
     int e = validate(h, A[i], m[i], n[i], lda[i], Qp[i], ldq[i], H[i], ldh[i], &opts[i]);
@@ -1274,16 +1281,26 @@ int zolo_tuned_r(zolo_handle_t h, int64_t m, int64_t n, int prec, double ell0) {
   return hit != h->tuned_r.end() ? hit->second : 0;
 }
 
+int zolo_autotune(zolo_handle_t h, int enable) {
+  if (!h) return -1;
+  if (enable != 0 && enable != 1) return -2;
+  h->tuner.tuning = enable != 0;
+  return 0;
+}
+
 int zolo_tune_save(zolo_handle_t h, const char* path) {
   if (!h) return -1;
   if (!path) return -2;
   FILE* f = std::fopen(path, "w");
   if (!f) return ZOLO_EIO;
-  bool ok = std::fprintf(f, "zolo-tune 1 %s\n", device_tag(h->device).c_str()) > 0;
+  bool ok = std::fprintf(f, "zolo-tune 2 %s\n", device_tag(h->device).c_str()) > 0;
   for (const auto& kv : h->tuned_r)
-    ok = ok && std::fprintf(f, "%lld %lld %lld %lld %d\n", (long long)kv.first[0],
+    ok = ok && std::fprintf(f, "r %lld %lld %lld %lld %d\n", (long long)kv.first[0],
                             (long long)kv.first[1], (long long)kv.first[2], (long long)kv.first[3],
                             kv.second) > 0;
+  for (const auto& kv : h->tuner.choice)
+    ok = ok && std::fprintf(f, "g %d %d %d %d %d %d %d\n", kv.first[0], kv.first[1], kv.first[2],
+                            kv.first[3], kv.first[4], kv.first[5], kv.second) > 0;
   ok = (std::fclose(f) == 0) && ok;
   return ok ? 0 : ZOLO_EIO;
 }
@@ -1297,25 +1314,44 @@ int zolo_tune_load(zolo_handle_t h, const char* path) {
   int version = 0;
   int rc = 0;
   if (std::fscanf(f, "%31s %d %255s", magic, &version, dev) != 3 ||
-      std::strcmp(magic, "zolo-tune") != 0 || version != 1 || device_tag(h->device) != dev) {
+      std::strcmp(magic, "zolo-tune") != 0 || version != 2 || device_tag(h->device) != dev) {
     rc = ZOLO_EINVAL;
   }
-  std::map<std::array<int64_t, 4>, int> got;
+  std::map<std::array<int64_t, 4>, int> got_r;
+  std::map<std::array<int, 7>, int> got_g;
   while (rc == 0) {
-    long long a, b, c, d;
-    int r;
-    const int k = std::fscanf(f, "%lld %lld %lld %lld %d", &a, &b, &c, &d, &r);
-    if (k == EOF) break;
-    if (k != 5 || r < 1 || r > kMaxR || a < 1 || b < 1 || a < b ||
-        (c != ZOLO_FP64 && c != ZOLO_SPLIT_BF16) || d < 0 || d > 400) {
+    char tag[4] = {0};
+    const int t = std::fscanf(f, "%3s", tag);
+    if (t == EOF) break;
+    if (t != 1) {
       rc = ZOLO_EINVAL;
-      break;
+    } else if (std::strcmp(tag, "r") == 0) {
+      long long a, b, c, d;
+      int r;
+      if (std::fscanf(f, "%lld %lld %lld %lld %d", &a, &b, &c, &d, &r) != 5 || r < 1 ||
+          r > kMaxR || a < 1 || b < 1 || a < b || (c != ZOLO_FP64 && c != ZOLO_SPLIT_BF16) ||
+          d < 0 || d > 400)
+        rc = ZOLO_EINVAL;
+      else
+        got_r[{a, b, c, d}] = r;
+    } else if (std::strcmp(tag, "g") == 0) {
+      int k[6], v;
+      if (std::fscanf(f, "%d %d %d %d %d %d %d", &k[0], &k[1], &k[2], &k[3], &k[4], &k[5], &v) !=
+              7 ||
+          k[0] < 1 || k[1] < 1 || k[2] < 1 || k[3] < 1 || k[3] > kGemmMaxBatch || k[4] < 0 ||
+          k[4] > 255 || (k[5] != 0 && k[5] != 8 && k[5] != 9) ||
+          !gemm_variant_allowed({k[0], k[1], k[2], k[3], k[4], k[5], 0}, v))
+        rc = ZOLO_EINVAL;
+      else
+        got_g[{k[0], k[1], k[2], k[3], k[4], k[5], 0}] = v;
+    } else {
+      rc = ZOLO_EINVAL;
     }
-    got[{a, b, c, d}] = r;
   }
   std::fclose(f);
   if (rc) return rc;
-  for (const auto& kv : got) h->tuned_r[kv.first] = kv.second;
+  for (const auto& kv : got_r) h->tuned_r[kv.first] = kv.second;
+  for (const auto& kv : got_g) h->tuner.choice[kv.first] = kv.second;
   return 0;
 }
 

@@ -698,24 +698,24 @@ void split_prepare() {
 thread_local SplitWork* t_split = nullptr;
 
 void set_split_engine(SplitWork* w) { t_split = w; }
+SplitWork* get_split_engine() { return t_split; }
 
 // Estimated seconds on GB300 of one call on the FP64 pipe and on the split
 // tensor-core path (slicing traffic + output traffic + slice-pair products +
-// launch latency); the cheaper one runs.
-cudaError_t gemm_any(const GemmArgs& g, cudaStream_t st) {
-  if (!t_split || g.M <= 0 || g.N <= 0 || g.K <= 0) return gemm_f64(g, st);
+// launch latency).
+bool split_preferred(const GemmArgs& g, const SplitWork& w) {
   const double t64 = gemm_flops(g) / 0.9e12;
   const bool swap = g.M < kTileM && g.N > g.M;
   const double ra = (double)round_up(swap ? g.N : g.M, kTileM);
   const double rb = (double)round_up(swap ? g.M : g.N, 64);
   const double kp = (double)round_up(g.K, kBK);
-  const double S = t_split->slices_s;
+  const double S = w.slices_s;
   const double slice_bytes = g.batch * (8.0 + 2.0 * S) * (ra + rb) * kp;
   const double out_bytes = (g.reduce ? 1 : g.batch) * 8.0 * g.M * (double)g.N * (g.beta != 0.0 ? 2 : 1);
   const double pairs = S * (S + 1) / 2 + (S - 1);   // s + t <= S + 2
   const double tensor = pairs * 2.0 * ra * rb * kp * g.batch / 0.7e15;
   const double tsplit = slice_bytes / 4e12 + out_bytes / 5e12 + tensor + 30e-6;
-  return tsplit < t64 ? gemm_split(g, *t_split, st) : gemm_f64(g, st);
+  return tsplit < t64;
 }
 
 size_t split_slice_elems(int64_t M, int64_t N, int64_t K, int batch, int S) {

@@ -1,8 +1,10 @@
 // Internal declarations shared by the libzolo translation units.
 #pragma once
 
+#include <array>
 #include <cstddef>
 #include <cstdint>
+#include <map>
 
 #ifdef __CUDACC__
 #include <cuda_runtime.h>
@@ -103,7 +105,54 @@ struct GemmArgs {
   // the small rows their precision.
   int k_equilibrate = 0;
 };
+// Kernel variants of the FP64 contraction: output tile shape, and split-K
+// (K cut into 2 / 4 / 8 slices of whole BK steps whose raw sums go to a scratch
+// of ksplit * (reduce ? 1 : batch) * M * N doubles, then one deterministic
+// reduction kernel).  kGemmVSplit names the split tensor-core path.
+enum GemmVariant {
+  kGemmV64x64 = 0, kGemmV32x128 = 1, kGemmV32x64 = 2,
+  kGemmVSplitK2 = 3, kGemmVSplitK4 = 4, kGemmVSplitK8 = 5,
+  kGemmVSplit = 8
+};
+// one FP64 launch of the given variant (a split-K variant without enough
+// scratch runs as kGemmV64x64)
+cudaError_t gemm_f64_variant(const GemmArgs& g, int variant, double* scratch,
+                             size_t scratch_elems, cudaStream_t st);
+size_t gemm_f64_scratch_elems(const GemmArgs& g, int variant);
+int gemm_f64_default_variant(const GemmArgs& g);
+// FP64 contraction: the variant the current thread's tuner chose for this
+// shape, else the default one.
 cudaError_t gemm_f64(const GemmArgs& g, cudaStream_t st);
+
+// Measured kernel choice per contraction shape (sizes, batch, transposes,
+// structure flags, slice count): the cache of a handle, made current for the
+// calls of one API entry point by TunerScope.  With `tuning` set, a shape met
+// for the first time is run with every candidate variant into a scratch output
+// (the real output untouched) and timed with CUDA events; the fastest is kept.
+// No tuning while the stream is being captured.
+struct GemmTuner {
+  std::map<std::array<int, 7>, int> choice;
+  bool tuning = false;
+  bool busy = false;
+  double* scratch = nullptr;
+  size_t scratch_elems = 0;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  ~GemmTuner();
+};
+std::array<int, 7> gemm_key(const GemmArgs& g, int split_slices);
+// C's elements overlap those of A or B (flag 128 of the key)
+bool gemm_output_aliases_input(const GemmArgs& g);
+// whether kernel v may serve a key (tile variants other than the built-in one
+// are barred for in-place products: their CTAs would overwrite rows of B that
+// other CTAs still read)
+bool gemm_variant_allowed(const std::array<int, 7>& key, int v);
+void set_gemm_tuner(GemmTuner* t);
+GemmTuner* get_gemm_tuner();
+struct TunerScope {
+  GemmTuner* prev;
+  explicit TunerScope(GemmTuner* t) : prev(get_gemm_tuner()) { set_gemm_tuner(t); }
+  ~TunerScope() { set_gemm_tuner(prev); }
+};
 // algorithmic flops of one call (structural zeros excluded)
 double gemm_flops(const GemmArgs& g);
 
@@ -124,6 +173,10 @@ size_t split_slice_elems(int64_t M, int64_t N, int64_t K, int batch, int S);
 // The engine every contraction of the current call goes through: FP64 (DFMA)
 // when no split workspace is installed, the split tensor-core path otherwise.
 void set_split_engine(SplitWork* w);
+SplitWork* get_split_engine();
+// the built-in router: true when the split path's estimated time (slicing and
+// output traffic, slice-pair products, launch latency) beats the FP64 pipe's
+bool split_preferred(const GemmArgs& g, const SplitWork& w);
 // Sets the kernels' launch attributes ahead of a stream capture.
 void split_prepare();
 cudaError_t gemm_any(const GemmArgs& g, cudaStream_t st);

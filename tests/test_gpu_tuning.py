@@ -71,12 +71,12 @@ def test_tuned_r_runs_caches_and_matches_oracle(zb, tmp_path):
             lines = open(path).read().splitlines()
             other = str(tmp_path / "other.txt")
             with open(other, "w") as f:
-                f.write("zolo-tune 1 Some_Other_GPU\n512 512 0 8 3\n")
+                f.write("zolo-tune 2 Some_Other_GPU\nr 512 512 0 8 3\n")
             assert zb.tune_load(h2, other) == 9   # ZOLO_EINVAL
             assert zb.tuned_r(h2, 512, 512, zb.ZOLO_FP64, 1e-8) == 0
             bad = str(tmp_path / "bad.txt")
             with open(bad, "w") as f:
-                f.write(lines[0] + "\n64 64 0 2 5\n64 128 0 2 5\n")   # m < n
+                f.write(lines[0] + "\nr 64 64 0 2 5\nr 64 128 0 2 5\n")   # m < n
             assert zb.tune_load(h2, bad) == 9
             assert zb.tuned_r(h2, 64, 64, zb.ZOLO_FP64, 1e-2) == 0
             assert zb.tune_load(h2, str(tmp_path / "missing.txt")) == 8   # ZOLO_EIO
