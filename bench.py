@@ -437,6 +437,9 @@ def main():
                          "(default)")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="built-in kernel rules only")
+    ap.add_argument("--tune-cache", default=None,
+                    help="tuning-cache file: loaded before the warm-up steps when it exists, "
+                         "written after them")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -475,6 +478,9 @@ def main():
     sm = make_input(w, seed=2000 + rank)
     A = torch.from_numpy(sm.A).cuda()
     h = zb.Handle(local)
+    if args.tune_cache and os.path.exists(args.tune_cache):
+        if zb.tune_load(h, args.tune_cache) != 0:
+            raise SystemExit(f"tuning cache {args.tune_cache} refused (other GPU or malformed)")
     if args.autotune:
         zb.autotune(h, True)
     split = args.prec == "split"
@@ -497,6 +503,8 @@ def main():
     torch.cuda.synchronize()
     if args.autotune:
         zb.autotune(h, False)   # the timed steps use the kept kernels
+    if args.tune_cache:
+        zb.tune_save(h, args.tune_cache)
 
     def barrier():
         if dist:

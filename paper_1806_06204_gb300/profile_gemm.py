@@ -4,7 +4,9 @@ split precision (nine BF16 slices on the tensor cores), through zolo_dgemm.
     python -m paper_1806_06204_gb300.profile_gemm --m 4096 --n 4096 --k 4096 --prec split
 
 Seeded N(0,1) operands; `--reps` timed calls after one warm-up call, timed with
-CUDA events on the current stream.  Prints one JSON line: milliseconds per
+CUDA events on the current stream.  `--tune-cache F`: the FP64 kernel comes
+from the tuning file F when it holds this shape; otherwise the warm-up call
+measures the candidates (zolo_autotune) and F is written with the choice.  Prints one JSON line: milliseconds per
 call, FP64-equivalent TFLOP/s (2MNK per call), and for the split path the BF16
 tensor TFLOP/s actually issued (53 slice-pair products).  Also the launch
 target for kernel profilers: each call is one row-exponent + slicing pass per
@@ -27,6 +29,7 @@ def main():
     ap.add_argument("--transA", action="store_true")
     ap.add_argument("--transB", action="store_true")
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--tune-cache", default=None)
     args = ap.parse_args()
     build.build()
     from . import binding as zb
@@ -39,12 +42,27 @@ def main():
     C = zb.empty_colmajor(args.m, args.n)
     prec = zb.ZOLO_SPLIT_BF16 if args.prec == "split" else zb.ZOLO_FP64
     h = zb.Handle(torch.cuda.current_device())
+    if args.tune_cache:
+        import os
+        if os.path.exists(args.tune_cache) and zb.tune_load(h, args.tune_cache) != 0:
+            raise SystemExit(f"tuning cache {args.tune_cache} refused")
+        zb.autotune(h, True)
 
     def call():
         zb.zolo_dgemm(h, A, B, C, transA=args.transA, transB=args.transB, prec=prec, slices=9)
 
     call()
     torch.cuda.synchronize()
+    kernel = None
+    if args.tune_cache:
+        zb.autotune(h, False)
+        zb.tune_save(h, args.tune_cache)
+        names = {0: "64x64", 1: "32x128", 2: "32x64", 3: "64x64 split-K 2", 4: "64x64 split-K 4",
+                 5: "64x64 split-K 8", 8: "split"}
+        for line in open(args.tune_cache).read().splitlines():
+            f = line.split()
+            if f[0] == "g" and [int(x) for x in f[1:4]] == [args.m, args.n, args.k]:
+                kernel = names.get(int(f[-1]), f[-1])
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record()
@@ -58,6 +76,8 @@ def main():
            "fp64_equiv_tflops": flops / ms / 1e9}
     if args.prec == "split":
         out["bf16_issued_tflops"] = 53 * flops / ms / 1e9
+    if kernel:
+        out["tuned_kernel"] = kernel
     ref = A @ B if not (args.transA or args.transB) else None
     if ref is not None:
         out["max_rel_err_vs_cublas"] = float((C - ref).abs().max() / ref.abs().max())
