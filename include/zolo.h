@@ -225,7 +225,9 @@ int zolo_dgemm_noalloc(int transA, int transB, int64_t m, int64_t n, int64_t k, 
    deterministic reduction; the split tensor-core path when opts.prec asks for
    it) into a scratch output, timed with CUDA events, and keeps the fastest
    for that shape; the call's own outputs are written once, by the kept
-   kernel.  zolo_autotune(h, 0) stops measuring; choices already made stay in
+   kernel.  To bound the cost of measuring, a shape whose built-in kernel takes
+   over 50 ms keeps it, and the split path (or FP64) is not timed where the
+   cost model puts it 4x behind the other.  zolo_autotune(h, 0) stops measuring; choices already made stay in
    use.  Without choices the built-in rules apply (the split path where its
    cost model predicts a gain, else the 64x64 FP64 tile, 32x128 for M <= 32).
    zolo_pd_batched always uses the built-in rules.  A tuned kernel may sum in

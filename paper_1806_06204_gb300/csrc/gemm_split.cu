@@ -703,7 +703,9 @@ SplitWork* get_split_engine() { return t_split; }
 // Estimated seconds on GB300 of one call on the FP64 pipe and on the split
 // tensor-core path (slicing traffic + output traffic + slice-pair products +
 // launch latency).
-bool split_preferred(const GemmArgs& g, const SplitWork& w) {
+bool split_preferred(const GemmArgs& g, const SplitWork& w) { return split_time_ratio(g, w) < 1.0; }
+
+double split_time_ratio(const GemmArgs& g, const SplitWork& w) {
   const double t64 = gemm_flops(g) / 0.9e12;
   const bool swap = g.M < kTileM && g.N > g.M;
   const double ra = (double)round_up(swap ? g.N : g.M, kTileM);
@@ -715,7 +717,7 @@ bool split_preferred(const GemmArgs& g, const SplitWork& w) {
   const double pairs = S * (S + 1) / 2 + (S - 1);   // s + t <= S + 2
   const double tensor = pairs * 2.0 * ra * rb * kp * g.batch / 0.7e15;
   const double tsplit = slice_bytes / 4e12 + out_bytes / 5e12 + tensor + 30e-6;
-  return tsplit < t64;
+  return tsplit / t64;
 }
 
 size_t split_slice_elems(int64_t M, int64_t N, int64_t K, int batch, int S) {

@@ -63,14 +63,14 @@ __device__ __forceinline__ double warp_reduce_scatter32(double (&a)[32], int lan
 // column; the partial buffers alternate between columns so that no third
 // barrier is needed before they are rewritten.  All rows a CTA reads or writes
 // in W and V are its own, so the only cross-CTA traffic is the partials.
-template <int NB, int CG>
-__global__ void __cluster_dims__(CG, 1, 1) __launch_bounds__(256)
+template <int NB, int CG, int KT>
+__global__ void __cluster_dims__(CG, 1, 1) __launch_bounds__(KT)
 qr_panel_cluster_kernel(double* W, int64_t strideW, int64_t ldw, int64_t m, int64_t c0, int nbp,
                         double* V, int64_t strideV, int64_t ldv, double* T, int64_t strideT,
                         int* status) {
   namespace cgrp = cooperative_groups;
   cgrp::cluster_group cluster = cgrp::this_cluster();
-  constexpr int kT = 256, kWarps = kT / 32;
+  constexpr int kT = KT, kWarps = kT / 32;
   __shared__ double part[2][NB + 2];        // [0, NB): dots, NB: norm^2, NB+1: alpha
   __shared__ double red[kWarps][NB + 2];
   __shared__ double dots[NB];
@@ -575,7 +575,9 @@ cudaError_t structured_qr_q(const QrBuffers& b, int64_t m, int64_t n, int r, int
                                                     sizeof(double) * NB * rows8, st>>>(
               b.W, b.strideW, ldw, m, c0, nbp, Vpan, b.strideV, ldv, b.T, b.strideT, status);
         else
-          qr_panel_cluster_kernel<NB, kPanelCluster><<<r * kPanelCluster, 256, 0, st>>>(
+          // tall panels (m > 8 x 768 rows): 512 threads per CTA halve each thread's
+          // share of the rows on the serial chain of every column
+          qr_panel_cluster_kernel<NB, kPanelCluster, 512><<<r * kPanelCluster, 512, 0, st>>>(
               b.W, b.strideW, ldw, m, c0, nbp, Vpan, b.strideV, ldv, b.T, b.strideT, status);
       }
       if ((err = cudaGetLastError()) != cudaSuccess) return err;

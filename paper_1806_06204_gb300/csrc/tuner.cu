@@ -69,7 +69,10 @@ bool ensure_scratch(GemmTuner& t, size_t elems, cudaStream_t st) {
 }
 
 // Time every candidate of g's shape; returns the fastest (or -1 when tuning
-// could not run: no scratch, a failed launch).  When the output overlaps A or B
+// could not run: no scratch, a failed launch).  With the split path on, a shape
+// whose estimated split time is under a quarter of the FP64 time is given to
+// the split path untimed, and one estimated 4x slower on it is not timed there;
+// a shape whose built-in kernel takes over 50 ms keeps it.  When the output overlaps A or B
 // (a product computed in place, as the Cholesky panel update is) the only
 // candidates are the built-in tile, which the call site is written for, and
 // the variants that read all of A and B before writing C (split-K, split).
@@ -79,7 +82,13 @@ int tune(GemmTuner& t, const GemmArgs& g, SplitWork* split, cudaStream_t st) {
   if (gemm_output_aliases_input(g)) cand = {gemm_f64_default_variant(g)};
   for (int v : {kGemmVSplitK2, kGemmVSplitK4, kGemmVSplitK8})
     if (g.K >= 2 * 16 * ksplit_of(v)) cand.push_back(v);
-  if (split) cand.push_back(kGemmVSplit);
+  if (split) {
+    // where the estimate puts one path 4x ahead of the other, the slower one is
+    // not timed (a large FP64 product takes seconds per candidate)
+    const double ratio = split_time_ratio(g, *split);
+    if (ratio < 0.25) return kGemmVSplit;
+    if (ratio <= 4.0) cand.push_back(kGemmVSplit);
+  }
   size_t part = 0;
   for (int v : cand) part = std::max(part, gemm_f64_scratch_elems(g, v));
   if (!ensure_scratch(t, out + part, st)) {
@@ -94,6 +103,12 @@ int tune(GemmTuner& t, const GemmArgs& g, SplitWork* split, cudaStream_t st) {
   h.ldcout = g.M;
   h.strideCout = (int64_t)g.M * g.N;
   double* partials = t.scratch + out;
+  // the built-in choice first: a shape that takes it over 50 ms keeps it (large
+  // products already fill the GPU, and timing every candidate there would cost
+  // seconds per shape)
+  const int builtin = split && split_preferred(g, *split) ? (int)kGemmVSplit
+                                                          : gemm_f64_default_variant(g);
+  std::stable_partition(cand.begin(), cand.end(), [&](int v) { return v == builtin; });
   int best = -1;
   float best_ms = FLT_MAX;
   for (int v : cand) {
@@ -112,6 +127,7 @@ int tune(GemmTuner& t, const GemmArgs& g, SplitWork* split, cudaStream_t st) {
       best_ms = ms;
       best = v;
     }
+    if (v == builtin && ms > 50.f) return builtin;
   }
   return best;
 }

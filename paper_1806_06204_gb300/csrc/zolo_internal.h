@@ -177,6 +177,8 @@ SplitWork* get_split_engine();
 // the built-in router: true when the split path's estimated time (slicing and
 // output traffic, slice-pair products, launch latency) beats the FP64 pipe's
 bool split_preferred(const GemmArgs& g, const SplitWork& w);
+// the same estimate as a ratio: split-path time / FP64 time
+double split_time_ratio(const GemmArgs& g, const SplitWork& w);
 // Sets the kernels' launch attributes ahead of a stream capture.
 void split_prepare();
 cudaError_t gemm_any(const GemmArgs& g, cudaStream_t st);

@@ -115,6 +115,21 @@ def test_pd_matches_oracle(zb, handle, m, n, kappa, r):
     assert np.allclose(info.delta, io.delta, rtol=max(1e-6, 10 * EPS * kappa), atol=1e-13)
 
 
+@pytest.mark.parametrize("m,n,kappa,r", [(6400, 48, 1e6, 3), (7000, 33, 1e10, 2)])
+def test_tall_panels_in_global_memory_match_oracle(zb, handle, m, n, kappa, r):
+    # m + 32 > 8 x 768 rows: the QR panels run in the cluster kernel that keeps the
+    # panel in global memory (512 threads per CTA); two panels, the last ragged
+    sm = synth.make_matrix(m, n, synth.geometric_sigma(n, kappa), seed=4000 + m + n)
+    beta = float(sm.sigma[-1])
+    Qp, H, info = zb.zolo_pd(handle, dev(sm.A), zb.opts(beta=beta, r=r))
+    Qo, Ho, io = zo.zolo_pd(sm.A, 1.0, beta, r=r)
+    Qp, H = host(Qp), host(H)
+    assert info.iters == io.iters and info.used_qr == io.used_qr and io.used_qr[0]
+    check_pd_invariants(sm.A, Qp, H)
+    assert np.linalg.norm(H - Ho) <= 1e-13 * np.linalg.norm(Ho)
+    assert np.linalg.norm(Qp - Qo) <= polar_tol(sm) * math.sqrt(n)
+
+
 @pytest.mark.parametrize("m,n,kappa,r,form", [(700, 200, 1e6, 6, 0), (256, 256, 1e12, 8, 2),
                                               (520, 130, 1e8, 2, 2), (190, 190, 1e4, 3, 1)])
 def test_pd_inverse_cholesky_form_matches_oracle(zb, handle, m, n, kappa, r, form):
