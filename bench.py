@@ -52,6 +52,9 @@ WORKLOADS = {
                     desc="Plain FP64 Zolo-SVD of one 1024x1024 matrix, kappa 1e8, r=6"),
     "pd16384x4096": dict(kind="pd", m=16384, n=4096, kappa=1e6, r=6, sample_n=384, tall=True,
                          desc="Zolo-PD of one 16384x4096 matrix, sigma uniform in [1e-6, 1], r=6"),
+    # panels taller than 8 x 768 rows: the QR panel runs in the global-memory cluster kernel
+    "pd8192x512": dict(kind="pd", m=8192, n=512, kappa=1e8, r=6, sample_n=256, tall=True,
+                       desc="Zolo-PD of one 8192x512 matrix, sigma uniform in [1e-8, 1], r=6"),
     "pd1024": dict(kind="pd", m=1024, n=1024, kappa=1e8, r=6, sample_n=256,
                    desc="Zolo-PD of one 1024x1024 matrix, kappa 1e8, r=6"),
     # beta = sigma_min / 100: forming A in FP64 perturbs its singular values by about

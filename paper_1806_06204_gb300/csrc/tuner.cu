@@ -92,7 +92,10 @@ int tune(GemmTuner& t, const GemmArgs& g, SplitWork* split, cudaStream_t st) {
   size_t part = 0;
   for (int v : cand) part = std::max(part, gemm_f64_scratch_elems(g, v));
   if (!ensure_scratch(t, out + part, st)) {
-    cand.resize(3);   // without split-K partials, if at least the output fits
+    // without split-K partials, if at least the output fits
+    cand.erase(std::remove_if(cand.begin(), cand.end(),
+                              [&](int v) { return gemm_f64_scratch_elems(g, v) > 0; }),
+               cand.end());
     part = 0;
     if (!ensure_scratch(t, out, st)) return -1;
   }
