@@ -115,10 +115,12 @@ def test_pd_matches_oracle(zb, handle, m, n, kappa, r):
     assert np.allclose(info.delta, io.delta, rtol=max(1e-6, 10 * EPS * kappa), atol=1e-13)
 
 
-@pytest.mark.parametrize("m,n,kappa,r", [(6400, 48, 1e6, 3), (7000, 33, 1e10, 2)])
+@pytest.mark.parametrize("m,n,kappa,r", [(6400, 48, 1e6, 3), (7000, 33, 1e10, 2),
+                                         (2500, 40, 1e8, 4)])
 def test_tall_panels_in_global_memory_match_oracle(zb, handle, m, n, kappa, r):
     # m + 32 > 8 x 768 rows: the QR panels run in the cluster kernel that keeps the
-    # panel in global memory (512 threads per CTA); two panels, the last ragged
+    # panel in global memory (512 threads per CTA); 2500 rows: the shared-memory
+    # cluster kernel with more rows per CTA than threads; two panels, the last ragged
     sm = synth.make_matrix(m, n, synth.geometric_sigma(n, kappa), seed=4000 + m + n)
     beta = float(sm.sigma[-1])
     Qp, H, info = zb.zolo_pd(handle, dev(sm.A), zb.opts(beta=beta, r=r))
