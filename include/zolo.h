@@ -131,6 +131,16 @@ int zolo_coefficients(double ell, int r, double* c, double* a, double* Mhat, dou
    the r taken (may be NULL). */
 int zolo_schedule(double ell0, int r, int max_iter, double* ells, int* used_qr, int* r_used);
 
+/* Device memory a zolo_pd (svd = 0) or zolo_svd (svd = 1) call on an m x n
+   matrix keeps in its handle (host computation, no GPU work): the workspace
+   for r shifts (r <= 0: for up to 8) plus, for ZOLO_SPLIT_BF16, the slice
+   planes and exponents, as the call allocates them (the planes are capped at
+   16 GB; a smaller allocation is tried when that fails).  Not counted: the
+   host entry points' staging copies of A and the results, and the tuner's
+   scratch (zolo_autotune).  Returns 0 and writes *bytes, or -i for an illegal
+   argument i (m < n, n < 1, r outside -1..8, prec, svd not 0/1, NULL). */
+int zolo_workspace_bytes(int64_t m, int64_t n, int r, int prec, int svd, uint64_t* bytes);
+
 /* Polar decomposition A = Qp H (Algorithm 1).
    A (m x n, lda >= m) is read only; Qp (m x n, ldq >= m) and H (n x n,
    ldh >= n) are written.  H is exactly symmetric. */

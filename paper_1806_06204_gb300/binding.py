@@ -81,6 +81,8 @@ def _load():
     lib.zolo_pd_batched.argtypes = [P, I, P, P, P, P, P, P, P, P, ctypes.POINTER(ZoloOpts),
                                     ctypes.POINTER(ZoloInfo), P]
     lib.zolo_pd_batched.restype = I
+    lib.zolo_workspace_bytes.argtypes = [I64, I64, I, I, I, ctypes.POINTER(ctypes.c_uint64)]
+    lib.zolo_workspace_bytes.restype = I
     lib.zolo_autotune.argtypes = [P, I]
     lib.zolo_autotune.restype = I
     lib.zolo_tuned_r.argtypes = [P, I64, I64, I, D]
@@ -103,7 +105,8 @@ EXPORTED = ["zolo_opts_default", "zolo_create", "zolo_destroy", "zolo_coefficien
             "zolo_schedule", "zolo_pd", "zolo_svd", "zolo_pd_host", "zolo_svd_host",
             "zolo_strerror", "zolo_kernel_launches", "zolo_profile", "zolo_profile_read",
             "zolo_dgemm", "zolo_dgemm_noalloc", "zolo_pd_batched", "zolo_tuned_r",
-            "zolo_tune_save", "zolo_tune_load", "zolo_autotune"]
+            "zolo_tune_save", "zolo_tune_load", "zolo_autotune",
+            "zolo_workspace_bytes"]
 
 
 def kernel_launches() -> int:
@@ -178,6 +181,15 @@ def schedule(ell0: float, r: int = 0, max_iter: int = 8):
     if k < 0:
         raise ZoloError(k, "zolo_schedule")
     return list(ells[:k + 1]), [bool(x) for x in qr[:k]], ru.value
+
+
+def workspace_bytes(m: int, n: int, r: int = 0, prec: int = ZOLO_FP64, svd: bool = False) -> int:
+    """Device bytes a zolo_pd / zolo_svd call keeps in its handle (host-only query)."""
+    out = ctypes.c_uint64()
+    e = LIB.zolo_workspace_bytes(m, n, r, prec, int(svd), ctypes.byref(out))
+    if e:
+        raise ZoloError(e, "zolo_workspace_bytes")
+    return int(out.value)
 
 
 def autotune(handle, enable: bool) -> None:

@@ -780,6 +780,27 @@ int zolo_coefficients(double ell, int r, double* c, double* a, double* Mhat, dou
   return 0;
 }
 
+int zolo_workspace_bytes(int64_t m, int64_t n, int r, int prec, int svd, uint64_t* bytes) {
+  if (n < 1 || n > INT32_MAX) return -2;
+  if (m < n || m > INT32_MAX) return -1;
+  if (r < ZOLO_R_TUNED || r > kMaxR) return -3;
+  if (prec != ZOLO_FP64 && prec != ZOLO_SPLIT_BF16) return -4;
+  if (svd != 0 && svd != 1) return -5;
+  if (!bytes) return -6;
+  const int rr = r > 0 ? r : kMaxR;   // r chosen by the call: at most 8 shifts
+  PdBufs b;
+  uint64_t total = layout(nullptr, m, n, rr, svd != 0, &b);
+  if (prec == ZOLO_SPLIT_BF16) {
+    // as SplitScope::begin asks for: slice planes (BF16), exponents (int), error flag
+    const size_t per = split_elems_per_entry(m, n);
+    const size_t want = std::max(per, std::min(per * (size_t)rr, (size_t)8 << 30));
+    const size_t exps = (size_t)2 * kGemmMaxBatch * (size_t)(std::max(m, n) + m + n + 512);
+    total += want * 2 + exps * sizeof(int) + sizeof(int);
+  }
+  *bytes = total;
+  return 0;
+}
+
 int zolo_schedule(double ell0, int r, int max_iter, double* ells, int* used_qr, int* r_used) {
   Schedule s;
   const int e = build_schedule(ell0, r, max_iter, &s);

@@ -84,3 +84,28 @@ def test_illegal_arguments_rejected_before_device_work(zb):
         assert call(fake, P, 4, 4, 4, P, 4, P, 4, ctypes.byref(ob)) == -10, bad
     assert zb.LIB.zolo_coefficients(0.0, 3, None, None, None, None) == -1
     assert zb.LIB.zolo_coefficients(0.5, 9, None, None, None, None) == -2
+
+
+def test_workspace_bytes_query(zb):
+    # host-only: the workspace a call keeps, from the same layout the call carves
+    m, n = 3000, 1000
+    f = lambda **k: zb.workspace_bytes(m, n, **k)
+    b8 = f(r=8)
+    # at least X, X_next, S (m x n), M (n x n) and, per shift, the stacked W
+    # ((m + n) x n) and the reflectors V ((m + 128) x n)
+    floor = 8 * (3 * m * n + n * n + 8 * ((m + n) * n + (m + 128) * n))
+    assert floor <= b8 <= 1.25 * floor + (1 << 20)
+    assert f(r=1) < f(r=4) < b8 == f(r=0) == f(r=zb.ZOLO_R_TUNED)
+    assert f(r=8, svd=True) > b8
+    assert f(r=8, prec=zb.ZOLO_SPLIT_BF16) > b8
+    assert zb.workspace_bytes(16384, 16384, 8, zb.ZOLO_SPLIT_BF16) < 100e9
+    import ctypes
+    out = ctypes.c_uint64()
+    call = zb.LIB.zolo_workspace_bytes
+    assert call(10, 20, 1, 0, 0, ctypes.byref(out)) == -1       # m < n
+    assert call(10, 0, 1, 0, 0, ctypes.byref(out)) == -2
+    assert call(10, 10, 9, 0, 0, ctypes.byref(out)) == -3
+    assert call(10, 10, -2, 0, 0, ctypes.byref(out)) == -3
+    assert call(10, 10, 1, 5, 0, ctypes.byref(out)) == -4
+    assert call(10, 10, 1, 0, 2, ctypes.byref(out)) == -5
+    assert call(10, 10, 1, 0, 0, None) == -6
