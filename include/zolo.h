@@ -66,8 +66,9 @@ typedef struct {
                       assumes it known): beta = alpha / ||R^{-1}||_F with R from
                       a Householder QR of A / alpha, a lower bound of
                       sigma_min(A) (||R^{-1}||_F >= ||R^{-1}||_2) within a
-                      factor sqrt(n); about 2mn^2 + n^3 more flops.  Not
-                      accepted by zolo_pd_batched.                            */
+                      factor sqrt(n); about 2mn^2 + n^3 more flops (in
+                      zolo_pd_batched: matrix after matrix, before the
+                      batch starts)                                           */
   int max_iter;    /* cap on iterations, 1..8 (default 6)                    */
   int posteriori;  /* 1: after the a-priori iterations, apply the test of
                       Algorithm 1 step (d) literally and iterate while

@@ -1024,7 +1024,7 @@ int zolo_pd_batched(zolo_handle_t h, int count, const double* const* A, const in
   for (int i = 0; i < count; ++i) {
     std::memset(&info[i], 0, sizeof(zolo_info_t));
     int e = validate(h, A[i], m[i], n[i], lda[i], Qp[i], ldq[i], H[i], ldh[i], &opts[i]);
-    if (e == 0 && (opts[i].posteriori || !(opts[i].beta > 0.0))) e = -10;
+    if (e == 0 && opts[i].posteriori) e = -10;
     if (e) {
       info[i].status = e;
       return e;
@@ -1035,7 +1035,7 @@ int zolo_pd_batched(zolo_handle_t h, int count, const double* const* A, const in
   cudaEventRecord(h->e0, st);
   // ---- bounds and schedules (alpha <= 0: min(||A_i||_F, sqrt(||A_i||_1 ||A_i||_inf)),
   // all sums in one pass; the scratch is reused matrix after matrix on one stream)
-  std::vector<double> alpha(count);
+  std::vector<double> alpha(count), beta(count);
   std::vector<Schedule> sch(count);
   {
     std::vector<int> need;
@@ -1079,7 +1079,21 @@ int zolo_pd_batched(zolo_handle_t h, int count, const double* const* A, const in
         info[i].status = ZOLO_ENONFINITE;
         return ZOLO_ENONFINITE;
       }
-      const double ell0 = std::min(1.0, opts[i].beta / alpha[i]);
+      // beta <= 0: estimated on the handle's own workspace, before any lane starts
+      beta[i] = opts[i].beta;
+      if (!(beta[i] > 0.0)) {
+        PdBufs eb;
+        if (int e = ensure_ws(h, layout(nullptr, m[i], n[i], 1, false, &eb))) {
+          info[i].status = e;
+          return e;
+        }
+        layout(h->ws, m[i], n[i], 1, false, &eb);
+        if (int e = estimate_beta(A[i], lda[i], m[i], n[i], alpha[i], eb, st, &beta[i])) {
+          info[i].status = e;
+          return e;
+        }
+      }
+      const double ell0 = std::min(1.0, beta[i] / alpha[i]);
       int ri = opts[i].r;
       if (ri == ZOLO_R_TUNED) {
         const auto hit = h->tuned_r.find(tune_key(m[i], n[i], opts[i].prec, ell0));
@@ -1163,6 +1177,8 @@ int zolo_pd_batched(zolo_handle_t h, int count, const double* const* A, const in
     key.insert(key.end(), ob, ob + sizeof(zolo_opts_t) / 8 + 1);
     uint64_t ab;
     std::memcpy(&ab, &alpha[i], 8);
+    key.push_back(ab);
+    std::memcpy(&ab, &beta[i], 8);   // an estimated beta follows A's contents
     key.push_back(ab);
     key.push_back((uint64_t)sch[i].r);   // a tuned r may change between calls
   }

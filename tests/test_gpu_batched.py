@@ -5,6 +5,8 @@ meet the same invariants as a single zolo_pd call and agree with the oracle's
 polar factor within the conditioning-scaled tolerance (the polar factor's
 sensitivity is ~1/(sigma_{n-1} + sigma_n)).  A second call with the same
 pointers replays the recorded CUDA graph and must give the same bits."""
+import math
+
 import numpy as np
 import pytest
 
@@ -109,6 +111,31 @@ def test_batched_inverse_cholesky_form_equals_single_calls(zb, handle):
         assert np.array_equal(hh.cpu().numpy(), h1.cpu().numpy())
 
 
+def test_batched_estimates_beta_as_the_single_call_does(zb, handle):
+    # beta <= 0 and alpha <= 0: both bounds computed on the device before the batch
+    # starts; every matrix then runs the schedule the single call would run
+    shapes = [(180, 120), (96, 96), (250, 70)]
+    mats = _case(shapes, [1e9, 1e3, 1e6], 500)
+    os = [zb.opts(beta=0.0, alpha=0.0), zb.opts(beta=-1.0, alpha=1.0, r=3),
+          zb.opts(beta=0.0, alpha=0.0, prec=zb.ZOLO_SPLIT_BF16, ns_steps=1)]
+    As = [dev(sm.A) for sm in mats]
+    Qps, Hs, infos, st = zb.zolo_pd_batched(handle, As, os)
+    assert st == 0
+    for sm, a, o, q, hh, inf in zip(mats, As, os, Qps, Hs, infos):
+        q1, h1, inf1 = zb.zolo_pd(handle, a, o)
+        assert inf.ell[0] == inf1.ell[0] and inf.r == inf1.r and inf.iters == inf1.iters
+        s = np.sort(sm.sigma)
+        alpha = zo.alpha_bound(sm.A) if o.alpha <= 0 else o.alpha
+        beta = inf.ell[0] * alpha
+        assert s[0] / math.sqrt(len(s)) * (1 - 1e-6) <= beta <= s[0] * (1 + 1e-6)
+        Qh, Hh = q.cpu().numpy(), hh.cpu().numpy()
+        assert zo.orthogonality(Qh) <= 1e-13 and zo.backward_error_pd(sm.A, Qh, Hh) <= 1e-13
+        if o.prec == zb.ZOLO_FP64:
+            assert np.array_equal(Qh, q1.cpu().numpy()) and np.array_equal(Hh, h1.cpu().numpy())
+        else:   # the lanes' slice buffers may chunk a batched product differently
+            assert np.max(np.abs(Qh - q1.cpu().numpy())) <= 200 * zo.EPS / ((s[0] + s[1]) / s[-1])
+
+
 def test_batched_split_precision_invariants(zb, handle):
     shapes = [(256, 256), (192, 128), (128, 128)]
     mats = _case(shapes, [1e8, 1e3, 1e14], 300)
@@ -128,9 +155,5 @@ def test_batched_empty_and_bad_arguments(zb, handle):
     assert st == 0 and infos == []
     sm = synth.make_matrix(64, 64, synth.geometric_sigma(64, 10.0), seed=7)
     o = zb.opts(beta=0.05, alpha=sm.sigma.max(), posteriori=True)
-    _, _, infos, st = zb.zolo_pd_batched(handle, [dev(sm.A)], [o], check=False)
-    assert st == -10 and infos[0].status == -10
-    # the batched call takes no beta estimate: beta must be given
-    o = zb.opts(beta=0.0, alpha=sm.sigma.max())
     _, _, infos, st = zb.zolo_pd_batched(handle, [dev(sm.A)], [o], check=False)
     assert st == -10 and infos[0].status == -10
