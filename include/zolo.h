@@ -48,8 +48,8 @@ enum {
 /* Arithmetic of the contractions.  ZOLO_FP64: plain FP64 on the FP64 FMA pipe.
    ZOLO_SPLIT_BF16: the iterations' products on the BF16 tensor cores, each FP64
    operand cut into 9 power-of-two-scaled 6-bit slices (Ozaki scheme, product
-   error ~2^-54 of max|row| max|column|); panel factorisations, diagonal blocks
-   and coefficients stay FP64. */
+   error a few times sqrt(k) 2^-54 of max|row| max|column|); panel
+   factorisations, diagonal blocks and coefficients stay FP64. */
 enum { ZOLO_FP64 = 0, ZOLO_SPLIT_BF16 = 1 };
 
 typedef struct {

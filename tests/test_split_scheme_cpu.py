@@ -1,0 +1,116 @@
+"""A numpy model of the split-precision product's arithmetic (no GPU).
+
+The tensor-core path writes every FP64 row of op(A) / column of op(B), scaled by
+its power of two 2^e into (-1/2, 1/2), as the integer N = round(x 2^(6S - e)) in
+S balanced base-64 digits (|d_s| <= 32), and sums the digit-pair products of
+levels s + t <= S + 2.  This model does the same in exact integer arithmetic and
+checks the claims the design rests on: the error bound, a small multiple of
+sqrt(K) 2^-6S max|A_i| max|B_j| (the rounding of N, relative to a row maximum in
+[1/4, 1/2), dominates it), FP64 grade at S = 9, the gain from keeping level S + 2, the bias that
+truncated digits put on a Gram diagonal and balanced ones do not, and that a
+level's partial sums over a 2048-long chunk stay exact in FP32.
+"""
+import math
+
+import numpy as np
+import pytest
+
+BETA = 6
+
+
+def exponents(X, axis):
+    """e with max |x| 2^-e in [1/4, 1/2) along the given axis (0 for zero rows)."""
+    mx = np.max(np.abs(X), axis=axis)
+    e = np.zeros(mx.shape, dtype=np.int64)
+    nz = mx > 0
+    e[nz] = np.frexp(mx[nz])[1] + 1          # mx = f 2^E, f in [1/2, 1): mx 2^-(E+1) in [1/4, 1/2)
+    return e
+
+
+def digits(X, e, S, balanced=True):
+    """Integer digits d[s] (s = 0..S-1, most significant first) of X 2^-e on S base-64 places."""
+    N = np.vectorize(int, otypes=[object])(np.rint(np.ldexp(X, (BETA * S - e))))  # exact ints
+    out = []
+    for _ in range(S - 1):
+        d = np.vectorize(lambda v: ((v + 32) % 64) - 32 if balanced else v % 64, otypes=[object])(N)
+        out.append(d)
+        N = (N - d) // 64
+    out.append(N)
+    return out[::-1]
+
+
+def split_product(A, B, S, max_level, balanced=True):
+    ea = exponents(A, axis=1)                 # rows of A
+    eb = exponents(B, axis=0)                 # columns of B
+    da = digits(A, ea[:, None], S, balanced)
+    db = digits(B, eb[None, :], S, balanced)
+    acc = np.zeros((A.shape[0], B.shape[1]), dtype=object)
+    for s in range(S):
+        for t in range(S):
+            if (s + 1) + (t + 1) > max_level:
+                continue
+            acc += (da[s].dot(db[t])) * (2 ** (BETA * (2 * S - (s + 1) - (t + 1))))
+    # value = acc 2^-(12S) 2^(ea + eb)
+    C = np.empty(acc.shape)
+    for i in range(acc.shape[0]):
+        for j in range(acc.shape[1]):
+            C[i, j] = math.ldexp(float(acc[i, j]), int(ea[i] + eb[j]) - 2 * BETA * S)
+    return C
+
+
+def exact_product(A, B):
+    return (A.astype(np.longdouble) @ B.astype(np.longdouble)).astype(np.float64)
+
+
+@pytest.fixture(scope="module")
+def operands():
+    rng = np.random.default_rng(11)
+    A = rng.standard_normal((12, 300)) * np.exp(rng.uniform(-8, 8, (12, 1)))
+    B = rng.standard_normal((300, 10)) * np.exp(rng.uniform(-8, 8, (1, 10)))
+    return A, B
+
+
+def test_nine_slices_are_fp64_grade(operands):
+    A, B = operands
+    S, K = 9, A.shape[1]
+    C = split_product(A, B, S, S + 2)
+    ref = exact_product(A, B)
+    scale = np.max(np.abs(A), axis=1)[:, None] * np.max(np.abs(B), axis=0)[None, :]
+    err = np.max(np.abs(C - ref) / scale)
+    assert err <= 8 * math.sqrt(K) * 2.0 ** (-BETA * S)
+    assert err <= 2e-16 * math.sqrt(K)
+
+
+def test_keeping_level_s_plus_2_cuts_the_error(operands):
+    A, B = operands
+    S = 9
+    ref = exact_product(A, B)
+    scale = np.max(np.abs(A), axis=1)[:, None] * np.max(np.abs(B), axis=0)[None, :]
+    e_keep = np.max(np.abs(split_product(A, B, S, S + 2) - ref) / scale)
+    e_drop = np.max(np.abs(split_product(A, B, S, S + 1) - ref) / scale)
+    assert e_drop > 4 * e_keep
+
+
+def test_balanced_digits_leave_no_bias_on_a_gram_diagonal():
+    # the dropped pairs of a truncated (non-negative) digit expansion all push
+    # x^T x the same way; balanced digits make them zero-mean
+    rng = np.random.default_rng(12)
+    x = rng.uniform(0.25, 0.5, (1, 4000))
+    S, lvl = 4, 4 + 1           # coarse enough that the dropped pairs, not the rounding, dominate
+    ref = float(exact_product(x, x.T)[0, 0])
+    bal = split_product(x, x.T, S, lvl, balanced=True)[0, 0]
+    tru = split_product(x, x.T, S, lvl, balanced=False)[0, 0]
+    assert abs(tru - ref) > 5 * abs(bal - ref)
+
+
+def test_level_sums_are_exact_in_fp32_over_a_chunk():
+    # a level of p pairs (p <= 7 for levels 2..8, each in its own TMEM accumulator)
+    # of |d_s d_t| <= 2^10 over 2048 terms stays within FP32's 24-bit integer range
+    for level in range(2, 9):
+        p = level - 1
+        assert p * 2048 * 2 ** 10 <= 2 ** 24
+    # and the digits' bound itself: |d| <= 32 for every digit of the model
+    rng = np.random.default_rng(13)
+    X = rng.standard_normal((5, 64)) * 10.0 ** rng.uniform(-20, 20, (5, 1))
+    for d in digits(X, exponents(X, axis=1)[:, None], 9):
+        assert max(abs(int(v)) for v in d.ravel()) <= 32
