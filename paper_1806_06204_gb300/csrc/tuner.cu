@@ -71,11 +71,12 @@ bool ensure_scratch(GemmTuner& t, size_t elems, cudaStream_t st) {
 // Time every candidate of g's shape; returns the fastest (or -1 when tuning
 // could not run: no scratch, a failed launch).  With the split path on, a shape
 // whose estimated split time is under a quarter of the FP64 time is given to
-// the split path untimed, and one estimated 4x slower on it is not timed there;
-// a shape whose built-in kernel takes over 50 ms keeps it.  When the output overlaps A or B
-// (a product computed in place, as the Cholesky panel update is) the only
-// candidates are the built-in tile, which the call site is written for, and
-// the variants that read all of A and B before writing C (split-K, split).
+// the split path untimed, and one estimated 4x slower on it is not timed
+// there; a shape whose built-in kernel takes over 50 ms keeps it.  When the
+// output overlaps A or B (a product computed in place, as the Cholesky panel
+// update is) the only candidates are the built-in tile, which the call site is
+// written for, and the variants that read all of A and B before writing C
+// (split-K, split).
 int tune(GemmTuner& t, const GemmArgs& g, SplitWork* split, cudaStream_t st) {
   const size_t out = (size_t)(g.reduce ? 1 : g.batch) * (size_t)g.M * (size_t)g.N;
   std::vector<int> cand = {kGemmV64x64, kGemmV32x128, kGemmV32x64};
