@@ -484,7 +484,9 @@ def main():
     if args.tune_cache and os.path.exists(args.tune_cache):
         if zb.tune_load(h, args.tune_cache) != 0:
             raise SystemExit(f"tuning cache {args.tune_cache} refused (other GPU or malformed)")
-    if args.autotune:
+    # kernels are measured during the warm-up steps only, never inside the timed region
+    tuning = args.autotune and args.warmup > 0
+    if tuning:
         zb.autotune(h, True)
     split = args.prec == "split"
     beta_scale = args.beta_scale if args.beta_scale is not None else w.get("beta_scale", 1.0)
@@ -504,7 +506,7 @@ def main():
     for _ in range(args.warmup):
         outs, info = step()
     torch.cuda.synchronize()
-    if args.autotune:
+    if tuning:
         zb.autotune(h, False)   # the timed steps use the kept kernels
     if args.tune_cache:
         zb.tune_save(h, args.tune_cache)
@@ -582,7 +584,7 @@ def main():
                 "data": "synthetic",
                 "config": {"workload": args.workload, "desc": w["desc"], "m": m, "n": n,
                            "kappa": w["kappa"], "r": info.r, "r_requested": r_req,
-                           "chol_form": info.chol_form, "autotune": bool(args.autotune),
+                           "chol_form": info.chol_form, "autotune": bool(tuning),
                            "prec": args.prec,
                            "beta_over_sigma_min": beta_scale,
                            "l2": "inputs larger than L2 (no flush)",
