@@ -130,3 +130,20 @@ def test_alpha_bound_exact_cases_and_upper_bound():
         A = rng(seed).standard_normal((30, 17)) * rng(seed + 9).uniform(0.01, 10, 17)
         assert zo.alpha_bound(A) >= np.linalg.norm(A, 2) * (1 - 1e-14)
         assert zo.alpha_bound(A) <= np.linalg.norm(A) * (1 + 1e-15)
+
+
+@pytest.mark.parametrize("m,n", [(9, 5), (40, 17), (33, 33)])
+def test_stacked_qr_structure_of_section_3_1(m, n):
+    # The structure the GPU's structured QR is built on (Section 3.1): for
+    # W = [X; sqrt(c) I], the dense Householder QR's k-th reflector is non-zero
+    # only on rows k..m+k, and the lower block Q2 of the thin Q is upper triangular
+    # (both exactly: the zeros are structural)
+    X = rng(m * 7 + n).standard_normal((m, n))
+    W = np.vstack([X, math.sqrt(0.37) * np.eye(n)])
+    refl, R = zo.householder_qr(W)
+    for k, (v, tau) in enumerate(refl):
+        rows = np.nonzero(v)[0] + k           # v acts on rows k.. of W
+        assert rows.min() == k and rows.max() == m + k
+    Q = zo.thin_q(refl, m + n, n)
+    assert np.all(np.tril(Q[m:], -1) == 0.0)
+    assert np.linalg.norm(Q @ R - W) <= 1e-13 * np.linalg.norm(W)
