@@ -147,3 +147,34 @@ def test_stacked_qr_structure_of_section_3_1(m, n):
     Q = zo.thin_q(refl, m + n, n)
     assert np.all(np.tril(Q[m:], -1) == 0.0)
     assert np.linalg.norm(Q @ R - W) <= 1e-13 * np.linalg.norm(W)
+
+
+def test_compact_wy_block_merge():
+    # The merge the block T factor is built with: for reflector blocks V1, V2 with
+    # I - V1 T1 V1^T and I - V2 T2 V2^T, their product is I - V T V^T with
+    # V = [V1 V2] and T = [[T1, -T1 (V1^T V2) T2], [0, T2]]  (Schreiber-Van Loan)
+    p, k1, k2 = 30, 6, 5
+    refl, _ = zo.householder_qr(rng(21).standard_normal((p, k1 + k2)))
+    V = np.zeros((p, k1 + k2))
+    taus = []
+    for k, (v, tau) in enumerate(refl):
+        V[k:, k] = v
+        taus.append(tau)
+
+    def t_factor(Vb, tb):
+        # I - Vb T Vb^T = H_1 ... H_k, column by column
+        k = Vb.shape[1]
+        T = np.zeros((k, k))
+        for j in range(k):
+            T[j, j] = tb[j]
+            T[:j, j] = -tb[j] * T[:j, :j] @ (Vb[:, :j].T @ Vb[:, j])
+        return T
+
+    V1, V2 = V[:, :k1], V[:, k1:]
+    T1, T2 = t_factor(V1, taus[:k1]), t_factor(V2, taus[k1:])
+    T = np.block([[T1, -T1 @ (V1.T @ V2) @ T2], [np.zeros((k2, k1)), T2]])
+    prod = np.eye(p)
+    for k in range(k1 + k2):
+        prod = prod @ (np.eye(p) - taus[k] * np.outer(V[:, k], V[:, k]))
+    assert np.allclose(np.eye(p) - V @ T @ V.T, prod, atol=1e-14)
+    assert np.allclose(T, t_factor(V, taus), atol=1e-14)
