@@ -128,8 +128,9 @@ int zolo_coefficients(double ell, int r, double* c, double* a, double* Mhat, dou
 /* A-priori schedule (Table 1): l_0 = ell0 and l_{k+1} = Zhat(l_k; l_k) until
    1 - l_K <= 1e-15 or K = max_iter.  Writes ells[0..K] and used_qr[0..K-1]
    (QR form while (1+c_1)/(l_k^2+c_1) > 100) and returns K >= 0, or < 0 on
-   illegal arguments.  r = 0 selects r as zolo_opts_t does; *r_used receives
-   the r taken (may be NULL). */
+   illegal arguments.  r = 0 selects r as zolo_opts_t does (ZOLO_R_TUNED is
+   illegal here: a measured r belongs to a handle, see zolo_tuned_r); *r_used
+   receives the r taken (may be NULL). */
 int zolo_schedule(double ell0, int r, int max_iter, double* ells, int* used_qr, int* r_used);
 
 /* Device memory a zolo_pd (svd = 0) or zolo_svd (svd = 1) call on an m x n
