@@ -62,6 +62,9 @@ def test_schedule_r_choice_and_switch_match_oracle(zb):
         oe = zo.ell_schedule(1.0 / kappa, r)
         assert np.allclose(ells, oe, rtol=1e-14, atol=1e-16)
         assert qr == [zo.uses_qr(zo.zolotarev_coeffs(e, r), e) for e in oe[:-1]]
+    # a measured r belongs to a handle: the host-only schedule refuses it
+    with pytest.raises(zb.ZoloError):
+        zb.schedule(1e-8, zb.ZOLO_R_TUNED)
 
 
 def test_illegal_arguments_rejected_before_device_work(zb):
