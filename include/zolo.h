@@ -205,9 +205,11 @@ int zolo_dgemm(zolo_handle_t handle, int transA, int transB, int64_t m, int64_t 
    live in a 16 MiB file-scope device array that every GPU loading the library
    holds until the process exits.  Sizes whose slices do not fit are refused
    with ZOLO_ENOMEM before any device work: slices * (ceil128(rows) +
-   ceil64(cols)) * ceil64(k) * 2 bytes must stay within 16 MiB - 64.25 KiB,
-   with (rows, cols) = (n, m) when m < 128 and n > m, else (m, n) (so
-   m = n = k = 512 fits with 8 slices, 1024 x 1024 x 512 does not).  The
+   ceil64(cols)) * ceil64(k) * 2 bytes must stay within 16 MiB - 64.25 KiB
+   and ceil128(rows) + ceil64(cols) within 16384 exponents, with
+   (rows, cols) = (n, m) when m < 128 and n > m, else (m, n) (so
+   m = n = k = 512 fits with 8 slices, 1024 x 1024 x 512 does not, and a tall
+   9000 x 8 x 8 product fits).  Every size accepted here runs.  The
    first call on a device looks up the array's device address; make it before
    any stream capture.  All calls share the array: calls that overlap on the
    GPU race and must be serialised by the caller.  Matrices are device
@@ -263,7 +265,9 @@ const char* zolo_strerror(int code);
 /* ---- Diagnostics (no counterpart in the paper). ---------------------------
    zolo_kernel_launches: kernels this process has launched through libzolo.
    zolo_profile(1) resets the statistics and brackets every later launch with
-   a CUDA event pair on its stream (a few microseconds each); zolo_profile(0)
+   a CUDA event pair on its stream (a few microseconds each); while it is on,
+   zolo_pd_batched queues its matrices one after another on a single lane
+   without a graph, so that every pair times its kernel alone.  zolo_profile(0)
    stops.  zolo_profile_read synchronises on the pending events, fills up to
    max_entries records (one per kernel class: launches, summed device time,
    summed algorithmic flops and bytes as stated by each launch site) and

@@ -369,19 +369,34 @@ def zolo_svd_host(handle: Handle, A, o: ZoloOpts, U, S, V, stream=None, check=Tr
     return Info.from_c(info)
 
 
+def _gemm_shape(A, B, transA, transB):
+    """(m, n, k) of op(A) op(B); raises unless op(B)'s rows match op(A)'s columns."""
+    m = A.shape[1] if transA else A.shape[0]
+    k = A.shape[0] if transA else A.shape[1]
+    kb = B.shape[1] if transB else B.shape[0]
+    n = B.shape[0] if transB else B.shape[1]
+    if kb != k:
+        raise ValueError(f"op(A) is {m} x {k} but op(B) has {kb} rows")
+    return m, n, k
+
+
+def _check_c(C, m, n):
+    if tuple(C.shape) != (m, n):
+        raise ValueError(f"C must be {m} x {n}, got {tuple(C.shape)}")
+
+
 def zolo_dgemm(handle: Handle, A, B, C=None, alpha=1.0, beta=0.0, transA=False, transB=False,
                prec: int = ZOLO_FP64, slices: int = 0, stream=None, check=True):
     """C = alpha op(A) op(B) + beta C on the device (column-major float64 tensors)."""
     _colmajor(A, "A")
     _colmajor(B, "B")
-    m = A.shape[1] if transA else A.shape[0]
-    k = A.shape[0] if transA else A.shape[1]
-    n = B.shape[0] if transB else B.shape[1]
+    m, n, k = _gemm_shape(A, B, transA, transB)
     if C is None:
         C = empty_colmajor(m, n, A.device)
         if beta != 0.0:
             raise ValueError("beta != 0 needs C")
     _colmajor(C, "C")
+    _check_c(C, m, n)
     e = LIB.zolo_dgemm(handle.ptr, int(transA), int(transB), m, n, k, alpha,
                        ctypes.c_void_p(A.data_ptr()), _ld(A), ctypes.c_void_p(B.data_ptr()), _ld(B),
                        beta, ctypes.c_void_p(C.data_ptr()), _ld(C), prec, slices, _stream(stream))
@@ -397,9 +412,8 @@ def zolo_dgemm_noalloc(A, B, C, alpha=1.0, beta=0.0, transA=False, transB=False,
     _colmajor(A, "A")
     _colmajor(B, "B")
     _colmajor(C, "C")
-    m = A.shape[1] if transA else A.shape[0]
-    k = A.shape[0] if transA else A.shape[1]
-    n = B.shape[0] if transB else B.shape[1]
+    m, n, k = _gemm_shape(A, B, transA, transB)
+    _check_c(C, m, n)
     e = LIB.zolo_dgemm_noalloc(int(transA), int(transB), m, n, k, alpha,
                                ctypes.c_void_p(A.data_ptr()), _ld(A), ctypes.c_void_p(B.data_ptr()),
                                _ld(B), beta, ctypes.c_void_p(C.data_ptr()), _ld(C), slices,

@@ -625,17 +625,11 @@ cudaError_t run_split(const GemmArgs& g, SplitWork& w, cudaStream_t st) {
   p.batch = nb; p.reduce = g.reduce; p.swap = swap ? 1 : 0;
   p.err = w.err;
   using L = SmemLayout<BN, S>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    if ((err = cudaFuncSetAttribute(split_gemm_kernel<BN, S>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, L::kAlloc)) !=
-        cudaSuccess) {
-      if (std::getenv("ZOLO_DEBUG"))
-        std::fprintf(stderr, "zolo: cudaFuncSetAttribute(%d B): %s\n", L::kAlloc,
-                     cudaGetErrorString(err));
-      return err;
-    }
-    attr_set = true;
+  if ((err = smem_attr_once((const void*)split_gemm_kernel<BN, S>, L::kAlloc)) != cudaSuccess) {
+    if (std::getenv("ZOLO_DEBUG"))
+      std::fprintf(stderr, "zolo: cudaFuncSetAttribute(%d B): %s\n", L::kAlloc,
+                   cudaGetErrorString(err));
+    return err;
   }
   dim3 grid((unsigned)(Npad / BN), (unsigned)(Mpad / kTileM), g.reduce ? 1 : nb);
   ProfScope ps(kProfSplitGemm, st, gemm_flops(g), 0.0);
@@ -659,12 +653,11 @@ cudaError_t run_split(const GemmArgs& g, SplitWork& w, cudaStream_t st) {
 cudaError_t gemm_split(const GemmArgs& g, SplitWork& w, cudaStream_t st) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
   if (g.K <= 0 || g.batch > kGemmMaxBatch) return gemm_f64(g, st);
-  // batch entries per launch that the slice workspace holds
+  // batch entries per launch that the slice workspace and the exponent array hold
   const size_t per = split_slice_elems(g.M, g.N, g.K, 1, w.slices_s);
-  const int64_t rows = std::max<int64_t>(round_up(std::max(g.M, g.N), kTileM), 64) * 2 +
-                       (g.k_equilibrate ? round_up(g.K, kBK) : 0);
+  const size_t rows = split_exp_elems(g.M, g.N, g.K, 1, g.k_equilibrate);
   int gs = (int)std::min<size_t>(g.batch, w.slice_elems / std::max<size_t>(per, 1));
-  gs = (int)std::min<int64_t>(gs, (int64_t)(w.exp_elems / rows));
+  gs = (int)std::min<size_t>((size_t)gs, w.exp_elems / std::max<size_t>(rows, 1));
   if (gs < 1) return cudaErrorMemoryAllocation;
   auto run = [&](const GemmArgs& h) {
     return w.slices_s == 9 ? run_split<64, 9>(h, w, st) : run_split<64, 8>(h, w, st);
@@ -689,10 +682,8 @@ cudaError_t gemm_split(const GemmArgs& g, SplitWork& w, cudaStream_t st) {
 }
 
 void split_prepare() {
-  cudaFuncSetAttribute(split_gemm_kernel<64, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       SmemLayout<64, 8>::kAlloc);
-  cudaFuncSetAttribute(split_gemm_kernel<64, 9>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       SmemLayout<64, 9>::kAlloc);
+  smem_attr_once((const void*)split_gemm_kernel<64, 8>, SmemLayout<64, 8>::kAlloc);
+  smem_attr_once((const void*)split_gemm_kernel<64, 9>, SmemLayout<64, 9>::kAlloc);
   encode_fn();
 }
 
@@ -719,6 +710,15 @@ double split_time_ratio(const GemmArgs& g, const SplitWork& w) {
   const double tensor = pairs * 2.0 * ra * rb * kp * g.batch / 0.7e15;
   const double tsplit = slice_bytes / 4e12 + out_bytes / 5e12 + tensor + 30e-6;
   return tsplit / t64;
+}
+
+// Exponents run_split writes: one per padded tile row and column of every batch
+// entry, plus one per padded inner index with the equilibration.
+size_t split_exp_elems(int64_t M, int64_t N, int64_t K, int batch, int k_equilibrate) {
+  const bool swap = M < kTileM && N > M;
+  const int64_t rows = swap ? N : M, cols = swap ? M : N;
+  return (size_t)batch *
+         (size_t)(round_up(rows, kTileM) + round_up(cols, 64) + (k_equilibrate ? round_up(K, kBK) : 0));
 }
 
 size_t split_slice_elems(int64_t M, int64_t N, int64_t K, int batch, int S) {

@@ -75,8 +75,9 @@ extern "C" int zolo_dgemm_noalloc(int transA, int transB, int64_t m, int64_t n, 
   if (slices != 0 && slices != 8 && slices != 9) return -14;
   const int S = slices ? slices : 8;
   // sizes beyond what the fixed scratch holds are refused before any device work
+  // (the same counts gemm_split checks against, so a size accepted here runs)
   const size_t need = split_slice_elems(m, n, k, 1, S) * 2;
-  const size_t exps = (size_t)((m + 127) / 128 * 128 + (n + 127) / 128 * 128 + 256);
+  const size_t exps = split_exp_elems(m, n, k, 1, 0);
   if (need > kSliceBytes || exps * sizeof(int) > kExpBytes) return ZOLO_ENOMEM;
   void* base = nullptr;
   if (int e = scratch_address(&base)) return e;

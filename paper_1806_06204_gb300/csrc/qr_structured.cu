@@ -540,14 +540,12 @@ int64_t qr_partial_elems(int64_t m, int r) {
 cudaError_t structured_qr_q(const QrBuffers& b, int64_t m, int64_t n, int r, int* status,
                             cudaStream_t st, bool explicit_q) {
   constexpr int NB = kQrNB, NBb = kQrBlock;
-  static const bool smem_ready = [] {
+  {
     const int bytes = (int)(sizeof(double) * NB * kSmemPanelRows);
-    return cudaFuncSetAttribute(qr_panel_smem_kernel<NB, 1>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess &&
-           cudaFuncSetAttribute(qr_panel_smem_kernel<NB, kPanelCluster>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess;
-  }();
-  if (!smem_ready) return cudaErrorInvalidConfiguration;
+    if (smem_attr_once((const void*)qr_panel_smem_kernel<NB, 1>, bytes) != cudaSuccess ||
+        smem_attr_once((const void*)qr_panel_smem_kernel<NB, kPanelCluster>, bytes) != cudaSuccess)
+      return cudaErrorInvalidConfiguration;
+  }
   const int64_t ldw = m + n;
   const int64_t ldv = m + NBb;
   cudaError_t err;

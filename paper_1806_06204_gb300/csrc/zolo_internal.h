@@ -62,6 +62,10 @@ class ProfScope {
   void* a_ = nullptr;
 };
 
+// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) applies to the current device
+// only: set it once per (kernel, device), thread-safely.
+cudaError_t smem_attr_once(const void* func, int bytes);
+
 // Launch bookkeeping for graphs: kernels recorded at capture time are counted
 // when the graph is launched.
 void add_launches(int64_t n);
@@ -170,6 +174,8 @@ struct SplitWork {
 cudaError_t gemm_split(const GemmArgs& g, SplitWork& w, cudaStream_t st);
 // slice elements one call of the given shape needs
 size_t split_slice_elems(int64_t M, int64_t N, int64_t K, int batch, int S);
+// exponent entries (ints) one call of the given shape needs
+size_t split_exp_elems(int64_t M, int64_t N, int64_t K, int batch, int k_equilibrate);
 // The engine every contraction of the current call goes through: FP64 (DFMA)
 // when no split workspace is installed, the split tensor-core path otherwise.
 void set_split_engine(SplitWork* w);

@@ -28,7 +28,10 @@ def dev(a):
     return torch.from_numpy(np.asfortranarray(a)).cuda()
 
 
-@pytest.mark.parametrize("m,n,k,ta,tb,S", [(256, 192, 300, 0, 0, 8), (100, 257, 129, 1, 1, 9)])
+# the last case is a tall product with more than 8192 rows: its slices fit the
+# scratch and so must its exponents (one per padded row and column)
+@pytest.mark.parametrize("m,n,k,ta,tb,S", [(256, 192, 300, 0, 0, 8), (100, 257, 129, 1, 1, 9),
+                                           (9000, 8, 8, 0, 0, 8)])
 def test_noalloc_matches_allocating_entry_point_twice(zb, m, n, k, ta, tb, S):
     h = zb.Handle(0)
     try:
