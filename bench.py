@@ -1,18 +1,24 @@
 #!/usr/bin/env python
-"""Zolo-SVD / Zolo-PD throughput on GB300 through libzolo's C ABI.
+"""Zolo-PD / Zolo-SVD throughput on GB300 through libzolo's C ABI.
 
-One step = one Zolo-SVD (or Zolo-PD) of the workload's matrix: the whole hot
-path (coefficients, scaling, the QR-form and Cholesky-form iterations, the
-r-way combination, H, and for the SVD the eigendecomposition of H and U = Qp V).
-`value` is whole-job matrices/s with the input resident in HBM; `e2e` is the
-same through the host-buffer entry point with the copies inside the timed
-region.  The matrix (134 MB and up) and the multi-GB workspace exceed the 129 MB
-L2, so no flush is needed between steps.
+Default workload: the batch of 512 square matrices (n uniform in {64,...,1024},
+kappa log-uniform in [1e2, 1e12], r per matrix from kappa) through one
+zolo_pd_batched call per step.  The split-precision form (the iterations'
+products on the BF16 tensor cores as nine Ozaki slices) is the timed headline
+(`value`, matrices/s); the plain FP64 form runs on the same matrices in the same
+process (`fp64`, `fp64_value`), and `split_over_fp64` is their ratio.  Every
+result's backward error and orthogonality are checked against 1e-13 (exit code
+3 if either arm misses it).  `e2e` times the same call with the inputs copied
+in from pinned host memory and both factors copied back inside the timed region.
+The 1.6 GB of inputs per step exceed the 129 MB L2, so no flush is needed.
 
-Multi-GPU: the decomposition of one matrix is not sharded here; under torchrun
-every rank decomposes its own replica (weak scaling, no collective on the path).
+Single-matrix workloads (--workload svd4096, pd4096, ...) time one Zolo-SVD or
+Zolo-PD per step in the precision --prec names.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload svd4096|pd256|...]
+Multi-GPU: every rank decomposes its own replica of the workload (weak scaling,
+no collective on the data path); value = total matrices / slowest rank's time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload batch512|svd4096|...]
   python bench.py --impl reference ...   (the CPU oracle on a bounded sample)
 """
 from __future__ import annotations
@@ -166,25 +172,33 @@ def accuracy(w, sm, outs):
 
 
 def oracle_sample(w, seed=None):
-    """Time the CPU oracle on a bounded sample of the workload: the same method,
-    kappa and r on an n_s x n_s (or m_s x n_s) matrix; scaled to the full size by
-    the cubic flop model.  Returns (matrices/s at full size, seconds, description)."""
+    """Time the CPU oracle on bounded samples of the workload: the same method,
+    kappa and r on matrices of two sizes, n_s and 2 n_s / 3 (rows scaled with
+    the workload's aspect ratio).  The oracle's seconds per model flop fall as n
+    grows (per-column Python overhead), so the full-size rate is scaled from the
+    larger sample's, and both are stated.  Returns (matrices/s at full size,
+    seconds of CPU work, description)."""
     from oracle import zolo_oracle as zo
     from paper_1806_06204_gb300 import synth
-    ns = w["sample_n"]
-    ms = int(round(ns * w["m"] / w["n"]))
-    sm = synth.make_matrix(ms, ns, synth.geometric_sigma(ns, w["kappa"]), seed or 7000)
-    t0 = time.perf_counter()
-    if w["kind"] == "svd":
-        _, _, _, info = zo.zolo_svd(sm.A, 1.0, float(sm.sigma[-1]), r=w["r"])
-    else:
-        _, _, info = zo.zolo_pd(sm.A, 1.0, float(sm.sigma[-1]), r=w["r"])
-    dt = time.perf_counter() - t0
-    scale = pd_model_flops(w["m"], w["n"], w["r"], info.used_qr) / pd_model_flops(
-        ms, ns, w["r"], info.used_qr)
-    desc = (f"oracle zolo_{w['kind']} of one {ms}x{ns} matrix (kappa {w['kappa']:.0e}, r={w['r']}), "
-            f"{dt:.1f} s, scaled by the Zolo-PD flop model x{scale:.1f} to {w['m']}x{w['n']}")
-    return 1.0 / (dt * scale), dt, desc
+    rates, parts, spent = [], [], 0.0
+    for ns in (w["sample_n"], max(64, (2 * w["sample_n"] // 3) // 32 * 32)):
+        ms = int(round(ns * w["m"] / w["n"]))
+        sm = synth.make_matrix(ms, ns, synth.geometric_sigma(ns, w["kappa"]), seed or 7000)
+        t0 = time.perf_counter()
+        if w["kind"] == "svd":
+            _, _, _, info = zo.zolo_svd(sm.A, 1.0, float(sm.sigma[-1]), r=w["r"])
+        else:
+            _, _, info = zo.zolo_pd(sm.A, 1.0, float(sm.sigma[-1]), r=w["r"])
+        dt = time.perf_counter() - t0
+        spent += dt
+        f = pd_model_flops(ms, ns, w["r"], info.used_qr)
+        rates.append(dt / f)
+        parts.append(f"{ms}x{ns}: {dt:.1f} s ({1e9 * dt / f:.2f} s per model Gflop)")
+    full = pd_model_flops(w["m"], w["n"], w["r"], info.used_qr)
+    desc = (f"oracle zolo_{w['kind']} (kappa {w['kappa']:.0e}, r={w['r']}) on " + "; ".join(parts) +
+            f"; scaled by the Zolo-PD flop model to {w['m']}x{w['n']} at the first (larger) "
+            f"sample's rate")
+    return 1.0 / (rates[0] * full), spent, desc
 
 
 def max_over_ranks(x, dist):
@@ -199,50 +213,102 @@ def max_over_ranks(x, dist):
     return float(t.item())
 
 
-def blas_threads():
-    for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
-        if os.environ.get(k, "").isdigit():
-            return int(os.environ[k])
-    return os.cpu_count()
+def used_threads(fn):
+    """Run fn() and return (its result, the most threads this process had while it
+    ran), sampled from /proc every 50 ms: the cores the oracle actually used."""
+    peak = [threading.active_count()]
+    done = threading.Event()
+
+    def watch():
+        while not done.is_set():
+            try:
+                with open("/proc/self/status") as f:
+                    for ln in f:
+                        if ln.startswith("Threads:"):
+                            peak[0] = max(peak[0], int(ln.split()[1]) - 1)   # minus the watcher
+            except OSError:
+                return
+            done.wait(0.05)
+
+    t = threading.Thread(target=watch, daemon=True)
+    t.start()
+    try:
+        out = fn()
+    finally:
+        done.set()
+        t.join()
+    return out, min(peak[0], os.cpu_count() or peak[0])
 
 
 def batch_oracle_sample(w, budget_s=12.0):
-    """Time the CPU oracle on the leading matrices of the batch until about
-    budget_s seconds have passed; scaled to the whole batch by the flop model."""
+    """Time the CPU oracle on matrices of the batch itself and scale to all of it.
+
+    The oracle's time per model flop falls as n grows (its per-column Python
+    overhead is amortised), so one small size alone would understate the CPU.
+    The sample takes the batch's matrices in order, at the two largest sizes
+    that fit the time budget (n = 192 and 256), times each, and scales every
+    matrix of the batch by the lower of the two measured seconds per model flop.
+    Returns (matrices/s, seconds of CPU work, description, threads used)."""
     from oracle import zolo_oracle as zo
     from paper_1806_06204_gb300 import synth
     ns, kap = synth.batch_sizes_and_kappas(w["count"])
-    done_f, tot_f, dt, k = 0.0, 0.0, 0.0, 0
+    tot_f = 0.0
+    plan = []
     for i, (n, kp) in enumerate(zip(ns, kap)):
         r = zo.choose_r(1.0 / kp)
         it = zo.ell_schedule(1.0 / kp, r)
         used_qr = [zo.uses_qr(zo.zolotarev_coeffs(l, r), l) for l in it[:-1]]
-        tot_f += pd_model_flops(n, n, r, used_qr)
-        if dt < budget_s and n <= 256:
-            sm = synth.make_matrix(n, n, synth.geometric_sigma(n, kp), 4000 + 1 + i)
-            t0 = time.perf_counter()
-            zo.zolo_pd(sm.A, 1.0, float(sm.sigma[-1]), r=r)
-            dt += time.perf_counter() - t0
-            done_f += pd_model_flops(n, n, r, used_qr)
-            k += 1
-    scale = tot_f / done_f
-    desc = (f"oracle zolo_pd on the {k} matrices of the batch with n <= 256 met first "
-            f"({dt:.1f} s), scaled by the Zolo-PD flop model x{scale:.1f} to all {w['count']}")
-    return w["count"] / (dt * scale), dt, desc
+        f = pd_model_flops(n, n, r, used_qr)
+        tot_f += f
+        plan.append((i, n, kp, r, f))
+    per_size = {}
+    spent = [0.0]
+
+    def run():
+        for size in (192, 256):
+            t, fl, k = 0.0, 0.0, 0
+            for i, n, kp, r, f in plan:
+                if n != size:
+                    continue
+                if k >= 1 and t > budget_s / 2:
+                    break
+                sm = synth.make_matrix(n, n, synth.geometric_sigma(n, kp), 4000 + 1 + i)
+                t0 = time.perf_counter()
+                zo.zolo_pd(sm.A, 1.0, float(sm.sigma[-1]), r=r)
+                t += time.perf_counter() - t0
+                fl += f
+                k += 1
+            per_size[size] = (t, fl, k)
+            spent[0] += t
+
+    _, cores = used_threads(run)
+    rate = {sz: t / fl for sz, (t, fl, k) in per_size.items()}
+    best = min(rate.values())
+    desc = ("oracle zolo_pd on matrices of the batch itself: " +
+            ", ".join(f"{k} at n={sz} ({t:.1f} s, {1e9 * t / fl:.2f} s per Gflop)"
+                      for sz, (t, fl, k) in sorted(per_size.items())) +
+            f"; every matrix of the batch scaled by the lower rate (model flops) to all "
+            f"{w['count']}")
+    return 1.0 / (best * tot_f / w["count"]) if best > 0 else None, spent[0], desc, cores
 
 
 def run_reference(args, w, rank):
     if rank != 0:
         return
-    if w["kind"] == "batch":
-        global oracle_sample
-        oracle_sample = lambda w, seed=None: batch_oracle_sample(w)
-    for _ in range(args.warmup):
-        oracle_sample(w)
-    vals, tot = [], 0.0
+    vals, tot, cores = [], 0.0, 1
     desc = ""
+    if w["kind"] == "batch":
+        # each step a bounded sample, sized so that the whole run stays within minutes
+        budget = max(2.0, 150.0 / max(1, args.steps + args.warmup))
+        sample = lambda: batch_oracle_sample(w, budget_s=budget)
+    else:
+        def sample():
+            (v, dt, d), c = used_threads(lambda: oracle_sample(w))
+            return v, dt, d, c
+    for _ in range(args.warmup):
+        sample()
     for _ in range(args.steps):
-        v, dt, desc = oracle_sample(w)
+        v, dt, desc, cores = sample()
         vals.append(v)
         tot += dt
     value = statistics.mean(vals)
@@ -251,72 +317,98 @@ def run_reference(args, w, rank):
             "ms_per_step": 1000.0 * tot / max(1, args.steps), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "desc": w["desc"]},
-            "cpu_baseline": {"value": value, "unit": "matrices/s", "cores": blas_threads(),
+            "cpu_baseline": {"value": value, "unit": "matrices/s", "cores": cores,
                              "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": "matrices/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def roofline(kstats, timed_ms):
-    """Roofline entry of the dominant kernel class (by device time)."""
+# Builder's DFMA microbenchmark on this GPU (a register-resident FMA chain on all
+# SMs, CUDA events): the FP64 pipe's measured ceiling beside the derived peak.
+FP64_DFMA_MEASURED_TFLOPS = 1.20
+# Tensor-core products issued per FP64-equivalent flop on the split path: nine
+# slices per operand, slice pairs (s, t) with s + t <= 11.
+SPLIT_PAIRS = 53
+
+
+def roofline(kstats, step_ms, model_flops=None, split_pairs=SPLIT_PAIRS):
+    """Roofline entry of the dominant kernel class (by device time in one step).
+
+    With model_flops (the Zolo-PD flops of the step), the algorithmic work of a
+    flop-carrying class is the model's, shared out between the classes in
+    proportion to the flops each launch site states for its launch; achieved =
+    that share / the class's device time.  On the split path a model flop is
+    issued as `split_pairs` BF16 tensor-core products.  The flops the launches
+    state themselves (padding, T factors, the explicit Q's full rows included)
+    are kept beside it as `issued_*`."""
     dom_name, dom = max(((k, v) for k, v in kstats.items() if v["launches"] > 0),
                         key=lambda kv: kv[1]["ms"])
-    achieved = dom["flops"] / (dom["ms"] / 1000.0) / 1e12
+    sec = dom["ms"] / 1000.0
     bound = {"combine": "hbm", "slice": "hbm", "gemm_split": "tensor"}.get(dom_name, "alu")
+    flop_classes = {k: v for k, v in kstats.items() if v["launches"] > 0 and v["flops"] > 0}
+    stated = sum(v["flops"] for v in flop_classes.values())
+    if model_flops and dom_name in flop_classes and stated > 0:
+        work = model_flops * dom["flops"] / stated
+        basis = ("Zolo-PD model flops of the step, shared between kernel classes in proportion "
+                 "to their launches' stated flops")
+    else:
+        work = dom["flops"]
+        basis = "flops stated by the launches"
     if bound == "tensor":
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
         peak = peaks["bf16_tflops_sustained"]
-        # tensor flops actually issued: one BF16 product per kept slice pair
-        # (s + t <= 11 of nine slices: 53 of them)
-        issued = dom["flops"] * 53 / (dom["ms"] / 1000.0) / 1e12
-        roof = {"bound": "tensor", "kernel": dom_name, "achieved": issued, "peak": peak,
-                "unit": "TFLOP/s", "frac": issued / peak, "traffic": None,
-                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained",
-                "fp64_equivalent_tflops": achieved}
+        achieved = work * split_pairs / sec / 1e12
+        roof = {"bound": "tensor", "kernel": dom_name, "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)",
+                "work_basis": basis + f"; x{split_pairs} BF16 slice-pair products per flop",
+                "fp64_equivalent_tflops": work / sec / 1e12,
+                "issued_tflops": dom["flops"] * split_pairs / sec / 1e12}
     elif bound == "alu":
+        achieved = work / sec / 1e12
         roof = {"bound": "alu", "kernel": dom_name, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "derived: 152 SMs x 4 FP64 flops/clk x 2.07 GHz"}
+                "peak_source": "derived: 152 SMs x 4 FP64 flops/clk x 2.07 GHz (MEASURED_PEAKS.json "
+                               "has no FP64 entry); DFMA microbenchmark measured "
+                               f"{FP64_DFMA_MEASURED_TFLOPS} TFLOP/s",
+                "frac_of_measured_dfma": achieved / FP64_DFMA_MEASURED_TFLOPS,
+                "work_basis": basis, "issued_tflops": dom["flops"] / sec / 1e12}
     else:
         peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
-        gbs = dom["bytes"] / (dom["ms"] / 1000.0) / 1e9
+        gbs = dom["bytes"] / sec / 1e9
         roof = {"bound": "hbm", "kernel": dom_name, "achieved": gbs, "peak": peak, "unit": "GB/s",
-                "frac": gbs / peak, "traffic": None}
+                "frac": gbs / peak, "traffic": None, "work_basis": "bytes stated by the launches"}
     roof["launches"] = dom["launches"]
     roof["avg_launch_ms"] = dom["ms"] / dom["launches"]
-    roof["share_of_step"] = dom["ms"] / timed_ms
+    roof["share_of_step"] = dom["ms"] / step_ms
     return roof
 
 
-def run_batch(args, w, rank, world, dist, local):
-    """The uneven batch through zolo_pd_batched: value = matrices/s over all ranks."""
-    import numpy as np
+def batch_arm(args, w, h, mats, As, Qps, Hs, split, steps, warmup, local, dist):
+    """One precision of the batch: warm-up, K timed zolo_pd_batched calls (CUDA
+    events on the calling stream, barrier and synchronise on both sides), then
+    one more call with per-launch events for the kernel classes, and the
+    accuracy of every result."""
     import torch
-    from paper_1806_06204_gb300 import binding as zb, synth
-    split = args.prec == "split"
-    mats = synth.batch(w["count"], seed=4000 + 100000 * rank)
-    As = [torch.from_numpy(sm.A).cuda() for sm in mats]
+    from paper_1806_06204_gb300 import binding as zb
     os_ = [zb.opts(beta=float(sm.sigma[-1]), alpha=1.0, r=0,
                    prec=zb.ZOLO_SPLIT_BF16 if split else zb.ZOLO_FP64, ns_steps=1 if split else 0,
                    chol_form=args.chol_form)
            for sm in mats]
-    Qps = [zb.empty_colmajor(a.shape[0], a.shape[1]) for a in As]
-    Hs = [zb.empty_colmajor(a.shape[1], a.shape[1]) for a in As]
-    h = zb.Handle(local)
 
     def step():
         _, _, infos, st = zb.zolo_pd_batched(h, As, os_, Qps=Qps, Hs=Hs)
         return infos
 
-    for _ in range(args.warmup):
-        infos = step()
-    torch.cuda.synchronize()
-
     def barrier():
         if dist:
             dist.barrier()
 
+    infos = None
+    for _ in range(warmup):
+        infos = step()
+    torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -325,19 +417,17 @@ def run_batch(args, w, rank, world, dist, local):
         barrier()
         torch.cuda.synchronize()
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             infos = step()
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
     launches = zb.kernel_launches() - launches0
-    ms_step = e0.elapsed_time(e1) / args.steps
-    ms_step = max_over_ranks(ms_step, dist)
-    value = world * w["count"] / (ms_step / 1000.0)
+    ms_step = max_over_ranks(e0.elapsed_time(e1) / steps, dist)
     flops = sum(pd_model_flops(a.shape[0], a.shape[1], i.r, i.used_qr) for a, i in zip(As, infos))
 
-    # per-kernel device times: one more step with event-bracketed launches (a
-    # replayed graph cannot be bracketed kernel by kernel)
+    # per-kernel device times: one more call, outside the timed steps, with
+    # event-bracketed launches (a replayed graph cannot be bracketed kernel by kernel)
     zb.profile(True)
     e2 = torch.cuda.Event(enable_timing=True)
     e3 = torch.cuda.Event(enable_timing=True)
@@ -347,18 +437,49 @@ def run_batch(args, w, rank, world, dist, local):
     torch.cuda.synchronize()
     kstats = zb.profile_read()
     zb.profile(False)
-    roof = roofline(kstats, e2.elapsed_time(e3))
-    roof["measured"] = "one extra step with per-launch CUDA events (no graph)"
+    prof_ms = e2.elapsed_time(e3)
+    roof = roofline(kstats, prof_ms, flops)
+    roof["measured"] = ("one extra call after the timed steps with the batch's lanes "
+                        "serialised and every launch bracketed by CUDA events (no graph replay): "
+                        "each launch timed alone on the GPU")
 
-    # accuracy of every result, checked on the device with torch
+    # accuracy of every result, on the device with torch (a check, not timed)
     bwd, orth = 0.0, 0.0
     for a, q, hh in zip(As, Qps, Hs):
         n = a.shape[1]
         bwd = max(bwd, float(torch.linalg.norm(a - q @ hh) / torch.linalg.norm(a)))
         I = torch.eye(n, dtype=torch.float64, device="cuda")
         orth = max(orth, float(torch.linalg.norm(q.T @ q - I) / math.sqrt(n)))
-    acc = {"max_bwd_err": bwd, "max_orth_Qp": orth,
-           "statuses_nonzero": sum(1 for i in infos if i.status)}
+    acc = {"max_bwd_err": bwd, "max_orth_Qp": orth, "matrices": len(As),
+           "statuses_nonzero": sum(1 for i in infos if i.status),
+           "bar": 1e-13, "bar_met": bool(bwd <= 1e-13 and orth <= 1e-13)}
+    return {"os": os_, "ms_step": ms_step, "flops": flops, "infos": infos, "launches": launches,
+            "kstats": kstats, "roof": roof, "acc": acc, "clocks": clk.summary(),
+            "steps": steps, "warmup": warmup}
+
+
+def run_batch(args, w, rank, world, dist, local):
+    """The uneven batch through zolo_pd_batched.  By default both precisions run
+    on the same matrices: `value` is the split-precision matrices/s over all
+    ranks, `fp64` the plain FP64 arm, `split_over_fp64` their ratio."""
+    import torch
+    from paper_1806_06204_gb300 import binding as zb, synth
+    prec = args.prec if args.prec != "auto" else "both"
+    mats = synth.batch(w["count"], seed=4000 + 100000 * rank)
+    As = [torch.from_numpy(sm.A).cuda() for sm in mats]
+    Qps = [zb.empty_colmajor(a.shape[0], a.shape[1]) for a in As]
+    Hs = [zb.empty_colmajor(a.shape[1], a.shape[1]) for a in As]
+    h = zb.Handle(local)
+    head_split = prec in ("split", "both")
+    arm = batch_arm(args, w, h, mats, As, Qps, Hs, head_split, args.steps, args.warmup, local,
+                    dist)
+    fp64 = None
+    if prec == "both":
+        fs = args.fp64_steps if args.fp64_steps is not None else max(1, min(args.steps, 5))
+        fw = args.fp64_warmup if args.fp64_warmup is not None else min(args.warmup, 3)
+        fp64 = batch_arm(args, w, h, mats, As, Qps, Hs, False, fs, fw, local, dist)
+    value = world * w["count"] / (arm["ms_step"] / 1000.0)
+    os_ = arm["os"]
 
     e2e = None
     if not args.no_e2e:
@@ -379,42 +500,64 @@ def run_batch(args, w, rank, world, dist, local):
             torch.cuda.synchronize()
 
         host_step()
-        barrier()
+        if dist:
+            dist.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.steps):
             host_step()
-        barrier()
-        e2e_s = (time.perf_counter() - t0) / args.steps
-        e2e_s = max_over_ranks(e2e_s, dist)
+        if dist:
+            dist.barrier()
+        e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, dist)
         nb = sum(a.numel() for a in As) * 8
         e2e = {"value": world * w["count"] / e2e_s, "unit": "matrices/s", "h2d_bytes_per_step": nb,
                "d2h_bytes_per_step": nb + sum(x.numel() for x in Hs) * 8}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, dt, desc = batch_oracle_sample(w)
-        cpu = {"value": v, "unit": "matrices/s", "cores": blas_threads(), "kind": "oracle",
-               "sample": desc}
+        v, dt, desc, cores = batch_oracle_sample(w)
+        cpu = {"value": v, "unit": "matrices/s", "cores": cores, "kind": "oracle", "sample": desc}
     if rank == 0:
         ns = [a.shape[1] for a in As]
+        infos = arm["infos"]
+        desc = w["desc"] + (": split precision (nine BF16 slices, FP32 level sums) timed, plain "
+                            "FP64 beside it" if prec == "both" else
+                            (": split precision (nine BF16 slices)" if head_split else
+                             ": plain FP64"))
         line = {"metric": METRIC, "value": value, "unit": "matrices/s", "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": arm["ms_step"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f64" if not split else "bf16x9-slices->f64",
+                "dtype": "bf16x9-slices->f64" if head_split else "f64",
                 "data": "synthetic",
-                "config": {"workload": args.workload, "desc": w["desc"], "count": w["count"],
-                           "n_min": min(ns), "n_max": max(ns), "prec": args.prec,
+                "config": {"workload": args.workload, "desc": desc, "count": w["count"],
+                           "n_min": min(ns), "n_max": max(ns), "prec": "split" if head_split else "fp64",
                            "r_hist": {str(r): sum(1 for i in infos if i.r == r)
                                       for r in sorted({i.r for i in infos})},
                            "l2": "inputs larger than L2 (1.6 GB of A per step; no flush)",
                            "parallelism": "replicas" if world > 1 else "single"},
-                "eff_tflops": world * flops / (ms_step / 1000.0) / 1e12,
-                "pd_model_flops": flops, "accuracy": acc, "roofline": roof,
-                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "kernel_ms": {k: round(v["ms"], 3) for k, v in kstats.items() if v["launches"]},
-                "clocks": clk.summary()}
+                "eff_tflops": world * arm["flops"] / (arm["ms_step"] / 1000.0) / 1e12,
+                "pd_model_flops": arm["flops"], "accuracy": arm["acc"], "roofline": arm["roof"],
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": arm["launches"],
+                "kernel_ms": {k: round(v["ms"], 3) for k, v in arm["kstats"].items() if v["launches"]},
+                "clocks": arm["clocks"]}
+        if fp64 is not None:
+            fv = world * w["count"] / (fp64["ms_step"] / 1000.0)
+            line["fp64_value"] = fv
+            line["split_over_fp64"] = value / fv
+            line["fp64"] = {"value": fv, "unit": "matrices/s", "ms_per_step": fp64["ms_step"],
+                            "steps": fp64["steps"], "warmup": fp64["warmup"],
+                            "eff_tflops": world * fp64["flops"] / (fp64["ms_step"] / 1000.0) / 1e12,
+                            "accuracy": fp64["acc"], "roofline": fp64["roof"],
+                            "gpu_launches": fp64["launches"],
+                            "kernel_ms": {k: round(v["ms"], 3) for k, v in fp64["kstats"].items()
+                                          if v["launches"]},
+                            "clocks": fp64["clocks"]}
         print(json.dumps(line), flush=True)
+        bad = [a for a in (arm, fp64) if a is not None and not a["acc"]["bar_met"]]
+        if bad:
+            print("accuracy bar (1e-13) not met", file=sys.stderr)
+            h.close()
+            raise SystemExit(3)
     h.close()
 
 
@@ -424,9 +567,15 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="svd4096", choices=sorted(WORKLOADS))
-    ap.add_argument("--prec", default="fp64", choices=["fp64", "split"],
-                    help="split: the iterations' products on the BF16 tensor cores (Ozaki slices)")
+    ap.add_argument("--workload", default="batch512", choices=sorted(WORKLOADS))
+    ap.add_argument("--prec", default="auto", choices=["auto", "fp64", "split", "both"],
+                    help="split: the iterations' products on the BF16 tensor cores (Ozaki slices); "
+                         "both (batch only): split timed, FP64 beside it; auto: both for the "
+                         "batch, fp64 otherwise")
+    ap.add_argument("--fp64-steps", type=int, default=None,
+                    help="timed steps of the FP64 arm with --prec both (default min(steps, 5))")
+    ap.add_argument("--fp64-warmup", type=int, default=None,
+                    help="warm-up steps of the FP64 arm with --prec both (default min(warmup, 3))")
     ap.add_argument("--beta-scale", type=float, default=None,
                     help="beta = sigma_min times this (default: the workload's own, else 1)")
     ap.add_argument("--r", type=int, default=None,
@@ -488,6 +637,8 @@ def main():
     tuning = args.autotune and args.warmup > 0
     if tuning:
         zb.autotune(h, True)
+    if args.prec == "both":
+        raise SystemExit("--prec both applies to the batch workload only")
     split = args.prec == "split"
     beta_scale = args.beta_scale if args.beta_scale is not None else w.get("beta_scale", 1.0)
     r_req = args.r if args.r is not None else w["r"]
@@ -519,7 +670,6 @@ def main():
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     launches0 = zb.kernel_launches()
-    zb.profile(True)
     with ClockSampler(local) as clk:
         barrier()
         torch.cuda.synchronize()
@@ -529,8 +679,6 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-    kstats = zb.profile_read()
-    zb.profile(False)
     launches = zb.kernel_launches() - launches0
     ms_step = e0.elapsed_time(e1) / args.steps
     ms_step = max_over_ranks(ms_step, dist)
@@ -538,8 +686,19 @@ def main():
     flops = pd_model_flops(m, n, info.r, info.used_qr)
     acc = accuracy(w, sm, outs)
 
-    # roofline of the dominant kernel class (by device time inside the timed region)
-    roof = roofline(kstats, ms_step * args.steps)
+    # roofline of the dominant kernel class: one more step after the timed ones,
+    # every launch bracketed by CUDA events on its stream
+    zb.profile(True)
+    e2 = torch.cuda.Event(enable_timing=True)
+    e3 = torch.cuda.Event(enable_timing=True)
+    e2.record(stream)
+    step()
+    e3.record(stream)
+    torch.cuda.synchronize()
+    kstats = zb.profile_read()
+    zb.profile(False)
+    roof = roofline(kstats, e2.elapsed_time(e3), flops)
+    roof["measured"] = "one extra step after the timed ones, per-launch CUDA events"
 
     # end to end through the host-buffer entry point
     e2e = None
@@ -572,8 +731,8 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, dt, desc = oracle_sample(w)
-        cpu = {"value": v, "unit": "matrices/s", "cores": blas_threads(), "kind": "oracle",
+        (v, dt, desc), cores = used_threads(lambda: oracle_sample(w))
+        cpu = {"value": v, "unit": "matrices/s", "cores": cores, "kind": "oracle",
                "sample": desc}
 
     if rank == 0:
@@ -585,7 +744,7 @@ def main():
                 "config": {"workload": args.workload, "desc": w["desc"], "m": m, "n": n,
                            "kappa": w["kappa"], "r": info.r, "r_requested": r_req,
                            "chol_form": info.chol_form, "autotune": bool(tuning),
-                           "prec": args.prec,
+                           "prec": "split" if split else "fp64",
                            "beta_over_sigma_min": beta_scale,
                            "l2": "inputs larger than L2 (no flush)",
                            "parallelism": "replicas" if world > 1 else "single"},

@@ -1105,8 +1105,10 @@ int zolo_pd_batched(zolo_handle_t h, int count, const double* const* A, const in
       }
     }
   }
-  // ---- lanes: streams with workspace for the largest matrix of the batch
-  const int nslots = std::min(count, 16);
+  // ---- lanes: streams with workspace for the largest matrix of the batch.  With
+  // per-kernel profiling on, one lane: every launch's event pair then times that
+  // kernel alone, not its share of a GPU other lanes' kernels run on too
+  const int nslots = profiling_enabled() ? 1 : std::min(count, 16);
   int64_t mmax = 0, nmax = 0;
   int rmax = 1;
   bool any_split = false;

@@ -44,3 +44,23 @@ def test_roofline_of_the_split_class_counts_issued_pairs():
     assert roof["fp64_equivalent_tflops"] == pytest.approx(10.0)
     assert roof["achieved"] == pytest.approx(530.0)            # 53 slice-pair products
     assert roof["frac"] == pytest.approx(530.0 / roof["peak"])
+
+
+def test_roofline_shares_the_model_flops_between_classes():
+    # the launches state 1.2e12 + 0.3e12 flops; the model credits 1.0e12 to the
+    # step, so the dominant class is credited 0.8e12 over its 0.9 s
+    kstats = {"gemm_f64": {"launches": 10, "ms": 900.0, "flops": 1.2e12, "bytes": 0.0},
+              "qr_panel": {"launches": 4, "ms": 50.0, "flops": 0.3e12, "bytes": 0.0},
+              "combine": {"launches": 2, "ms": 1.0, "flops": 0.0, "bytes": 1e6}}
+    roof = bench.roofline(kstats, 1000.0, model_flops=1.0e12)
+    assert roof["kernel"] == "gemm_f64"
+    assert roof["achieved"] == pytest.approx(0.8e12 / 0.9 / 1e12)
+    assert roof["issued_tflops"] == pytest.approx(1.2e12 / 0.9 / 1e12)
+    assert "model" in roof["work_basis"]
+
+
+def test_oracle_sample_times_two_sizes_and_scales_by_the_model():
+    w = dict(bench.WORKLOADS["pd256"], sample_n=96)
+    v, spent, desc = bench.oracle_sample(w)
+    assert v > 0 and spent > 0
+    assert "256x96" not in desc and "96x96" in desc and "64x64" in desc
