@@ -42,7 +42,8 @@ enum {
   ZOLO_EEIG = 6,       /* the Jacobi eigensolver did not converge               */
   ZOLO_ETIMEOUT = 7,   /* a bounded wait inside a tensor-core kernel expired    */
   ZOLO_EIO = 8,        /* a tuning-cache file could not be written or read      */
-  ZOLO_EINVAL = 9      /* a tuning-cache file is malformed or from another GPU  */
+  ZOLO_EINVAL = 9,     /* a tuning-cache file is malformed or from another GPU  */
+  ZOLO_ECOMM = 10      /* the caller's sum over ranks (zolo_pd_sharded) failed  */
 };
 
 /* Arithmetic of the contractions.  ZOLO_FP64: plain FP64 on the FP64 FMA pipe.
@@ -158,6 +159,42 @@ int zolo_svd(zolo_handle_t handle, const double* A, int64_t m, int64_t n, int64_
              double* U, int64_t ldu, double* S, double* V, int64_t ldv,
              const zolo_opts_t* opts, zolo_info_t* info, void* stream);
 
+/* ---- Shifts sharded over ranks (Section 3.2, Algorithm 3): the paper splits
+   the processes into r groups, group j factors the j-th shifted problem and
+   DGSUM2D sums the r terms T_j.  Here each of `nranks` ranks (one per GPU,
+   each holding all of A) takes the contiguous block of the r shifts that
+   zolo_shift_range gives it, forms the sum S_rank of its own T_j for every
+   iteration, and hands S_rank to the caller's `sum` function, which must
+   replace it by the elementwise sum over all ranks (an all-reduce, e.g. NCCL
+   or torch.distributed); X_{k+1} = M_hat (X_k + S) then follows on every rank
+   alike, as do the Newton-Schulz steps and H.
+
+   zolo_shift_range: shifts [*j0, *j1) (0-based, j1 - j0 of them, possibly
+   none when nranks > r) of rank `rank`: consecutive blocks, the first r mod
+   nranks ranks one larger.  Host only.  Returns 0 or -i for argument i.
+
+   zolo_sum_fn: called once per iteration (more after a Cholesky breakdown)
+   with buf = a device array of `count` = m n + 1 doubles on the handle's
+   device (S, column-major, ld m, then this rank's Cholesky-breakdown flag as
+   0.0 / 1.0) and the call's stream; it must leave in buf, for work queued on
+   that stream after it returns, the elementwise sum of every rank's buf (the
+   same order of summation on every rank, so that all ranks continue with
+   identical bits), and return 0; anything else makes the call return
+   ZOLO_ECOMM.  A non-zero summed flag makes every rank redo that iteration in
+   the QR form.
+
+   zolo_pd_sharded: as zolo_pd, with every rank passing the same A (bitwise),
+   opts and nranks; opts.r must not be ZOLO_R_TUNED and opts.posteriori must be
+   0 (-10 otherwise).  rank (argument 13) in [0, nranks), nranks (14) >= 1,
+   sum (15) may be NULL only when nranks = 1, ctx is passed to sum untouched.
+   Every rank writes the same Qp and H. */
+typedef int (*zolo_sum_fn)(double* buf, int64_t count, void* stream, void* ctx);
+int zolo_shift_range(int r, int rank, int nranks, int* j0, int* j1);
+int zolo_pd_sharded(zolo_handle_t handle, const double* A, int64_t m, int64_t n, int64_t lda,
+                    double* Qp, int64_t ldq, double* H, int64_t ldh, const zolo_opts_t* opts,
+                    zolo_info_t* info, void* stream, int rank, int nranks, zolo_sum_fn sum,
+                    void* ctx);
+
 /* Many polar decompositions in one call.  Matrix i is A[i] (m[i] x n[i],
    leading dimension lda[i]) with its own options opts[i] (its own r, bounds,
    precision); results go to Qp[i] (ldq[i]) and H[i] (ldh[i]), and info[i].
@@ -258,6 +295,26 @@ int zolo_autotune(zolo_handle_t handle, int enable);
 int zolo_tuned_r(zolo_handle_t handle, int64_t m, int64_t n, int prec, double ell0);
 int zolo_tune_save(zolo_handle_t handle, const char* path);
 int zolo_tune_load(zolo_handle_t handle, const char* path);
+
+/* ---- Test hook of the bounded waits (no counterpart in the paper). --------
+   Every wait inside a kernel of this library is bounded: when it gives up it
+   sets an error flag, the kernel lets the copies and tensor-core operations it
+   has in flight finish (with bounded waits), releases its tensor memory and
+   returns, and the call returns ZOLO_ETIMEOUT; the context stays usable.
+   zolo_debug_stall makes that path run on purpose, for tests: from then on,
+   calls on this handle make the named kernel first wait, for `ns` nanoseconds
+   (0 .. 1e9), on a barrier or flag that nothing completes:
+     ZOLO_STALL_SPLIT_GEMM: the MMA-issuing thread of every split-precision
+       product (opts.prec = ZOLO_SPLIT_BF16, zolo_dgemm with the split path),
+       on an mbarrier no thread or copy arrives at;
+     ZOLO_STALL_JACOBI32: block 0 of the first FP32 sweep of zolo_svd's
+       eigensolver, on a flag no thread sets (the other blocks leave the grid
+       barrier when they see the error flag).
+   where = 0 switches it off.  Returns 0, -1 (NULL handle), -2 (where) or -3
+   (ns). */
+#define ZOLO_STALL_SPLIT_GEMM 1
+#define ZOLO_STALL_JACOBI32 2
+int zolo_debug_stall(zolo_handle_t handle, int where, int64_t ns);
 
 /* Short text for a return code. */
 const char* zolo_strerror(int code);

@@ -378,6 +378,27 @@ def zolo_step_chol(X: np.ndarray, co: Coeffs) -> np.ndarray:
     return co.Mhat * (X + S)
 
 
+def group_terms(X: np.ndarray, co: Coeffs, shifts, qr: bool) -> np.ndarray:
+    """Algorithm 3 step 4(c): the process groups j in `shifts` each factor their
+    own shifted problem and form T_j (Eq. 12 in the QR form, Algorithm 1 step
+    (d) in the Cholesky form); returns the sum of those T_j, which step 4(d)
+    (DGSUM2D) adds across all groups before X_{k+1} = M_hat (X + sum_j T_j)."""
+    m, n = X.shape
+    S = np.zeros_like(X)
+    G = None if qr else X.T @ X
+    for j in shifts:
+        c_odd = co.c[2 * j]
+        if qr:
+            W = np.vstack([X, math.sqrt(c_odd) * np.eye(n)])
+            refl, _ = householder_qr(W)
+            Q = thin_q(refl, m + n, n)
+            S += (co.a[j] / math.sqrt(c_odd)) * (Q[:m] @ Q[m:].T)
+        else:
+            R = cholesky_upper(G + c_odd * np.eye(n))
+            S += co.a[j] * solve_right_upper_transpose(solve_right_upper(X, R), R)
+    return S
+
+
 def newton_schulz_step(X: np.ndarray) -> np.ndarray:
     """X <- 1.5 X - 0.5 X (X^T X): one Newton-Schulz polar refinement step."""
     return 1.5 * X - 0.5 * (X @ (X.T @ X))

@@ -22,7 +22,12 @@ ZOLO_SPLIT_BF16 = 1
 ZOLO_R_TUNED = -1
 
 ERRORS = {1: "ZOLO_ENONFINITE", 2: "ZOLO_ECHOL", 3: "ZOLO_ENOTCONV", 4: "ZOLO_ECUDA",
-          5: "ZOLO_ENOMEM", 6: "ZOLO_EEIG", 7: "ZOLO_ETIMEOUT"}
+          5: "ZOLO_ENOMEM", 6: "ZOLO_EEIG", 7: "ZOLO_ETIMEOUT", 8: "ZOLO_EIO", 9: "ZOLO_EINVAL",
+          10: "ZOLO_ECOMM"}
+
+# int (*)(double* buf, int64_t count, void* stream, void* ctx)
+SUM_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                          ctypes.c_void_p)
 
 
 class ZoloOpts(ctypes.Structure):
@@ -83,6 +88,12 @@ def _load():
     lib.zolo_pd_batched.restype = I
     lib.zolo_workspace_bytes.argtypes = [I64, I64, I, I, I, ctypes.POINTER(ctypes.c_uint64)]
     lib.zolo_workspace_bytes.restype = I
+    lib.zolo_shift_range.argtypes = [I, I, I, ctypes.POINTER(I), ctypes.POINTER(I)]
+    lib.zolo_shift_range.restype = I
+    lib.zolo_pd_sharded.argtypes = pd_args + [I, I, SUM_FN, P]
+    lib.zolo_pd_sharded.restype = I
+    lib.zolo_debug_stall.argtypes = [P, I, I64]
+    lib.zolo_debug_stall.restype = I
     lib.zolo_autotune.argtypes = [P, I]
     lib.zolo_autotune.restype = I
     lib.zolo_tuned_r.argtypes = [P, I64, I64, I, D]
@@ -106,7 +117,8 @@ EXPORTED = ["zolo_opts_default", "zolo_create", "zolo_destroy", "zolo_coefficien
             "zolo_strerror", "zolo_kernel_launches", "zolo_profile", "zolo_profile_read",
             "zolo_dgemm", "zolo_dgemm_noalloc", "zolo_pd_batched", "zolo_tuned_r",
             "zolo_tune_save", "zolo_tune_load", "zolo_autotune",
-            "zolo_workspace_bytes"]
+            "zolo_workspace_bytes", "zolo_debug_stall", "zolo_shift_range",
+            "zolo_pd_sharded"]
 
 
 def kernel_launches() -> int:
@@ -197,6 +209,17 @@ def autotune(handle, enable: bool) -> None:
     e = LIB.zolo_autotune(handle.ptr, int(enable))
     if e:
         raise ZoloError(e, "zolo_autotune")
+
+
+ZOLO_STALL_SPLIT_GEMM = 1
+ZOLO_STALL_JACOBI32 = 2
+
+
+def debug_stall(handle, where: int, ns: int = 0) -> None:
+    """Test hook: make a kernel's first wait one that nothing completes (see zolo.h)."""
+    e = LIB.zolo_debug_stall(handle.ptr, where, ns)
+    if e:
+        raise ZoloError(e, "zolo_debug_stall")
 
 
 def tuned_r(handle, m: int, n: int, prec: int, ell0: float) -> int:
@@ -337,6 +360,70 @@ def zolo_pd_batched(handle: Handle, As, os, Qps=None, Hs=None, stream=None, chec
     if e and check:
         raise ZoloError(e, "zolo_pd_batched")
     return Qps, Hs, [Info.from_c(i_a[i]) for i in range(n_mat)], e
+
+
+def shift_range(r: int, rank: int, nranks: int):
+    """The shifts [j0, j1) rank `rank` of `nranks` takes (host only, no device)."""
+    j0, j1 = ctypes.c_int(), ctypes.c_int()
+    e = LIB.zolo_shift_range(r, rank, nranks, ctypes.byref(j0), ctypes.byref(j1))
+    if e:
+        raise ZoloError(e, "zolo_shift_range")
+    return j0.value, j1.value
+
+
+def torch_allreduce(group=None):
+    """A sum over the ranks of a torch.distributed process group, in place:
+    the function zolo_pd_sharded expects (NCCL on GPUs, gloo on CPUs)."""
+    import torch.distributed as dist
+
+    def f(t):
+        dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+    return f
+
+
+class _DeviceArray:
+    """`count` doubles of device memory at `ptr`, exposed to torch without a copy."""
+
+    def __init__(self, ptr: int, count: int):
+        self.__cuda_array_interface__ = {"shape": (count,), "typestr": "<f8",
+                                         "data": (ptr, False), "version": 3, "strides": None}
+
+
+def zolo_pd_sharded(handle: Handle, A, o: ZoloOpts, rank: int, nranks: int, allreduce,
+                    Qp=None, H=None, stream=None, check=True):
+    """Polar decomposition with the r shifts of every iteration shared out over
+    `nranks` ranks (each rank calls this with the same A and options).
+    allreduce(t) must sum the 1-D float64 device tensor t over all ranks in
+    place, ordered on torch's current stream (torch_allreduce(group) does)."""
+    import torch
+    _colmajor(A, "A")
+    m, n = A.shape
+    Qp = empty_colmajor(m, n, A.device) if Qp is None else _colmajor(Qp, "Qp")
+    H = empty_colmajor(n, n, A.device) if H is None else _colmajor(H, "H")
+    info = ZoloInfo()
+    st = _stream(stream)
+
+    def cb(buf, count, stream_ptr, ctx):
+        try:
+            t = torch.as_tensor(_DeviceArray(buf, count), device=A.device)
+            s = (torch.cuda.ExternalStream(stream_ptr, device=A.device) if stream_ptr
+                 else torch.cuda.default_stream(A.device))
+            with torch.cuda.stream(s):
+                allreduce(t)
+            return 0
+        except Exception:   # reported to the library as a failed sum (ZOLO_ECOMM)
+            import traceback
+            traceback.print_exc()
+            return 1
+
+    fn = SUM_FN(cb)
+    e = LIB.zolo_pd_sharded(handle.ptr, ctypes.c_void_p(A.data_ptr()), m, n, _ld(A),
+                            ctypes.c_void_p(Qp.data_ptr()), _ld(Qp), ctypes.c_void_p(H.data_ptr()),
+                            _ld(H), ctypes.byref(o), ctypes.byref(info), st, rank, nranks, fn,
+                            None)
+    if e and check:
+        raise ZoloError(e, "zolo_pd_sharded")
+    return Qp, H, Info.from_c(info)
 
 
 def _host_ptr(a):

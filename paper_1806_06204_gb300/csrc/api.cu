@@ -72,6 +72,10 @@ struct zolo_handle_s {
   std::map<std::array<int64_t, 4>, int> tuned_r;
   // contraction kernel measured fastest per shape (zolo_autotune)
   GemmTuner tuner;
+  // zolo_debug_stall: which kernel waits on a barrier nothing completes (0: none,
+  // ZOLO_STALL_SPLIT_GEMM, ZOLO_STALL_JACOBI32) and for how long
+  int dbg_stall = 0;
+  long long dbg_ns = 0;
 };
 
 namespace {
@@ -110,7 +114,7 @@ size_t layout(void* base, int64_t m, int64_t n, int r, bool svd, PdBufs* b) {
   PdBufs t{};
   t.X = c.take<double>(m * n);
   t.Xn = c.take<double>(m * n);
-  t.S = c.take<double>(m * n);
+  t.S = c.take<double>(m * n + 8);   // + the sharded path's breakdown count
   t.M = c.take<double>(n * n);
   t.partials = c.take<double>(2 * 1024);
   t.norms = c.take<double>(2 * (kMaxIters + 2));
@@ -253,6 +257,8 @@ struct SplitScope {
     w.exp_elems = h->exp_elems;
     w.err = h->err;
     w.slices_s = 9;
+    w.stall = h->dbg_stall == ZOLO_STALL_SPLIT_GEMM;
+    w.stall_ns = h->dbg_ns;
     set_split_engine(&w);
     on = true;
     return 0;
@@ -350,6 +356,109 @@ int iterate(const Run& R, const Coefficients& co, bool qr, const double* X, doub
   return 0;
 }
 
+// The rank's share of one iteration on the sharded path (Algorithm 3 step 4(c):
+// process group j forms T_j): S = sum of T_j over the shifts of `co` (a
+// sub-range of the iteration's shifts, re-indexed from 0), in the form the
+// iteration takes.  The kernels are iterate()'s; the terms are left unsummed
+// with X and M_hat so that the other ranks' shares can be added first.
+// `scratch` (m x n, not X) holds W = sum_j a_j Z_j^{-1} in the inverse form.
+int shift_terms(const Run& R, const Coefficients& co, bool qr, const double* X, double* S,
+                double* scratch) {
+  const int64_t m = R.m, n = R.n;
+  const int r = co.r;
+  const PdBufs& b = R.b;
+  if (qr) {
+    double sq[kMaxR];
+    for (int j = 0; j < r; ++j) sq[j] = std::sqrt(co.c[2 * j]);
+    CK(init_stacked(X, m, b.qr.W, b.qr.strideW, m, n, sq, r, R.st));
+    CK(structured_qr_q(b.qr, m, n, r, b.status, R.st));
+    GemmArgs g;   // sum_j a_j / sqrt(c_{2j-1}) Q1_j Q2_j^T   (Q2_j upper triangular)
+    g.M = (int)m; g.N = (int)n; g.K = (int)n; g.transA = 0; g.transB = 1;
+    g.A = b.qr.W; g.lda = m + n; g.strideA = b.qr.strideW;
+    g.B = b.qr.W + m; g.ldb = m + n; g.strideB = b.qr.strideW;
+    g.Cout = S; g.ldcout = m;
+    g.batch = r; g.reduce = 1; g.b_lower = 1;
+    for (int j = 0; j < r; ++j) g.alpha[j] = co.a[j] / sq[j];
+    CK(gemm_any(g, R.st));
+    return 0;
+  }
+  GemmArgs g;   // G = X^T X (upper triangle)
+  g.M = g.N = (int)n; g.K = (int)m; g.transA = 1; g.transB = 0;
+  g.A = X; g.lda = m; g.B = X; g.ldb = m;
+  g.Cout = b.M; g.ldcout = n; g.c_upper = 1;
+  g.alpha[0] = 1.0;
+  CK(gemm_any(g, R.st));
+  double shifts[kMaxR];
+  for (int j = 0; j < r; ++j) shifts[j] = co.c[2 * j];
+  CK(init_shifted(b.M, b.ch.Z, b.ch.strideZ, n, shifts, r, R.st));
+  CK(cholesky_upper_batched(b.ch, n, r, b.status, R.st));
+  if (R.inv_chol) {
+    CK(init_q_identity(b.M, 0, 0, n, 1, R.st));
+    CK(trsm_right_upper_batched(b.M, n, b.ch, b.Y, b.strideY, b.tmp, b.strideTmp, n, n, r, R.st));
+    GemmArgs w;   // W = sum_j a_j R_j^{-1} R_j^{-T} (upper tiles, then mirrored)
+    w.M = w.N = w.K = (int)n; w.transA = 0; w.transB = 1;
+    w.A = b.Y; w.lda = n; w.strideA = b.strideY;
+    w.B = b.Y; w.ldb = n; w.strideB = b.strideY;
+    w.Cout = scratch; w.ldcout = n;
+    w.batch = r; w.reduce = 1; w.b_lower = 1; w.c_upper = 1;
+    for (int j = 0; j < r; ++j) w.alpha[j] = co.a[j];
+    CK(gemm_any(w, R.st));
+    CK(mirror_upper(scratch, n, n, R.st));
+    GemmArgs t;   // X W
+    t.M = (int)m; t.N = (int)n; t.K = (int)n;
+    t.A = X; t.lda = m; t.B = scratch; t.ldb = n;
+    t.Cout = S; t.ldcout = m;
+    t.alpha[0] = 1.0;
+    CK(gemm_any(t, R.st));
+    return 0;
+  }
+  CK(trsm_pair_batched(X, m, b.ch, b.Y, b.strideY, b.tmp, b.strideTmp, m, n, r, R.st));
+  CK(weighted_sum(b.Y, m, b.strideY, co.a, r, S, m, m, n, R.st));
+  return 0;
+}
+
+// The sharded path's exchange: this rank's shifts, the sum over ranks, then
+// the combination X_{k+1} = M_hat (X + S) (Algorithm 3 steps 4(c)-(d), with the
+// caller's sum in place of DGSUM2D).  S carries one more double, this rank's
+// Cholesky-breakdown flag, so that every rank learns of a breakdown from the
+// same sum; *redo = true when any rank saw one (no combination then).
+struct ShardCtx {
+  int rank = 0, nranks = 1;
+  zolo_sum_fn fn = nullptr;
+  void* ctx = nullptr;
+};
+
+int iterate_sharded(const Run& R, const Coefficients& co, bool qr, const double* X, double* Xn,
+                    double* norms_k, const ShardCtx& sh, bool* redo) {
+  const int64_t m = R.m, n = R.n;
+  const PdBufs& b = R.b;
+  int j0 = 0, j1 = 0;
+  zolo_shift_range(co.r, sh.rank, sh.nranks, &j0, &j1);
+  Coefficients sub = co;
+  sub.r = j1 - j0;
+  for (int j = 0; j < sub.r; ++j) {
+    sub.c[2 * j] = co.c[2 * (j0 + j)];
+    sub.c[2 * j + 1] = co.c[2 * (j0 + j) + 1];
+    sub.a[j] = co.a[j0 + j];
+  }
+  CK(cudaMemsetAsync(b.status + kStatCholFail, 0, sizeof(int), R.st));
+  if (sub.r > 0) {
+    if (int e = shift_terms(R, sub, qr, X, b.S, Xn)) return e;
+  } else {
+    CK(cudaMemsetAsync(b.S, 0, sizeof(double) * m * n, R.st));
+  }
+  CK(flag_to_double(b.status + kStatCholFail, b.S + m * n, R.st));
+  if (sh.fn && sh.fn(b.S, m * n + 1, R.st, sh.ctx) != 0) return ZOLO_ECOMM;
+  double fails = 0.0;
+  CK(cudaMemcpyAsync(&fails, b.S + m * n, sizeof(double), cudaMemcpyDeviceToHost, R.st));
+  CK(cudaStreamSynchronize(R.st));
+  *redo = fails != 0.0;
+  if (*redo) return 0;
+  const double one = 1.0;
+  CK(combine(X, m, Xn, m, m, n, co.mhat, b.S, m, 0, &one, 1, b.partials, norms_k, b.status, R.st));
+  return 0;
+}
+
 int read_status(const Run& R, int* hstat) {
   CK(cudaMemcpyAsync(hstat, R.b.status, sizeof(int) * kStatSlots, cudaMemcpyDeviceToHost, R.st));
   CK(cudaStreamSynchronize(R.st));
@@ -428,7 +537,7 @@ std::array<int64_t, 4> tune_key(int64_t m, int64_t n, int prec, double ell0) {
 
 int pd_core(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda, double* Qp,
             int64_t ldq, double* H, int64_t ldh, const zolo_opts_t& o, zolo_info_t* info,
-            cudaStream_t st, bool svd, PdBufs* out_bufs);
+            cudaStream_t st, bool svd, PdBufs* out_bufs, const ShardCtx* shard = nullptr);
 
 // r = ZOLO_R_TUNED: the cached r for this key, else every r whose schedule
 // converges within max_iter is run on A itself and timed, and the fastest kept.
@@ -497,7 +606,7 @@ int tune_r(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda, 
 
 int pd_core(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda, double* Qp,
             int64_t ldq, double* H, int64_t ldh, const zolo_opts_t& o, zolo_info_t* info,
-            cudaStream_t st, bool svd, PdBufs* out_bufs) {
+            cudaStream_t st, bool svd, PdBufs* out_bufs, const ShardCtx* shard) {
   // alpha: caller's bound or min(||A||_F, sqrt(||A||_1 ||A||_inf))
   double alpha = o.alpha;
   int r_sched = o.r;
@@ -559,8 +668,18 @@ int pd_core(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda,
   for (int k = 0; k < sch.iters; ++k) {
     const Coefficients& co = sch.co[k];
     bool qr = o.force_qr == 1 ? true : (o.force_qr == 0 ? false : sch.use_qr[k]);
-    if (int e = iterate(R, co, qr, X, Xn, b.norms + 2 * it)) return e;
-    if (!qr) {
+    if (shard) {
+      // each rank forms its own shifts' terms; the caller's sum joins them
+      bool redo = false;
+      if (int e = iterate_sharded(R, co, qr, X, Xn, b.norms + 2 * it, *shard, &redo)) return e;
+      if (redo) {   // a Cholesky breakdown on some rank: every rank redoes it in the QR form
+        qr = true;
+        info->chol_fallbacks++;
+        if (int e = iterate_sharded(R, co, qr, X, Xn, b.norms + 2 * it, *shard, &redo)) return e;
+      }
+    } else if (int e = iterate(R, co, qr, X, Xn, b.norms + 2 * it)) {
+      return e;
+    } else if (!qr) {
       // a non-positive Cholesky pivot: redo this iteration in the QR form (X is intact)
       if (int e = read_status(R, hstat)) return e;
       if (hstat[kStatCholFail]) {
@@ -832,6 +951,48 @@ int zolo_pd(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda,
   return e;
 }
 
+int zolo_shift_range(int r, int rank, int nranks, int* j0, int* j1) {
+  if (r < 1 || r > kMaxR) return -1;
+  if (nranks < 1) return -3;
+  if (rank < 0 || rank >= nranks) return -2;
+  if (!j0 || !j1) return -4;
+  const int base = r / nranks, extra = r % nranks;
+  *j0 = rank * base + std::min(rank, extra);
+  *j1 = *j0 + base + (rank < extra ? 1 : 0);
+  return 0;
+}
+
+int zolo_pd_sharded(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda,
+                    double* Qp, int64_t ldq, double* H, int64_t ldh, const zolo_opts_t* opts,
+                    zolo_info_t* info, void* stream, int rank, int nranks, zolo_sum_fn sum,
+                    void* ctx) {
+  if (int e = validate(h, A, m, n, lda, Qp, ldq, H, ldh, opts)) return e;
+  if (opts->r == ZOLO_R_TUNED || opts->posteriori) return -10;
+  if (!info) return -11;
+  if (nranks < 1) return -14;
+  if (rank < 0 || rank >= nranks) return -13;
+  if (!sum && nranks > 1) return -15;
+  std::memset(info, 0, sizeof(*info));
+  if (cudaSetDevice(h->device) != cudaSuccess) return info->status = ZOLO_ECUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  TunerScope ts(&h->tuner);
+  ShardCtx sh;
+  sh.rank = rank;
+  sh.nranks = nranks;
+  sh.fn = sum;
+  sh.ctx = ctx;
+  cudaEventRecord(h->e0, st);
+  int e = pd_core(h, A, m, n, lda, Qp, ldq, H, ldh, *opts, info, st, false, nullptr, &sh);
+  cudaEventRecord(h->e1, st);
+  if (cudaEventSynchronize(h->e1) == cudaSuccess) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->e0, h->e1);
+    info->ms = ms;
+  }
+  info->status = e;
+  return e;
+}
+
 int zolo_svd(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda, double* U,
              int64_t ldu, double* S, double* V, int64_t ldv, const zolo_opts_t* opts,
              zolo_info_t* info, void* stream) {
@@ -860,6 +1021,8 @@ int zolo_svd(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda
   if (e == 0) {
     std::vector<double> lam(n);
     int sweeps = 0;
+    b.eig.stall = h->dbg_stall == ZOLO_STALL_JACOBI32;
+    b.eig.stall_ns = h->dbg_ns;
     const int ee = eig_sym_jacobi(Hm, n, n, V, ldv, lam.data(), b.eig, &sweeps, st);
     info->eig_sweeps = sweeps;
     if (ee == 1) e = ZOLO_ECUDA;
@@ -1003,6 +1166,8 @@ int zolo_dgemm(zolo_handle_t h, int transA, int transB, int64_t m, int64_t n, in
   if (int e = ensure_split(h, per, per, exps)) return e;
   if (cudaMemsetAsync(h->err, 0, sizeof(int), st) != cudaSuccess) return ZOLO_ECUDA;
   SplitWork w{h->slices, h->slice_elems, h->exps, h->exp_elems, h->err, S};
+  w.stall = h->dbg_stall == ZOLO_STALL_SPLIT_GEMM;
+  w.stall_ns = h->dbg_ns;
   if (gemm_split(g, w, st) != cudaSuccess) return ZOLO_ECUDA;
   int herr = 0;
   if (cudaMemcpyAsync(&herr, h->err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -1207,6 +1372,8 @@ int zolo_pd_batched(zolo_handle_t h, int count, const double* const* A, const in
       R.b.status = reinterpret_cast<int*>(rec);
       R.b.norms = rec + 4;
       SplitWork w{sl.slices, sl.slice_elems, sl.exps, sl.exp_elems, sl.err, 9};
+      w.stall = h->dbg_stall == ZOLO_STALL_SPLIT_GEMM;
+      w.stall_ns = h->dbg_ns;
       set_split_engine(opts[i].prec == ZOLO_SPLIT_BF16 ? &w : nullptr);
       const int e = pd_enqueue(R, A[i], lda[i], Qp[i], ldq[i], H[i], ldh[i], sch[i], opts[i], alpha[i]);
       set_split_engine(nullptr);
@@ -1314,6 +1481,15 @@ int zolo_pd_batched(zolo_handle_t h, int count, const double* const* A, const in
   return worst;
 }
 
+int zolo_debug_stall(zolo_handle_t h, int where, int64_t ns) {
+  if (!h) return -1;
+  if (where != 0 && where != ZOLO_STALL_SPLIT_GEMM && where != ZOLO_STALL_JACOBI32) return -2;
+  if (ns < 0 || ns > 1000000000) return -3;
+  h->dbg_stall = where;
+  h->dbg_ns = ns;
+  return 0;
+}
+
 int zolo_tuned_r(zolo_handle_t h, int64_t m, int64_t n, int prec, double ell0) {
   if (!h || !(ell0 > 0.0 && ell0 <= 1.0)) return 0;
   const auto hit = h->tuned_r.find(tune_key(m, n, prec, ell0));
@@ -1406,6 +1582,7 @@ const char* zolo_strerror(int code) {
     case ZOLO_ETIMEOUT: return "a bounded device wait expired (tensor-core pipeline)";
     case ZOLO_EIO: return "tuning-cache file could not be written or read";
     case ZOLO_EINVAL: return "tuning-cache file malformed or written on another GPU";
+    case ZOLO_ECOMM: return "the caller's sum over ranks reported a failure";
     default: return code < 0 ? "illegal argument" : "unknown error";
   }
 }

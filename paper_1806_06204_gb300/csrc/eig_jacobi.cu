@@ -165,7 +165,8 @@ constexpr int kJInner = 1;             // Jacobi sweeps on G per visit
 
 __global__ void __launch_bounds__(kJacThreads)
 jacobi32_block_sweep_kernel(float* X, float* Z, int64_t ld, int64_t m, int nb_even, int n_real,
-                            float tol, int* status, unsigned* bar, int* err) {
+                            float tol, int* status, unsigned* bar, int* err, int stall,
+                            long long stall_ns) {
   static_assert(kJacThreads == 256 && kJW == 32 && kJRows == kJacThreads, "thread mapping below");
   __shared__ float Ct[kJW * kJLd];             // chunk, column-major: Ct[j * kJLd + r]
   __shared__ float G[kJW][kJW + 1];
@@ -173,6 +174,25 @@ jacobi32_block_sweep_kernel(float* X, float* Z, int64_t ld, int64_t m, int nb_ev
   __shared__ __align__(16) float Q4[kJW][kJW]; // Q for the vectorised product
   __shared__ float s_c[kJB], s_s[kJB];
   __shared__ int s_a[kJB], s_b[kJB];
+  if (stall && blockIdx.x == 0) {
+    // test hook of the error exit: wait, bounded, on a flag that nothing sets
+    __shared__ int never;
+    if (threadIdx.x == 0) {
+      never = 0;
+      long long t0;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+      for (;;) {
+        if (*(volatile int*)&never) break;
+        long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (t - t0 > stall_ns) break;
+        __nanosleep(256);
+      }
+      atomicExch(err, 1);
+    }
+    __syncthreads();
+    return;
+  }
   __shared__ int s_rot;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int npairs = nb_even / 2;
@@ -551,7 +571,9 @@ int eig_sym_jacobi(const double* H, int64_t ldh, int64_t n, double* V, int64_t l
       int* status = w.status;
       unsigned* bar = w.bar;
       int* err = w.err;
-      void* args[] = {&X32, &Z32, &ld, &mm, &ne, &nr, &tol, &status, &bar, &err};
+      int stall = sw == 0 ? w.stall : 0;
+      long long stall_ns = w.stall_ns;
+      void* args[] = {&X32, &Z32, &ld, &mm, &ne, &nr, &tol, &status, &bar, &err, &stall, &stall_ns};
       {
         // Gram and two products with Q per block pair: 6 (2 kJB)^2 m flops
         ProfScope ps(kProfJacobi32, st,

@@ -105,6 +105,25 @@ __global__ void combine_kernel(const double* __restrict__ X, int64_t ldx, double
   }
 }
 
+// S = sum_t coef_t T_t (T_t at T + t strideT): the shifted terms of one rank's
+// shifts, before the sum over ranks.
+__global__ void weighted_sum_kernel(const double* __restrict__ T, int64_t ldt, int64_t strideT,
+                                    Vec8 coef, int nt, double* __restrict__ S, int64_t lds,
+                                    int64_t m, int64_t n) {
+  const int64_t total = m * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e % m, j = e / m;
+    double s = 0.0;
+    for (int t = 0; t < nt; ++t) s = fma(coef.v[t], T[i + j * ldt + t * strideT], s);
+    S[i + j * lds] = s;
+  }
+}
+
+__global__ void flag_to_double_kernel(const int* __restrict__ flag, double* __restrict__ out) {
+  *out = *flag ? 1.0 : 0.0;
+}
+
 __global__ void finish_pairs_kernel(const double* __restrict__ partials, int nblocks,
                                     double* __restrict__ out) {
   __shared__ double red[32];
@@ -285,6 +304,20 @@ cudaError_t combine(const double* X, int64_t ldx, double* Xn, int64_t ldxn, int6
   }
   ProfScope ps(kProfOther, st);
   finish_pairs_kernel<<<1, 1024, 0, st>>>(partials, kReduceBlocks, norms);
+  return cudaGetLastError();
+}
+
+cudaError_t weighted_sum(const double* T, int64_t ldt, int64_t strideT, const double* coef, int nt,
+                         double* S, int64_t lds, int64_t m, int64_t n, cudaStream_t st) {
+  ProfScope ps(kProfCombine, st, 2.0 * (double)m * n * nt, 8.0 * (double)m * n * (nt + 1));
+  weighted_sum_kernel<<<grid_for(m * n), kThreads, 0, st>>>(T, ldt, strideT, pack(coef, nt), nt, S,
+                                                             lds, m, n);
+  return cudaGetLastError();
+}
+
+cudaError_t flag_to_double(const int* flag, double* out, cudaStream_t st) {
+  ProfScope ps(kProfOther, st);
+  flag_to_double_kernel<<<1, 1, 0, st>>>(flag, out);
   return cudaGetLastError();
 }
 

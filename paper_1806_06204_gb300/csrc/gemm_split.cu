@@ -272,6 +272,8 @@ struct SplitEpi {
   int M, N, K, Mpad, Npad;
   int batch, reduce, swap;  // swap: the tile computes C^T (rows of the tile are columns of C)
   int* err;
+  int stall;                // test hook: the MMA issuer first waits on a barrier nothing completes
+  long long stall_ns;
 };
 
 template <int BN, int S>
@@ -282,7 +284,7 @@ struct SmemLayout {
   static constexpr int kOffB = 0;
   static constexpr int kOffA = 2 * kBStage;
   static constexpr int kOffBar = kOffA + kARing * kATile;
-  static constexpr int kBars = 2 + 2 + 2 * kARing + 3;
+  static constexpr int kBars = 2 + 2 + 2 * kARing + 3 + 1;   // the last: never completed
   static constexpr int kBytes = kOffBar + kBars * 8 + 16;
   static constexpr int kAlloc = kBytes + 1024;     // slack for 1024-byte alignment
 };
@@ -304,6 +306,7 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
   uint64_t* tfull = aempty + kARing;
   uint64_t* tempty = tfull + 1;
   uint64_t* tdone = tfull + 2;
+  uint64_t* never = tfull + 3;         // initialised, never arrived at (test hook)
   uint32_t* tslot = (uint32_t*)(bar + L::kBars);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -335,6 +338,7 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     tc::mbar_init(tfull, 1);
     tc::mbar_init(tempty, kEpiWarps);
     tc::mbar_init(tdone, 1);
+    tc::mbar_init(never, 1);
     tc::fence_barrier_init();
   }
   if (warp == 1) tc::tmem_alloc<512>(tslot);
@@ -384,6 +388,10 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     const uint64_t bdesc0 = tc::sdesc_k128(tc::smem_u32(sB));
     int kbg = 0, ia = 0;
     bool ok = true;
+    if (p.stall) {
+      tc::mbar_stall(never, err, p.stall_ns);
+      ok = false;
+    }
     for (int c = 0; c < nchunks && ok; ++c) {
       if (c > 0 && !(ok = tc::mbar_wait(tempty, (c - 1) & 1, err))) break;
       tc::tc_fence_after();
@@ -624,6 +632,8 @@ cudaError_t run_split(const GemmArgs& g, SplitWork& w, cudaStream_t st) {
   p.M = g.M; p.N = g.N; p.K = K; p.Mpad = Mpad; p.Npad = Npad;
   p.batch = nb; p.reduce = g.reduce; p.swap = swap ? 1 : 0;
   p.err = w.err;
+  p.stall = w.stall;
+  p.stall_ns = w.stall_ns;
   using L = SmemLayout<BN, S>;
   if ((err = smem_attr_once((const void*)split_gemm_kernel<BN, S>, L::kAlloc)) != cudaSuccess) {
     if (std::getenv("ZOLO_DEBUG"))

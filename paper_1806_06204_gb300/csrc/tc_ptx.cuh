@@ -69,6 +69,17 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* e
   return false;
 }
 
+// A wait that nothing completes, bounded by `ns` (test hook of the error exit):
+// polls an mbarrier no thread or copy arrives at, then sets *err.
+__device__ __forceinline__ void mbar_stall(uint64_t* never, int* err, long long ns) {
+  const uint64_t t0 = global_ns();
+  for (uint32_t i = 0;; ++i) {
+    if (mbar_try_wait(never, 0)) break;
+    if ((i & 255u) == 255u && (long long)(global_ns() - t0) > ns) break;
+  }
+  atomicExch(err, 1);
+}
+
 // Bounded wait that ignores the error flag (half a second at most): used on exit
 // paths to let copies or MMAs already in flight finish before their shared
 // memory / TMEM is released.

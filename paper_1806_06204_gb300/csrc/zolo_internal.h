@@ -170,6 +170,11 @@ struct SplitWork {
   size_t exp_elems;
   int* err;              // device error flag (bounded waits)
   int slices_s;          // S
+  // test hook of the failure path: with stall = 1 the MMA issuer first waits,
+  // for stall_ns, on an mbarrier that nothing arrives at, then takes the
+  // bounded-wait error exit
+  int stall = 0;
+  long long stall_ns = 0;
 };
 cudaError_t gemm_split(const GemmArgs& g, SplitWork& w, cudaStream_t st);
 // slice elements one call of the given shape needs
@@ -208,6 +213,11 @@ cudaError_t init_shifted(const double* G, double* Z, int64_t strideZ, int64_t n,
 cudaError_t combine(const double* X, int64_t ldx, double* Xn, int64_t ldxn, int64_t m, int64_t n,
                     double mhat, const double* T, int64_t ldt, int64_t strideT, const double* coef,
                     int nt, double* partials, double* norms, int* status, cudaStream_t st);
+// S = sum_t coef_t T_t, T_t at T + t * strideT (ld ldt), t < nt <= 8
+cudaError_t weighted_sum(const double* T, int64_t ldt, int64_t strideT, const double* coef, int nt,
+                         double* S, int64_t lds, int64_t m, int64_t n, cudaStream_t st);
+// *out = (*flag != 0) as a double
+cudaError_t flag_to_double(const int* flag, double* out, cudaStream_t st);
 // H = (M + M^T) / 2
 // W(i, j) = W(j, i) for i > j (n x n, ld ldw): a symmetric W from its upper triangle
 cudaError_t mirror_upper(double* W, int64_t ldw, int64_t n, cudaStream_t st);
@@ -281,6 +291,11 @@ struct EigWork {
   double* tmp;      // n x 64 scratch of the triangular solve
   unsigned* bar;    // grid-barrier words (2)
   int* err;         // bounded-wait error flag
+  // test hook of the failure path: with stall = 1, block 0 of the first FP32
+  // sweep waits, for stall_ns, on a flag nothing sets, then takes the
+  // bounded-wait error exit (the other blocks leave the grid barrier on the flag)
+  int stall = 0;
+  long long stall_ns = 0;
 };
 // Y <- X R^{-1} for upper R with inverted diagonal blocks (cholesky_upper_batched output)
 cudaError_t trsm_right_upper_batched(const double* X, int64_t ldx, const CholBuffers& b, double* Y,

@@ -112,3 +112,7 @@ def test_workspace_bytes_query(zb):
     assert call(10, 10, 1, 5, 0, ctypes.byref(out)) == -4
     assert call(10, 10, 1, 0, 2, ctypes.byref(out)) == -5
     assert call(10, 10, 1, 0, 0, None) == -6
+
+
+def test_debug_stall_rejects_bad_arguments_without_a_device(zb):
+    assert zb.LIB.zolo_debug_stall(None, zb.ZOLO_STALL_SPLIT_GEMM, 1000) == -1

@@ -123,3 +123,35 @@ def test_svd_against_brute_force_one_sided_jacobi():
     # singular vectors up to sign (distinct singular values)
     assert np.allclose(np.abs(np.sum(U * Ub, axis=0)), 1.0, atol=1e-9)
     assert np.allclose(np.abs(np.sum(V * Vb, axis=0)), 1.0, atol=1e-9)
+
+
+@pytest.mark.parametrize("qr,kappa", [(True, 1e6), (False, 20.0)])
+def test_group_terms_each_equal_the_closed_form_term(qr, kappa):
+    # Algorithm 3 step 4(c): group j forms T_j = a_j X (X^T X + c_{2j-1} I)^{-1}
+    # (Theorem 2), which on X = U diag(sigma) V^T is U diag(a_j sigma / (sigma^2 + c)) V^T
+    sm = synth.square_geometric(20, kappa, seed=14) if qr else synth.tall_uniform(30, 12, 1 / kappa, 15)
+    r = 5
+    co = zo.zolotarev_coeffs(1.0 / kappa, r)
+    for j in range(r):
+        c = co.c[2 * j]
+        ref = (sm.U * (co.a[j] * sm.sigma / (sm.sigma ** 2 + c))) @ sm.V.T
+        got = zo.group_terms(sm.A, co, [j], qr)
+        tol = 1e-13 if not qr else 1e-13 + 50 * zo.EPS * kappa
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < tol, j
+
+
+@pytest.mark.parametrize("qr", [True, False])
+def test_groups_of_a_partition_sum_to_the_whole_step(qr):
+    # Algorithm 3 step 4(d): the sum over the groups is the one-process step
+    sm = synth.tall_uniform(28, 12, 1e-2 if not qr else 1e-6, seed=16)
+    ell = float(sm.sigma[-1])
+    co = zo.zolotarev_coeffs(ell, 7)
+    whole = zo.zolo_step_qr(sm.A, co) if qr else zo.zolo_step_chol(sm.A, co)
+    for parts in ([range(7)], [range(0, 3), range(3, 7)], [range(0, 2), range(2, 4), range(4, 6),
+                                                          range(6, 7)]):
+        S = sum(zo.group_terms(sm.A, co, p, qr) for p in parts)
+        got = co.Mhat * (sm.A + S)
+        assert np.linalg.norm(got - whole) / np.linalg.norm(whole) < 1e-14
+    # a partition that drops a shift is caught
+    S = zo.group_terms(sm.A, co, range(0, 6), qr)
+    assert np.linalg.norm(co.Mhat * (sm.A + S) - whole) / np.linalg.norm(whole) > 1e-6
