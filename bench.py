@@ -539,6 +539,8 @@ def run_batch(args, w, rank, world, dist, local):
                 "pd_model_flops": arm["flops"], "accuracy": arm["acc"], "roofline": arm["roof"],
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": arm["launches"],
                 "kernel_ms": {k: round(v["ms"], 3) for k, v in arm["kstats"].items() if v["launches"]},
+                "kernel_gflop": {k: round(v["flops"] / 1e9, 1) for k, v in arm["kstats"].items()
+                                 if v["launches"]},
                 "clocks": arm["clocks"]}
         if fp64 is not None:
             fv = world * w["count"] / (fp64["ms_step"] / 1000.0)

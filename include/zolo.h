@@ -205,7 +205,10 @@ int zolo_pd_sharded(zolo_handle_t handle, const double* A, int64_t m, int64_t n,
    the whole batch is recorded as one CUDA graph and the graph is replayed when
    the same batch (pointers, sizes, options) is decomposed again.  A Cholesky
    breakdown found at the end is redone for that matrix on the single-matrix
-   path.  opts[i].posteriori must be 0.  Returns the first non-zero status
+   path.  Each matrix's result equals zolo_pd's to rounding (bit for bit below
+   512 rows: with many problems in flight the batched call factors a taller
+   QR panel on fewer CTAs, which sums its column norms in another order).
+   opts[i].posteriori must be 0.  Returns the first non-zero status
    (info[i].status per matrix); -i codes refer to the arguments as in zolo_pd
    with the offending matrix's info[].status set. */
 int zolo_pd_batched(zolo_handle_t handle, int count, const double* const* A, const int64_t* m,

@@ -276,6 +276,7 @@ struct Run {
   PdBufs b;
   cudaStream_t st;
   bool inv_chol = false;   // Cholesky-form iterations through W = sum_j a_j Z_j^{-1}
+  bool narrow_panels = false;   // many problems in flight: panels on the fewest CTAs
 };
 
 // opts.chol_form = 0: the explicit-inverse Cholesky form when its modelled flops,
@@ -299,7 +300,7 @@ int iterate(const Run& R, const Coefficients& co, bool qr, const double* X, doub
     double sq[kMaxR];
     for (int j = 0; j < r; ++j) sq[j] = std::sqrt(co.c[2 * j]);
     CK(init_stacked(X, m, b.qr.W, b.qr.strideW, m, n, sq, r, R.st));
-    CK(structured_qr_q(b.qr, m, n, r, b.status, R.st));
+    CK(structured_qr_q(b.qr, m, n, r, b.status, R.st, true, R.narrow_panels));
     GemmArgs g;   // S = sum_j a_j / sqrt(c_{2j-1}) Q1_j Q2_j^T   (Q2_j upper triangular)
     g.M = (int)m; g.N = (int)n; g.K = (int)n; g.transA = 0; g.transB = 1;
     g.A = b.qr.W; g.lda = m + n; g.strideA = b.qr.strideW;
@@ -371,7 +372,7 @@ int shift_terms(const Run& R, const Coefficients& co, bool qr, const double* X, 
     double sq[kMaxR];
     for (int j = 0; j < r; ++j) sq[j] = std::sqrt(co.c[2 * j]);
     CK(init_stacked(X, m, b.qr.W, b.qr.strideW, m, n, sq, r, R.st));
-    CK(structured_qr_q(b.qr, m, n, r, b.status, R.st));
+    CK(structured_qr_q(b.qr, m, n, r, b.status, R.st, true, R.narrow_panels));
     GemmArgs g;   // sum_j a_j / sqrt(c_{2j-1}) Q1_j Q2_j^T   (Q2_j upper triangular)
     g.M = (int)m; g.N = (int)n; g.K = (int)n; g.transA = 0; g.transB = 1;
     g.A = b.qr.W; g.lda = m + n; g.strideA = b.qr.strideW;
@@ -767,6 +768,11 @@ int pd_core(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda,
   if (hstat[kStatCholFail]) return ZOLO_ECHOL;
   return status;
 }
+
+// Concurrent lanes (streams) of zolo_pd_batched.  The batch of 512 matrices with
+// n in {64..1024} measured 209 / 213 / 215 matrices/s at 16 / 32 / 64 lanes:
+// past 32 the GPU is full.
+constexpr int kBatchLanes = 32;
 
 // Per-matrix device record of the batched path: status words, then norms.
 constexpr int kRecDoubles = 4 + 2 * (kMaxIters + 2);
@@ -1273,7 +1279,7 @@ int zolo_pd_batched(zolo_handle_t h, int count, const double* const* A, const in
   // ---- lanes: streams with workspace for the largest matrix of the batch.  With
   // per-kernel profiling on, one lane: every launch's event pair then times that
   // kernel alone, not its share of a GPU other lanes' kernels run on too
-  const int nslots = profiling_enabled() ? 1 : std::min(count, 16);
+  const int nslots = profiling_enabled() ? 1 : std::min(count, kBatchLanes);
   int64_t mmax = 0, nmax = 0;
   int rmax = 1;
   bool any_split = false;
@@ -1367,6 +1373,7 @@ int zolo_pd_batched(zolo_handle_t h, int count, const double* const* A, const in
       BatchSlot& sl = h->slots[q % nslots];
       Run R{m[i], n[i], sch[i].r, {}, sl.st};
       R.inv_chol = use_inverse_form(opts[i].chol_form, m[i], n[i], sch[i].r);
+      R.narrow_panels = true;
       layout(sl.ws, m[i], n[i], sch[i].r, false, &R.b);
       double* rec = h->brec + (size_t)i * kRecDoubles;
       R.b.status = reinterpret_cast<int*>(rec);

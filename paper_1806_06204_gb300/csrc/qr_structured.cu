@@ -538,11 +538,13 @@ int64_t qr_partial_elems(int64_t m, int r) {
 }
 
 cudaError_t structured_qr_q(const QrBuffers& b, int64_t m, int64_t n, int r, int* status,
-                            cudaStream_t st, bool explicit_q) {
+                            cudaStream_t st, bool explicit_q, bool narrow_panels) {
   constexpr int NB = kQrNB, NBb = kQrBlock;
   {
     const int bytes = (int)(sizeof(double) * NB * kSmemPanelRows);
-    if (smem_attr_once((const void*)qr_panel_smem_kernel<NB, 1>, bytes) != cudaSuccess ||
+    if (smem_attr_once((const void*)qr_panel_smem_kernel<NB, 2>, bytes) != cudaSuccess ||
+        smem_attr_once((const void*)qr_panel_smem_kernel<NB, 4>, bytes) != cudaSuccess ||
+        smem_attr_once((const void*)qr_panel_smem_kernel<NB, 1>, bytes) != cudaSuccess ||
         smem_attr_once((const void*)qr_panel_smem_kernel<NB, kPanelCluster>, bytes) != cudaSuccess)
       return cudaErrorInvalidConfiguration;
   }
@@ -550,6 +552,22 @@ cudaError_t structured_qr_q(const QrBuffers& b, int64_t m, int64_t n, int r, int
   const int64_t ldv = m + NBb;
   cudaError_t err;
   const int nblocks = (int)((n + NBb - 1) / NBb);
+  // CTAs per shift of the panel kernel.  The panel is a chain of dependent
+  // column steps on a few SMs.  Alone (one matrix, r shifts in flight) it goes
+  // fastest on an 8-CTA cluster, which splits each column's rows eight ways;
+  // when many problems are in flight (narrow_panels) the same SMs serve more
+  // panels at once with the fewest CTAs whose rows fit in shared memory (one
+  // CTA up to m = 736, two up to 1504).  0: the global-memory cluster kernel.
+  int cg = 0;
+  if (narrow_panels) {
+    for (int c = 1; c <= kPanelCluster; c *= 2)
+      if ((m + NB + c - 1) / c <= kSmemPanelRows) { cg = c; break; }
+  } else if (m + NB <= kSmemPanelRows && m < kClusterPanelMinRows) {
+    cg = 1;
+  } else if ((m + NB + kPanelCluster - 1) / kPanelCluster <= kSmemPanelRows) {
+    cg = kPanelCluster;
+  }
+  const int64_t rows_cta = cg ? (m + NB + cg - 1) / cg : 0;
   // every V entry outside the rows a panel writes must be an exact zero
   if ((err = cudaMemsetAsync(b.V, 0, sizeof(double) * r * b.strideV, st)) != cudaSuccess) return err;
   // ---------------- factorisation (structured GEQRF)
@@ -564,13 +582,18 @@ cudaError_t structured_qr_q(const QrBuffers& b, int64_t m, int64_t n, int r, int
       {
         ProfScope ps(kProfPanel, st, 3.0 * r * (double)(m + 1) * nbp * nbp,
                      8.0 * r * (double)(m + NB) * nbp * 2.0);
-        const int64_t rows8 = (m + NB + kPanelCluster - 1) / kPanelCluster;
-        if (m + NB <= kSmemPanelRows && m < kClusterPanelMinRows)
-          qr_panel_smem_kernel<NB, 1><<<r, 256, sizeof(double) * NB * (m + NB), st>>>(
+        const size_t smem = sizeof(double) * NB * rows_cta;
+        if (cg == 1)
+          qr_panel_smem_kernel<NB, 1><<<r, 256, smem, st>>>(
               b.W, b.strideW, ldw, m, c0, nbp, Vpan, b.strideV, ldv, b.T, b.strideT, status);
-        else if (rows8 <= kSmemPanelRows)
-          qr_panel_smem_kernel<NB, kPanelCluster><<<r * kPanelCluster, 256,
-                                                    sizeof(double) * NB * rows8, st>>>(
+        else if (cg == 2)
+          qr_panel_smem_kernel<NB, 2><<<r * 2, 256, smem, st>>>(
+              b.W, b.strideW, ldw, m, c0, nbp, Vpan, b.strideV, ldv, b.T, b.strideT, status);
+        else if (cg == 4)
+          qr_panel_smem_kernel<NB, 4><<<r * 4, 256, smem, st>>>(
+              b.W, b.strideW, ldw, m, c0, nbp, Vpan, b.strideV, ldv, b.T, b.strideT, status);
+        else if (cg == kPanelCluster)
+          qr_panel_smem_kernel<NB, kPanelCluster><<<r * kPanelCluster, 256, smem, st>>>(
               b.W, b.strideW, ldw, m, c0, nbp, Vpan, b.strideV, ldv, b.T, b.strideT, status);
         else
           // tall panels (m > 8 x 768 rows): 512 threads per CTA halve each thread's

@@ -256,8 +256,10 @@ struct QrBuffers {
 int64_t qr_partial_elems(int64_t m, int r);
 // Factor [X; sqrt(c_j) I] for j < r and overwrite W_j with the thin Q_j
 // (explicit_q = false: leave R on and above the diagonal of W_j's top block).
+// narrow_panels: many problems are in flight on other streams; the panel kernel
+// then takes the fewest CTAs per shift whose rows fit in shared memory.
 cudaError_t structured_qr_q(const QrBuffers& b, int64_t m, int64_t n, int r, int* status,
-                            cudaStream_t st, bool explicit_q = true);
+                            cudaStream_t st, bool explicit_q = true, bool narrow_panels = false);
 // Inverses of the NB x NB diagonal blocks of an upper-triangular R (ld n) in the
 // layout cholesky_upper_batched leaves in Rinv; a zero pivot sets status.
 cudaError_t tri_inv_diag_blocks(const double* R, int64_t n, double* Rinv, int* status,

@@ -99,8 +99,10 @@ def test_sharded_equals_single_rank(zb, n, kappa, r, nranks, split):
         assert np.allclose(info.delta, i1.delta, rtol=1e-10, atol=1e-15)
     Qp, H, _ = res[0]
     assert zo.orthogonality(Qp) < 1e-13 and zo.backward_error_pd(sm.A, Qp, H) < 1e-13
-    assert np.linalg.norm(Qp - Q1) / np.linalg.norm(Q1) < 1e-13
+    # H is well conditioned; Q_p's smallest singular directions move by ~eps kappa
+    # under a different rounding order of the shifts' sum
     assert np.linalg.norm(H - H1) / np.linalg.norm(H1) < 1e-13
+    assert np.linalg.norm(Qp - Q1) / np.linalg.norm(Q1) < 1e-13 + 1e-15 * kappa
 
 
 def test_breakdown_on_one_rank_makes_every_rank_redo_in_qr_form(zb):
