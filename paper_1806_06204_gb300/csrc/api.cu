@@ -1379,6 +1379,7 @@ int zolo_pd_batched(zolo_handle_t h, int count, const double* const* A, const in
       R.b.status = reinterpret_cast<int*>(rec);
       R.b.norms = rec + 4;
       SplitWork w{sl.slices, sl.slice_elems, sl.exps, sl.exp_elems, sl.err, 9};
+      w.throughput = true;   // many lanes in flight: latency is hidden
       w.stall = h->dbg_stall == ZOLO_STALL_SPLIT_GEMM;
       w.stall_ns = h->dbg_ns;
       set_split_engine(opts[i].prec == ZOLO_SPLIT_BF16 ? &w : nullptr);

@@ -708,6 +708,21 @@ SplitWork* get_split_engine() { return t_split; }
 bool split_preferred(const GemmArgs& g, const SplitWork& w) { return split_time_ratio(g, w) < 1.0; }
 
 double split_time_ratio(const GemmArgs& g, const SplitWork& w) {
+  if (w.throughput) {
+    // GPU-seconds of each path when other calls fill the rest of the chip: the
+    // FP64 pipe at its measured 1.2 TFLOP/s, the slice-pair products at 1.7 PFLOP/s
+    // of BF16 issue, the slicing and output traffic at 6 TB/s
+    const bool swap = g.M < kTileM && g.N > g.M;
+    const double ra = (double)round_up(swap ? g.N : g.M, kTileM);
+    const double rb = (double)round_up(swap ? g.M : g.N, 64);
+    const double kp = (double)round_up(g.K, kBK);
+    const double S = w.slices_s;
+    const double bytes = g.batch * (8.0 + 2.0 * S) * (ra + rb) * kp +
+                         (g.reduce ? 1 : g.batch) * 8.0 * g.M * (double)g.N * (g.beta != 0.0 ? 2 : 1);
+    const double pairs = S * (S + 1) / 2 + (S - 1);
+    const double tensor = pairs * 2.0 * ra * rb * kp * g.batch / 1.7e15;
+    return (bytes / 6e12 + tensor) / (gemm_flops(g) / 1.2e12);
+  }
   const double t64 = gemm_flops(g) / 0.9e12;
   const bool swap = g.M < kTileM && g.N > g.M;
   const double ra = (double)round_up(swap ? g.N : g.M, kTileM);

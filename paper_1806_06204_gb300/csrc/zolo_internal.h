@@ -175,6 +175,11 @@ struct SplitWork {
   // bounded-wait error exit
   int stall = 0;
   long long stall_ns = 0;
+  // the router's cost model: false = one call alone on the GPU (its launch and
+  // pipeline latency counts); true = many calls in flight at once (zolo_pd_batched's
+  // lanes), where latency is hidden and each path costs the share of the GPU's
+  // FP64 pipe, tensor pipe and memory bandwidth it takes
+  bool throughput = false;
 };
 cudaError_t gemm_split(const GemmArgs& g, SplitWork& w, cudaStream_t st);
 // slice elements one call of the given shape needs
