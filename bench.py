@@ -594,6 +594,10 @@ def main():
     ap.add_argument("--tune-cache", default=None,
                     help="tuning-cache file: loaded before the warm-up steps when it exists, "
                          "written after them")
+    ap.add_argument("--shard-shifts", action="store_true",
+                    help="Zolo-PD workloads under torchrun: the ranks decompose one matrix "
+                         "together, each taking a block of every iteration's r shifts, with one "
+                         "NCCL sum of S per iteration (zolo_pd_sharded; strong scaling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -629,7 +633,11 @@ def main():
         if dist:
             dist.destroy_process_group()
         return
-    sm = make_input(w, seed=2000 + rank)
+    shard = args.shard_shifts and world > 1 and w["kind"] == "pd"
+    if args.shard_shifts and not shard:
+        raise SystemExit("--shard-shifts needs torchrun with N > 1 and a Zolo-PD workload")
+    # sharded: every rank holds the same matrix; replicas: each rank its own
+    sm = make_input(w, seed=2000 + (0 if shard else rank))
     A = torch.from_numpy(sm.A).cuda()
     h = zb.Handle(local)
     if args.tune_cache and os.path.exists(args.tune_cache):
@@ -653,7 +661,10 @@ def main():
         if w["kind"] == "svd":
             U, S, V, info = zb.zolo_svd(h, A, o)
             return (U, S, V), info
-        Qp, H, info = zb.zolo_pd(h, A, o)
+        if shard:
+            Qp, H, info = zb.zolo_pd_sharded(h, A, o, rank, world, zb.torch_allreduce())
+        else:
+            Qp, H, info = zb.zolo_pd(h, A, o)
         return (Qp, H), info
 
     for _ in range(args.warmup):
@@ -684,7 +695,8 @@ def main():
     launches = zb.kernel_launches() - launches0
     ms_step = e0.elapsed_time(e1) / args.steps
     ms_step = max_over_ranks(ms_step, dist)
-    value = world / (ms_step / 1000.0)                # matrices/s over all ranks
+    # matrices/s over all ranks (sharded: the ranks decompose one matrix together)
+    value = (1 if shard else world) / (ms_step / 1000.0)
     flops = pd_model_flops(m, n, info.r, info.used_qr)
     acc = accuracy(w, sm, outs)
 
@@ -713,6 +725,21 @@ def main():
             Sh = torch.empty(n, dtype=torch.float64).pin_memory().numpy()
             host_step = lambda: zb.zolo_svd_host(h, Ah, o, Uh, Sh, Vh)
             d2h = 8 * (m * n + n * n + n)
+        elif shard:
+            # pinned host copies in and out around the sharded call
+            Ap = torch.from_numpy(sm.A.T.copy()).pin_memory().t()
+            Qt = torch.empty((n, m), dtype=torch.float64).pin_memory().t()
+            Ht = torch.empty((n, n), dtype=torch.float64).pin_memory().t()
+            Ad = zb.empty_colmajor(m, n)
+            sum_fn = zb.torch_allreduce()
+
+            def host_step():
+                Ad.copy_(Ap, non_blocking=True)
+                Qd, Hd, _ = zb.zolo_pd_sharded(h, Ad, o, rank, world, sum_fn)
+                Qt.copy_(Qd, non_blocking=True)
+                Ht.copy_(Hd, non_blocking=True)
+                torch.cuda.synchronize()
+            d2h = 8 * (m * n + n * n)
         else:
             Qh = torch.empty((n, m), dtype=torch.float64).pin_memory().numpy().T
             Hh = torch.empty((n, n), dtype=torch.float64).pin_memory().numpy().T
@@ -728,8 +755,8 @@ def main():
         barrier()
         e2e_s = (time.perf_counter() - t0) / args.steps
         e2e_s = max_over_ranks(e2e_s, dist)
-        e2e = {"value": world / e2e_s, "unit": "matrices/s", "h2d_bytes_per_step": 8 * m * n,
-               "d2h_bytes_per_step": d2h}
+        e2e = {"value": (1 if shard else world) / e2e_s, "unit": "matrices/s",
+               "h2d_bytes_per_step": 8 * m * n, "d2h_bytes_per_step": d2h}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -740,7 +767,8 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "matrices/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "higher_is_better": True, "scaling": "strong" if shard else "weak",
+                "vs_baseline": None,
                 "dtype": "f64" if not split else "bf16x9-slices->f64",
                 "data": "synthetic",
                 "config": {"workload": args.workload, "desc": w["desc"], "m": m, "n": n,
@@ -749,7 +777,9 @@ def main():
                            "prec": "split" if split else "fp64",
                            "beta_over_sigma_min": beta_scale,
                            "l2": "inputs larger than L2 (no flush)",
-                           "parallelism": "replicas" if world > 1 else "single"},
+                           "parallelism": (f"shifts sharded over {world} ranks, one NCCL sum of S "
+                                           "per iteration" if shard else
+                                           "replicas" if world > 1 else "single")},
                 "eff_tflops": world * flops / (ms_step / 1000.0) / 1e12,
                 "pd_model_flops": flops, "iters": info.iters, "used_qr": info.used_qr,
                 "eig_sweeps": info.eig_sweeps, "accuracy": acc,
