@@ -116,3 +116,48 @@ def test_workspace_bytes_query(zb):
 
 def test_debug_stall_rejects_bad_arguments_without_a_device(zb):
     assert zb.LIB.zolo_debug_stall(None, zb.ZOLO_STALL_SPLIT_GEMM, 1000) == -1
+
+
+def test_library_coefficients_against_mpmath_directly(zb):
+    """The library's coefficient module pinned to mpmath's elliptic functions at
+    50 digits on its own, not only through the oracle: c_i (Eq. 7), a_j as the
+    partial-fraction residues of Eq. (8) (Theorem 1), M_hat (Eq. 8) and the gap
+    1 - Zhat(l; l)."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    worst = {"c": 0.0, "a": 0.0, "M": 0.0, "gap": 0.0}
+    for ell in [1e-16, 1e-12, 1e-8, 1e-4, 1e-2, 0.1, 0.5, 0.9, 0.999]:
+        for r in (1, 2, 4, 6, 8):
+            c, a, mh, gap = zb.coefficients(ell, r)
+            L = mp.mpf(ell)
+            m = 1 - L * L
+            Kp = mp.ellipk(m)
+            cr = [L * L * (mp.ellipfun("sn", i * Kp / (2 * r + 1), m=m) /
+                           mp.ellipfun("cn", i * Kp / (2 * r + 1), m=m)) ** 2
+                  for i in range(1, 2 * r + 1)]
+            M = mp.mpf(1)
+            for j in range(r):
+                M *= (1 + cr[2 * j]) / (1 + cr[2 * j + 1])
+            # residue of M x prod (x^2 + c_2k) / prod (x^2 + c_2k-1) at x^2 = -c_2j-1,
+            # divided by M: a_j (Eq. 9)
+            ar = []
+            for j in range(r):
+                num = mp.mpf(1)
+                den = mp.mpf(1)
+                for k in range(r):
+                    num *= cr[2 * k + 1] - cr[2 * j]
+                    if k != j:
+                        den *= cr[2 * k] - cr[2 * j]
+                ar.append(num / den)
+            z = M * L
+            for j in range(r):
+                z *= (L * L + cr[2 * j + 1]) / (L * L + cr[2 * j])
+            worst["c"] = max(worst["c"], max(float(abs((ci - x) / x)) for ci, x in zip(c, cr)))
+            worst["a"] = max(worst["a"], max(float(abs((ai - x) / x)) for ai, x in zip(a, ar)))
+            worst["M"] = max(worst["M"], float(abs((mh - M) / M)))
+            g = 1 - z
+            if g > mp.mpf(10) ** -30:
+                worst["gap"] = max(worst["gap"], float(abs((gap - g) / g)))
+    # measured: c 5.8e-15, a 9.6e-15, M 1.6e-15, gap 3.9e-15
+    assert worst["c"] < 2e-14 and worst["M"] < 1e-14, worst
+    assert worst["a"] < 5e-14 and worst["gap"] < 2e-14, worst
