@@ -43,7 +43,8 @@ enum {
   ZOLO_ETIMEOUT = 7,   /* a bounded wait inside a tensor-core kernel expired    */
   ZOLO_EIO = 8,        /* a tuning-cache file could not be written or read      */
   ZOLO_EINVAL = 9,     /* a tuning-cache file is malformed or from another GPU  */
-  ZOLO_ECOMM = 10      /* the caller's sum over ranks (zolo_pd_sharded) failed  */
+  ZOLO_ECOMM = 10,     /* the caller's sum over ranks (zolo_pd_sharded) failed  */
+  ZOLO_EPENDING = 11   /* zolo_pd_async: the stream has not reached the end yet */
 };
 
 /* Arithmetic of the contractions.  ZOLO_FP64: plain FP64 on the FP64 FMA pipe.
@@ -89,7 +90,22 @@ typedef struct {
                       kappa(Z_j) <= 100 on this path.  0 = whichever has fewer
                       modelled flops: the inverse when
                       r (3/2) n^3 + 2 m n^2 < 0.85 * 2 r m n^2 (tall X, large r) */
+  int estimate;    /* 1: after H, compute info.bwd_est = ||A - Qp H||_F / ||A||_F
+                      and info.orth_est = ||Qp^T Qp - I||_F / sqrt(n) on the
+                      device (about 3 m n^2 more flops, in opts.prec's
+                      arithmetic); 0 (default): both left 0                   */
 } zolo_opts_t;
+
+/* Phases of a call timed into zolo_info_t.ms_phase (CUDA events on the call's
+   stream; NVTX ranges of the same names are pushed on the calling thread):
+   the bounds alpha, beta and a tuned r; the QR-form iterations (Eq. 12); the
+   Cholesky-form iterations (Algorithm 1 (d)); the Newton-Schulz steps; H
+   (Algorithm 1 step 5); the error estimates; and for zolo_svd the
+   eigendecomposition of H and U = Qp V (Algorithm 2). */
+enum {
+  ZOLO_PHASE_BOUNDS = 0, ZOLO_PHASE_QR = 1, ZOLO_PHASE_CHOL = 2, ZOLO_PHASE_NS = 3,
+  ZOLO_PHASE_H = 4, ZOLO_PHASE_EST = 5, ZOLO_PHASE_EIG = 6, ZOLO_PHASE_U = 7, ZOLO_PHASES = 8
+};
 
 typedef struct {
   int status;                  /* the return code of the call                */
@@ -105,13 +121,18 @@ typedef struct {
   int chol_form;               /* the Cholesky form the call would take (1 =
                                   triangular solves, 2 = explicit inverse; see
                                   zolo_opts_t.chol_form)                     */
+  double bwd_est;              /* ||A - Qp H||_F / ||A||_F   (opts.estimate)  */
+  double orth_est;             /* ||Qp^T Qp - I||_F / sqrt(n) (opts.estimate) */
+  float ms_phase[ZOLO_PHASES]; /* device time per phase (zolo_pd, zolo_svd,
+                                  zolo_pd_sharded; 0 in zolo_pd_batched and
+                                  zolo_pd_async)                              */
 } zolo_info_t;
 
 typedef struct zolo_handle_s* zolo_handle_t;
 
 /* Defaults: r = 0, alpha = 1, beta = 0 (estimated), max_iter = 6,
    posteriori = 0, ns_steps = 0, prec = ZOLO_FP64, force_qr = -1,
-   chol_form = 0. */
+   chol_form = 0, estimate = 0. */
 void zolo_opts_default(zolo_opts_t* opts);
 
 /* A handle binds a device and owns the library's workspace cache.
@@ -150,6 +171,23 @@ int zolo_workspace_bytes(int64_t m, int64_t n, int r, int prec, int svd, uint64_
 int zolo_pd(zolo_handle_t handle, const double* A, int64_t m, int64_t n, int64_t lda,
             double* Qp, int64_t ldq, double* H, int64_t ldh,
             const zolo_opts_t* opts, zolo_info_t* info, void* stream);
+
+/* zolo_pd without any host synchronisation: the whole decomposition is queued
+   on `stream` and the call returns at once with info->status = ZOLO_EPENDING;
+   when the stream reaches the end of the queued work a host function
+   (cudaLaunchHostFunc) fills *info (status, iterations, l's, deltas, the
+   estimates), so *info must stay valid until then (synchronise the stream or
+   an event recorded after the call before reading it; pinned or pageable host
+   memory).  Needs opts.alpha > 0 and opts.beta > 0 (bounds computed on the
+   device need a round trip), opts.r != ZOLO_R_TUNED and opts.posteriori = 0
+   (-10 otherwise).  No Cholesky fallback can be taken without a round trip: a
+   breakdown is reported as ZOLO_ECHOL in info->status (force_qr = 1 avoids
+   it).  Workspace growth may allocate (cudaMalloc) on the first call of a
+   shape.  Consecutive calls on one handle must use one stream (they share the
+   handle's workspace); up to 64 calls may be in flight. */
+int zolo_pd_async(zolo_handle_t handle, const double* A, int64_t m, int64_t n, int64_t lda,
+                  double* Qp, int64_t ldq, double* H, int64_t ldh,
+                  const zolo_opts_t* opts, zolo_info_t* info, void* stream);
 
 /* SVD A = U diag(S) V^T (Algorithm 2): Zolo-PD, the eigendecomposition of H
    (one-sided block Jacobi on its Cholesky factor), U = Qp V.

@@ -23,7 +23,10 @@ ZOLO_R_TUNED = -1
 
 ERRORS = {1: "ZOLO_ENONFINITE", 2: "ZOLO_ECHOL", 3: "ZOLO_ENOTCONV", 4: "ZOLO_ECUDA",
           5: "ZOLO_ENOMEM", 6: "ZOLO_EEIG", 7: "ZOLO_ETIMEOUT", 8: "ZOLO_EIO", 9: "ZOLO_EINVAL",
-          10: "ZOLO_ECOMM"}
+          10: "ZOLO_ECOMM", 11: "ZOLO_EPENDING"}
+ZOLO_EPENDING = 11
+ZOLO_PHASES = 8
+PHASE_NAMES = ["bounds", "qr", "chol", "newton_schulz", "H", "estimates", "eig", "U"]
 
 # int (*)(double* buf, int64_t count, void* stream, void* ctx)
 SUM_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
@@ -34,7 +37,7 @@ class ZoloOpts(ctypes.Structure):
     _fields_ = [("r", ctypes.c_int), ("alpha", ctypes.c_double), ("beta", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("posteriori", ctypes.c_int),
                 ("ns_steps", ctypes.c_int), ("prec", ctypes.c_int), ("force_qr", ctypes.c_int),
-                ("chol_form", ctypes.c_int)]
+                ("chol_form", ctypes.c_int), ("estimate", ctypes.c_int)]
 
 
 class ZoloInfo(ctypes.Structure):
@@ -43,7 +46,9 @@ class ZoloInfo(ctypes.Structure):
                 ("ell", ctypes.c_double * (ZOLO_MAX_ITERS + 1)),
                 ("delta", ctypes.c_double * ZOLO_MAX_ITERS),
                 ("chol_fallbacks", ctypes.c_int), ("eig_sweeps", ctypes.c_int),
-                ("ms", ctypes.c_double), ("chol_form", ctypes.c_int)]
+                ("ms", ctypes.c_double), ("chol_form", ctypes.c_int),
+                ("bwd_est", ctypes.c_double), ("orth_est", ctypes.c_double),
+                ("ms_phase", ctypes.c_float * ZOLO_PHASES)]
 
 
 class KStat(ctypes.Structure):
@@ -72,7 +77,7 @@ def _load():
                ctypes.POINTER(ZoloInfo), P]
     svd_args = [P, P, I64, I64, I64, P, I64, P, P, I64, ctypes.POINTER(ZoloOpts),
                 ctypes.POINTER(ZoloInfo), P]
-    for name, args in (("zolo_pd", pd_args), ("zolo_pd_host", pd_args),
+    for name, args in (("zolo_pd", pd_args), ("zolo_pd_host", pd_args), ("zolo_pd_async", pd_args),
                        ("zolo_svd", svd_args), ("zolo_svd_host", svd_args)):
         f = getattr(lib, name)
         f.argtypes = args
@@ -118,7 +123,7 @@ EXPORTED = ["zolo_opts_default", "zolo_create", "zolo_destroy", "zolo_coefficien
             "zolo_dgemm", "zolo_dgemm_noalloc", "zolo_pd_batched", "zolo_tuned_r",
             "zolo_tune_save", "zolo_tune_load", "zolo_autotune",
             "zolo_workspace_bytes", "zolo_debug_stall", "zolo_shift_range",
-            "zolo_pd_sharded"]
+            "zolo_pd_sharded", "zolo_pd_async"]
 
 
 def kernel_launches() -> int:
@@ -156,22 +161,28 @@ class Info:
     eig_sweeps: int
     ms: float
     chol_form: int
+    bwd_est: float = 0.0
+    orth_est: float = 0.0
+    ms_phase: dict = field(default_factory=dict)
 
     @staticmethod
     def from_c(ci: ZoloInfo) -> "Info":
         k = ci.iters
         return Info(ci.status, k, ci.r, [bool(x) for x in ci.used_qr[:k]], list(ci.ell[:k + 1]),
-                    list(ci.delta[:k]), ci.chol_fallbacks, ci.eig_sweeps, ci.ms, ci.chol_form)
+                    list(ci.delta[:k]), ci.chol_fallbacks, ci.eig_sweeps, ci.ms, ci.chol_form,
+                    ci.bwd_est, ci.orth_est,
+                    {nm: float(ci.ms_phase[i]) for i, nm in enumerate(PHASE_NAMES)})
 
 
 def opts(beta: float, alpha: float = 1.0, r: int = 0, max_iter: int = 6, posteriori: bool = False,
          ns_steps: int = 0, prec: int = ZOLO_FP64, force_qr: int = -1,
-         chol_form: int = 0) -> ZoloOpts:
+         chol_form: int = 0, estimate: bool = False) -> ZoloOpts:
     o = ZoloOpts()
     LIB.zolo_opts_default(ctypes.byref(o))
     o.r, o.alpha, o.beta, o.max_iter = r, alpha, beta, max_iter
     o.posteriori, o.ns_steps, o.prec, o.force_qr = int(posteriori), ns_steps, prec, force_qr
     o.chol_form = chol_form
+    o.estimate = int(estimate)
     return o
 
 
@@ -303,6 +314,25 @@ def zolo_pd(handle: Handle, A, o: ZoloOpts, Qp=None, H=None, stream=None, check=
     if e and check:
         raise ZoloError(e, "zolo_pd")
     return Qp, H, Info.from_c(info)
+
+
+def zolo_pd_async(handle: Handle, A, o: ZoloOpts, Qp=None, H=None, stream=None):
+    """Queue a polar decomposition without host synchronisation.
+
+    Returns (Qp, H, pending): Qp and H are written when the stream gets there,
+    and pending() -> Info reads the status the library's host function leaves
+    once the stream has been synchronised (ZOLO_EPENDING before that)."""
+    _colmajor(A, "A")
+    m, n = A.shape
+    Qp = empty_colmajor(m, n, A.device) if Qp is None else _colmajor(Qp, "Qp")
+    H = empty_colmajor(n, n, A.device) if H is None else _colmajor(H, "H")
+    info = ZoloInfo()   # filled by the library's host function; kept alive by the closure
+    e = LIB.zolo_pd_async(handle.ptr, ctypes.c_void_p(A.data_ptr()), m, n, _ld(A),
+                          ctypes.c_void_p(Qp.data_ptr()), _ld(Qp), ctypes.c_void_p(H.data_ptr()),
+                          _ld(H), ctypes.byref(o), ctypes.byref(info), _stream(stream))
+    if e:
+        raise ZoloError(e, "zolo_pd_async")
+    return Qp, H, lambda: Info.from_c(info)
 
 
 def zolo_svd(handle: Handle, A, o: ZoloOpts, stream=None, check=True):

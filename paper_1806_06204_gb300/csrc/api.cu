@@ -23,10 +23,33 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/zolo.h"
 #include "zolo_internal.h"
 
 using namespace zolo;
+
+// Per-matrix device norms: ||X_{k+1} - X_k||^2, ||X_{k+1}||^2 per iteration,
+// then the estimates ||A - Qp H||^2, ||A||^2, ||Qp^T Qp - I||^2 (opts.estimate).
+constexpr int kEstSlot = 2 * (kMaxIters + 2);
+constexpr int kNormSlots = kEstSlot + 4;
+constexpr int kPhaseEvents = 32;
+constexpr int kAsyncSlots = 64;
+
+// Host record of one zolo_pd_async call (pinned): the device status words and
+// norms are copied here at the end of the call's work, and a host function
+// turns them into the caller's zolo_info_t.
+struct AsyncSlot {
+  int stat[kStatSlots];
+  int err;
+  double norms[kNormSlots];
+  zolo_info_t base;        // the schedule's part, known at enqueue time
+  zolo_info_t* out;
+  int64_t n;
+  int estimate;
+  volatile int busy;       // set at enqueue, cleared by the host function
+};
 
 // One concurrent lane of zolo_pd_batched: a stream with its own workspace.
 struct BatchSlot {
@@ -76,6 +99,9 @@ struct zolo_handle_s {
   // ZOLO_STALL_SPLIT_GEMM, ZOLO_STALL_JACOBI32) and for how long
   int dbg_stall = 0;
   long long dbg_ns = 0;
+  cudaEvent_t ph_ev[kPhaseEvents] = {};   // phase boundaries of one call
+  AsyncSlot* async = nullptr;              // pinned ring of zolo_pd_async records
+  int async_next = 0;
 };
 
 namespace {
@@ -117,7 +143,7 @@ size_t layout(void* base, int64_t m, int64_t n, int r, bool svd, PdBufs* b) {
   t.S = c.take<double>(m * n + 8);   // + the sharded path's breakdown count
   t.M = c.take<double>(n * n);
   t.partials = c.take<double>(2 * 1024);
-  t.norms = c.take<double>(2 * (kMaxIters + 2));
+  t.norms = c.take<double>(kNormSlots);
   t.status = c.take<int>(kStatSlots);
   if (svd) {
     t.Qp_int = c.take<double>(m * n);
@@ -466,6 +492,86 @@ int read_status(const Run& R, int* hstat) {
   return 0;
 }
 
+// opts.estimate: ||A - Qp H||_F^2 and ||A||_F^2, then ||Qp^T Qp - I||_F^2 into
+// b.norms[kEstSlot ..] (S and M are free once H is formed).
+int enqueue_estimates(const PdBufs& b, const double* A, int64_t lda, const double* Qp, int64_t ldq,
+                      const double* H, int64_t ldh, int64_t m, int64_t n, cudaStream_t st) {
+  GemmArgs g;   // A - Qp H
+  g.M = (int)m; g.N = (int)n; g.K = (int)n;
+  g.A = Qp; g.lda = ldq; g.B = H; g.ldb = ldh;
+  g.Cin = A; g.ldcin = lda; g.beta = 1.0; g.Cout = b.S; g.ldcout = m;
+  g.alpha[0] = -1.0;
+  CK(gemm_any(g, st));
+  CK(frob_norm2(b.S, m, m, n, b.partials, b.norms + kEstSlot, st));
+  CK(frob_norm2(A, lda, m, n, b.partials, b.norms + kEstSlot + 1, st));
+  GemmArgs q;   // Qp^T Qp, upper tiles
+  q.M = q.N = (int)n; q.K = (int)m; q.transA = 1;
+  q.A = Qp; q.lda = ldq; q.B = Qp; q.ldb = ldq;
+  q.Cout = b.M; q.ldcout = n; q.c_upper = 1;
+  q.alpha[0] = 1.0;
+  CK(gemm_any(q, st));
+  CK(gram_identity_dev2(b.M, n, n, b.partials, b.norms + kEstSlot + 2, st));
+  return 0;
+}
+
+void fill_estimates(zolo_info_t* info, const double* norms, int64_t n) {
+  const double* e = norms + kEstSlot;
+  info->bwd_est = e[1] > 0.0 ? std::sqrt(e[0] / e[1]) : 0.0;
+  info->orth_est = std::sqrt(std::max(e[2], 0.0) / (double)n);
+}
+
+const char* const kPhaseNames[ZOLO_PHASES] = {
+    "zolo: bounds", "zolo: QR-form iteration", "zolo: Cholesky-form iteration",
+    "zolo: Newton-Schulz", "zolo: H", "zolo: estimates", "zolo: eig(H)", "zolo: U = Qp V"};
+
+// Device time per phase of one call: an event on the call's stream at every
+// phase boundary (and an NVTX range per phase on the calling thread), read once
+// the stream has been synchronised.
+struct PhaseClock {
+  zolo_handle_t h = nullptr;
+  cudaStream_t st = nullptr;
+  int n = 0;
+  int phase[kPhaseEvents] = {};
+  bool nvtx_open = false;
+  void start(zolo_handle_t hh, cudaStream_t s) {
+    h = hh;
+    st = s;
+    n = 0;
+    for (int i = 0; i < kPhaseEvents; ++i)
+      if (!h->ph_ev[i] && cudaEventCreate(&h->ph_ev[i]) != cudaSuccess) {
+        h->ph_ev[i] = nullptr;
+        h = nullptr;   // no clock for this call
+        cudaGetLastError();
+        return;
+      }
+  }
+  void record(int p) {
+    if (h && n < kPhaseEvents && cudaEventRecord(h->ph_ev[n], st) == cudaSuccess) phase[n++] = p;
+  }
+  void mark(int p) {
+    if (nvtx_open) nvtxRangePop();
+    nvtxRangePushA(kPhaseNames[p]);
+    nvtx_open = true;
+    record(p);
+  }
+  void stop() {
+    if (nvtx_open) nvtxRangePop();
+    nvtx_open = false;
+    record(-1);
+  }
+  void read(float* ms) {
+    for (int k = 0; k + 1 < n; ++k) {
+      float t = 0.f;
+      if (phase[k] >= 0 && cudaEventElapsedTime(&t, h->ph_ev[k], h->ph_ev[k + 1]) == cudaSuccess)
+        ms[phase[k]] += t;
+    }
+    cudaGetLastError();
+  }
+  ~PhaseClock() {
+    if (nvtx_open) nvtxRangePop();
+  }
+};
+
 int validate(zolo_handle_t h, const void* A, int64_t m, int64_t n, int64_t lda, const void* P,
              int64_t ldp, const void* Q, int64_t ldq, const zolo_opts_t* o) {
   if (!h) return -1;
@@ -482,6 +588,7 @@ int validate(zolo_handle_t h, const void* A, int64_t m, int64_t n, int64_t lda, 
         o->max_iter < 1 || o->max_iter > kMaxIters || o->ns_steps < 0 ||
         o->ns_steps > 4 || (o->prec != ZOLO_FP64 && o->prec != ZOLO_SPLIT_BF16) ||
         o->force_qr < -1 || o->force_qr > 1 || o->chol_form < 0 || o->chol_form > 2 ||
+        o->estimate < 0 || o->estimate > 1 ||
         (o->alpha > 0.0 && o->beta > o->alpha))
       return -10;
   } else {
@@ -538,7 +645,8 @@ std::array<int64_t, 4> tune_key(int64_t m, int64_t n, int prec, double ell0) {
 
 int pd_core(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda, double* Qp,
             int64_t ldq, double* H, int64_t ldh, const zolo_opts_t& o, zolo_info_t* info,
-            cudaStream_t st, bool svd, PdBufs* out_bufs, const ShardCtx* shard = nullptr);
+            cudaStream_t st, bool svd, PdBufs* out_bufs, const ShardCtx* shard = nullptr,
+            PhaseClock* pc = nullptr);
 
 // r = ZOLO_R_TUNED: the cached r for this key, else every r whose schedule
 // converges within max_iter is run on A itself and timed, and the fastest kept.
@@ -607,7 +715,9 @@ int tune_r(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda, 
 
 int pd_core(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda, double* Qp,
             int64_t ldq, double* H, int64_t ldh, const zolo_opts_t& o, zolo_info_t* info,
-            cudaStream_t st, bool svd, PdBufs* out_bufs, const ShardCtx* shard) {
+            cudaStream_t st, bool svd, PdBufs* out_bufs, const ShardCtx* shard,
+            PhaseClock* pc) {
+  if (pc) pc->mark(ZOLO_PHASE_BOUNDS);
   // alpha: caller's bound or min(||A||_F, sqrt(||A||_1 ||A||_inf))
   double alpha = o.alpha;
   int r_sched = o.r;
@@ -652,7 +762,7 @@ int pd_core(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda,
   if (o.prec == ZOLO_SPLIT_BF16)
     if (int e = split.begin(h, m, n, r, st)) return e;
   CK(cudaMemsetAsync(b.status, 0, sizeof(int) * kStatSlots, st));
-  CK(cudaMemsetAsync(b.norms, 0, sizeof(double) * 2 * (kMaxIters + 2), st));
+  CK(cudaMemsetAsync(b.norms, 0, sizeof(double) * kNormSlots, st));
 
   double* X = b.X;
   double* Xn = b.Xn;
@@ -669,6 +779,7 @@ int pd_core(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda,
   for (int k = 0; k < sch.iters; ++k) {
     const Coefficients& co = sch.co[k];
     bool qr = o.force_qr == 1 ? true : (o.force_qr == 0 ? false : sch.use_qr[k]);
+    if (pc) pc->mark(qr ? ZOLO_PHASE_QR : ZOLO_PHASE_CHOL);
     if (shard) {
       // each rank forms its own shifts' terms; the caller's sum joins them
       bool redo = false;
@@ -729,6 +840,7 @@ int pd_core(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda,
     }
   }
   // Newton-Schulz refinement steps (nine slices on the split path, as the iteration)
+  if (pc && o.ns_steps > 0) pc->mark(ZOLO_PHASE_NS);
   for (int s = 0; s < o.ns_steps; ++s) {
     GemmArgs g;
     g.M = g.N = (int)n; g.K = (int)m; g.transA = 1;
@@ -744,6 +856,7 @@ int pd_core(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda,
     std::swap(X, Xn);
   }
   // H = (Qp^T A + A^T Qp) / 2 with the original A
+  if (pc) pc->mark(ZOLO_PHASE_H);
   {
     GemmArgs g;
     g.M = g.N = (int)n; g.K = (int)m; g.transA = 1;
@@ -753,12 +866,17 @@ int pd_core(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda,
     CK(symmetrize(b.M, n, H, ldh, n, st));
     CK(copy_matrix(X, m, Qp, ldq, m, n, st));
   }
+  if (o.estimate) {
+    if (pc) pc->mark(ZOLO_PHASE_EST);
+    if (int e = enqueue_estimates(b, A, lda, Qp, ldq, H, ldh, m, n, st)) return e;
+  }
   // final status and norms
-  double hn[2 * (kMaxIters + 2)];
+  double hn[kNormSlots];
   CK(cudaMemcpyAsync(hn, b.norms, sizeof(hn), cudaMemcpyDeviceToHost, st));
   if (int e = read_status(R, hstat)) return e;
   info->iters = it;
   for (int k = 0; k < it; ++k) info->delta[k] = hn[2 * k + 1] > 0 ? std::sqrt(hn[2 * k] / hn[2 * k + 1]) : 0.0;
+  if (o.estimate) fill_estimates(info, hn, n);
   if (split.on) {
     int herr = 0;
     CK(cudaMemcpy(&herr, h->err, sizeof(int), cudaMemcpyDeviceToHost));
@@ -775,7 +893,7 @@ int pd_core(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda,
 constexpr int kBatchLanes = 32;
 
 // Per-matrix device record of the batched path: status words, then norms.
-constexpr int kRecDoubles = 4 + 2 * (kMaxIters + 2);
+constexpr int kRecDoubles = 4 + kNormSlots;
 
 // Queue one polar decomposition on `st` without any host synchronisation:
 // status and norms go to R.b.status / R.b.norms (the matrix's own record).
@@ -785,7 +903,7 @@ int pd_enqueue(const Run& R, const double* A, int64_t lda, double* Qp, int64_t l
   const PdBufs& b = R.b;
   cudaStream_t st = R.st;
   CK(cudaMemsetAsync(b.status, 0, sizeof(int) * kStatSlots, st));
-  CK(cudaMemsetAsync(b.norms, 0, sizeof(double) * 2 * (kMaxIters + 2), st));
+  CK(cudaMemsetAsync(b.norms, 0, sizeof(double) * kNormSlots, st));
   double* X = b.X;
   double* Xn = b.Xn;
   CK(scale_copy(A, lda, X, m, m, n, 1.0 / alpha, st));
@@ -816,7 +934,24 @@ int pd_enqueue(const Run& R, const double* A, int64_t lda, double* Qp, int64_t l
   CK(gemm_any(g, st));
   CK(symmetrize(b.M, n, H, ldh, n, st));
   CK(copy_matrix(X, m, Qp, ldq, m, n, st));
+  if (o.estimate)
+    if (int e = enqueue_estimates(b, A, lda, Qp, ldq, H, ldh, m, n, st)) return e;
   return 0;
+}
+
+// zolo_pd_async's host function: the copied status words and norms into the
+// caller's zolo_info_t (no CUDA call is made here).
+void CUDART_CB async_done(void* p) {
+  AsyncSlot* s = static_cast<AsyncSlot*>(p);
+  zolo_info_t inf = s->base;
+  for (int k = 0; k < inf.iters; ++k)
+    inf.delta[k] = s->norms[2 * k + 1] > 0.0 ? std::sqrt(s->norms[2 * k] / s->norms[2 * k + 1]) : 0.0;
+  if (s->estimate) fill_estimates(&inf, s->norms, s->n);
+  inf.status = s->err ? ZOLO_ETIMEOUT
+                      : s->stat[kStatNonFinite] ? ZOLO_ENONFINITE
+                                                : s->stat[kStatCholFail] ? ZOLO_ECHOL : ZOLO_OK;
+  *s->out = inf;
+  s->busy = 0;
 }
 
 int grow(void** p, size_t* have, size_t bytes) {
@@ -848,6 +983,7 @@ void zolo_opts_default(zolo_opts_t* o) {
   o->prec = ZOLO_FP64;
   o->force_qr = -1;
   o->chol_form = 0;
+  o->estimate = 0;
 }
 
 int zolo_create(zolo_handle_t* handle, int device) {
@@ -890,6 +1026,16 @@ int zolo_destroy(zolo_handle_t h) {
   if (h->hrec) cudaFreeHost(h->hrec);
   if (h->e0) cudaEventDestroy(h->e0);
   if (h->e1) cudaEventDestroy(h->e1);
+  for (cudaEvent_t ev : h->ph_ev)
+    if (ev) cudaEventDestroy(ev);
+  if (h->async) {
+    for (int k = 0; k < kAsyncSlots; ++k)
+      if (h->async[k].busy) {   // a host function still to run reads this ring
+        cudaDeviceSynchronize();
+        break;
+      }
+    cudaFreeHost(h->async);
+  }
   delete h;
   return 0;
 }
@@ -945,16 +1091,91 @@ int zolo_pd(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda,
   if (cudaSetDevice(h->device) != cudaSuccess) return info->status = ZOLO_ECUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   TunerScope ts(&h->tuner);
+  PhaseClock pc;
+  pc.start(h, st);
   cudaEventRecord(h->e0, st);
-  int e = pd_core(h, A, m, n, lda, Qp, ldq, H, ldh, *opts, info, st, false, nullptr);
+  int e = pd_core(h, A, m, n, lda, Qp, ldq, H, ldh, *opts, info, st, false, nullptr, nullptr, &pc);
+  pc.stop();
   cudaEventRecord(h->e1, st);
   if (cudaEventSynchronize(h->e1) == cudaSuccess) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, h->e0, h->e1);
     info->ms = ms;
+    pc.read(info->ms_phase);
   }
   info->status = e;
   return e;
+}
+
+int zolo_pd_async(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda, double* Qp,
+                  int64_t ldq, double* H, int64_t ldh, const zolo_opts_t* opts, zolo_info_t* info,
+                  void* stream) {
+  if (int e = validate(h, A, m, n, lda, Qp, ldq, H, ldh, opts)) return e;
+  const zolo_opts_t& o = *opts;
+  if (!(o.alpha > 0.0) || !(o.beta > 0.0) || o.r == ZOLO_R_TUNED || o.posteriori) return -10;
+  if (!info) return -11;
+  std::memset(info, 0, sizeof(*info));
+  if (cudaSetDevice(h->device) != cudaSuccess) return info->status = ZOLO_ECUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!h->async) {
+    void* p = nullptr;
+    if (cudaMallocHost(&p, sizeof(AsyncSlot) * kAsyncSlots) != cudaSuccess) {
+      cudaGetLastError();
+      return info->status = ZOLO_ENOMEM;
+    }
+    std::memset(p, 0, sizeof(AsyncSlot) * kAsyncSlots);
+    h->async = static_cast<AsyncSlot*>(p);
+  }
+  AsyncSlot* slot = &h->async[h->async_next];
+  // a slot still waiting for its host function belongs to a call 64 back on this
+  // stream: wait for it (calls on one handle are ordered on one stream)
+  if (slot->busy && cudaStreamSynchronize(st) != cudaSuccess) return info->status = ZOLO_ECUDA;
+  // kernels measured so far are used; none is timed here (timing synchronises)
+  const bool was_tuning = h->tuner.tuning;
+  h->tuner.tuning = false;
+  TunerScope ts(&h->tuner);
+  struct Restore {
+    zolo_handle_t h;
+    bool v;
+    ~Restore() { h->tuner.tuning = v; }
+  } restore{h, was_tuning};
+  const double ell0 = std::min(1.0, o.beta / o.alpha);
+  Schedule sch;
+  if (build_schedule(ell0, o.r, o.max_iter, &sch) != 0) return -10;
+  Run R{m, n, sch.r, {}, st};
+  R.inv_chol = use_inverse_form(o.chol_form, m, n, sch.r);
+  if (int e = ensure_ws(h, layout(nullptr, m, n, sch.r, false, &R.b))) return info->status = e;
+  layout(h->ws, m, n, sch.r, false, &R.b);
+  SplitScope split;
+  if (o.prec == ZOLO_SPLIT_BF16)
+    if (int e = split.begin(h, m, n, sch.r, st)) return info->status = e;
+  if (int e = pd_enqueue(R, A, lda, Qp, ldq, H, ldh, sch, o, o.alpha)) return info->status = e;
+  zolo_info_t& base = slot->base;
+  std::memset(&base, 0, sizeof(base));
+  base.r = sch.r;
+  base.iters = sch.iters;
+  base.chol_form = R.inv_chol ? 2 : 1;
+  base.ell[0] = sch.ell[0];
+  for (int k = 0; k < sch.iters; ++k) {
+    base.used_qr[k] = o.force_qr == 1 ? 1 : (o.force_qr == 0 ? 0 : sch.use_qr[k]);
+    base.ell[k + 1] = sch.ell[k + 1];
+  }
+  slot->out = info;
+  slot->n = n;
+  slot->estimate = o.estimate;
+  slot->err = 0;
+  slot->busy = 1;
+  CK(cudaMemcpyAsync(slot->stat, R.b.status, sizeof(slot->stat), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(slot->norms, R.b.norms, sizeof(slot->norms), cudaMemcpyDeviceToHost, st));
+  if (split.on)
+    CK(cudaMemcpyAsync(&slot->err, h->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  info->status = ZOLO_EPENDING;
+  if (cudaLaunchHostFunc(st, async_done, slot) != cudaSuccess) {
+    slot->busy = 0;
+    return info->status = ZOLO_ECUDA;
+  }
+  h->async_next = (h->async_next + 1) % kAsyncSlots;
+  return 0;
 }
 
 int zolo_shift_range(int r, int rank, int nranks, int* j0, int* j1) {
@@ -988,12 +1209,16 @@ int zolo_pd_sharded(zolo_handle_t h, const double* A, int64_t m, int64_t n, int6
   sh.fn = sum;
   sh.ctx = ctx;
   cudaEventRecord(h->e0, st);
-  int e = pd_core(h, A, m, n, lda, Qp, ldq, H, ldh, *opts, info, st, false, nullptr, &sh);
+  PhaseClock pc;
+  pc.start(h, st);
+  int e = pd_core(h, A, m, n, lda, Qp, ldq, H, ldh, *opts, info, st, false, nullptr, &sh, &pc);
+  pc.stop();
   cudaEventRecord(h->e1, st);
   if (cudaEventSynchronize(h->e1) == cudaSuccess) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, h->e0, h->e1);
     info->ms = ms;
+    pc.read(info->ms_phase);
   }
   info->status = e;
   return e;
@@ -1023,8 +1248,11 @@ int zolo_svd(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda
   }
   double* Qp = b.Qp_int;
   double* Hm = b.H_int;
-  e = pd_core(h, A, m, n, lda, Qp, m, Hm, n, *opts, info, st, true, &b);
+  PhaseClock pc;
+  pc.start(h, st);
+  e = pd_core(h, A, m, n, lda, Qp, m, Hm, n, *opts, info, st, true, &b, nullptr, &pc);
   if (e == 0) {
+    pc.mark(ZOLO_PHASE_EIG);
     std::vector<double> lam(n);
     int sweeps = 0;
     b.eig.stall = h->dbg_stall == ZOLO_STALL_JACOBI32;
@@ -1041,6 +1269,7 @@ int zolo_svd(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda
         sv[i] = std::fabs(lam[i]);
         sg[i] = lam[i] < 0.0 ? -1.0 : 1.0;
       }
+      pc.mark(ZOLO_PHASE_U);
       GemmArgs g;
       g.M = (int)m; g.N = (int)n; g.K = (int)n;
       g.A = Qp; g.lda = m; g.B = V; g.ldb = ldv; g.Cout = U; g.ldcout = ldu;
@@ -1056,11 +1285,13 @@ int zolo_svd(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda
       if (cudaStreamSynchronize(st) != cudaSuccess) e = ZOLO_ECUDA;
     }
   }
+  pc.stop();
   cudaEventRecord(h->e1, st);
   if (cudaEventSynchronize(h->e1) == cudaSuccess) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, h->e0, h->e1);
     info->ms = ms;
+    pc.read(info->ms_phase);
   }
   info->status = e;
   return e;
@@ -1464,6 +1695,7 @@ int zolo_pd_batched(zolo_handle_t h, int count, const double* const* A, const in
       const double* nk = rec + 4 + 2 * k;
       inf.delta[k] = nk[1] > 0.0 ? std::sqrt(nk[0] / nk[1]) : 0.0;
     }
+    if (opts[i].estimate) fill_estimates(&inf, rec + 4, n[i]);
     int e = 0;
     if (stv[kStatCholFail]) {
       // redo this matrix on the single-matrix path, which falls back to the QR form

@@ -156,6 +156,26 @@ __global__ void frob_kernel(const double* __restrict__ A, int64_t lda, int64_t m
   }
 }
 
+// Partial sums of ||G - I||_F^2 from the upper triangle of a symmetric G (each
+// off-diagonal entry counted twice).
+__global__ void gram_dev_kernel(const double* __restrict__ G, int64_t ldg, int64_t n,
+                                double* __restrict__ partials) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e % n, j = e / n;
+    if (i > j) continue;
+    const double d = G[i + j * ldg] - (i == j ? 1.0 : 0.0);
+    s = fma(i == j ? 1.0 : 2.0, d * d, s);
+  }
+  const double t = block_sum(s, red);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = t;
+    partials[2 * blockIdx.x + 1] = 0.0;
+  }
+}
+
 // Row sums of |A| over a chunk of kAbsChunk columns: part[i + c m] for chunk c.
 constexpr int kAbsChunk = 256;
 
@@ -369,6 +389,17 @@ double alpha_from_sums(const double* sums) {
   const double holder = std::sqrt(sums[1]) * std::sqrt(sums[2]);
   if (!std::isfinite(fro)) return fro;
   return holder < fro ? holder : fro;
+}
+
+cudaError_t gram_identity_dev2(const double* G, int64_t ldg, int64_t n, double* partials,
+                               double* out, cudaStream_t st) {
+  {
+    ProfScope ps(kProfOther, st);
+    gram_dev_kernel<<<kReduceBlocks, kThreads, 0, st>>>(G, ldg, n, partials);
+  }
+  ProfScope ps(kProfOther, st);
+  finish_pairs_kernel<<<1, 1024, 0, st>>>(partials, kReduceBlocks, out);
+  return cudaGetLastError();
 }
 
 cudaError_t frob_norm2(const double* A, int64_t lda, int64_t m, int64_t n, double* partials,

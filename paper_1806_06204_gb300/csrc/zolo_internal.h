@@ -230,6 +230,10 @@ cudaError_t symmetrize(const double* M, int64_t ldm, double* H, int64_t ldh, int
                        cudaStream_t st);
 cudaError_t check_finite(const double* A, int64_t lda, int64_t m, int64_t n, int* status,
                          cudaStream_t st);
+// ||G - I||_F^2 into out[0] from the upper triangle of a symmetric n x n G
+// (out[1] = 0)
+cudaError_t gram_identity_dev2(const double* G, int64_t ldg, int64_t n, double* partials,
+                               double* out, cudaStream_t st);
 // ||A||_F^2 into out[0] (via partials)
 cudaError_t frob_norm2(const double* A, int64_t lda, int64_t m, int64_t n, double* partials,
                        double* out, cudaStream_t st);
