@@ -406,9 +406,19 @@ def batch_arm(args, w, h, mats, As, Qps, Hs, split, steps, warmup, local, dist):
             dist.barrier()
 
     infos = None
+    # --autotune-batch: the first warm-up call measures the batch's contraction
+    # shapes (zolo_autotune) and the timed calls replay the kept kernels.  Off by
+    # default: on the batch of 512 the kept kernels measured no faster (split
+    # 275.3 vs 275.1 matrices/s, FP64 71.0 vs 71.8) -- they win alone on the GPU,
+    # but 32 lanes in flight already fill it
+    tuning = args.autotune_batch and warmup > 0
+    if tuning:
+        zb.autotune(h, True)
     for _ in range(warmup):
         infos = step()
     torch.cuda.synchronize()
+    if tuning:
+        zb.autotune(h, False)
     stream = torch.cuda.current_stream()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -454,6 +464,7 @@ def batch_arm(args, w, h, mats, As, Qps, Hs, split, steps, warmup, local, dist):
            "statuses_nonzero": sum(1 for i in infos if i.status),
            "bar": 1e-13, "bar_met": bool(bwd <= 1e-13 and orth <= 1e-13)}
     return {"os": os_, "ms_step": ms_step, "flops": flops, "infos": infos, "launches": launches,
+            "autotune": bool(tuning),
             "kstats": kstats, "roof": roof, "acc": acc, "clocks": clk.summary(),
             "steps": steps, "warmup": warmup}
 
@@ -534,6 +545,7 @@ def run_batch(args, w, rank, world, dist, local):
                            "r_hist": {str(r): sum(1 for i in infos if i.r == r)
                                       for r in sorted({i.r for i in infos})},
                            "l2": "inputs larger than L2 (1.6 GB of A per step; no flush)",
+                           "autotune": arm["autotune"],
                            "parallelism": "replicas" if world > 1 else "single"},
                 "eff_tflops": world * arm["flops"] / (arm["ms_step"] / 1000.0) / 1e12,
                 "pd_model_flops": arm["flops"], "accuracy": arm["acc"], "roofline": arm["roof"],
@@ -591,6 +603,9 @@ def main():
                          "(default)")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="built-in kernel rules only")
+    ap.add_argument("--autotune-batch", action="store_true",
+                    help="batch workload: measure the contraction kernels during the warm-up "
+                         "steps (off by default: no gain measured on the batch of 512)")
     ap.add_argument("--tune-cache", default=None,
                     help="tuning-cache file: loaded before the warm-up steps when it exists, "
                          "written after them")

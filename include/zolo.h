@@ -322,7 +322,14 @@ int zolo_dgemm_noalloc(int transA, int transB, int64_t m, int64_t n, int64_t k, 
    cost model puts it 4x behind the other.  zolo_autotune(h, 0) stops measuring; choices already made stay in
    use.  Without choices the built-in rules apply (the split path where its
    cost model predicts a gain, else the 64x64 FP64 tile, 32x128 for M <= 32).
-   zolo_pd_batched always uses the built-in rules.  A tuned kernel may sum in
+   zolo_pd_batched uses the handle's choices too: with tuning on, it first
+   decomposes one matrix of every distinct configuration of the batch (sizes,
+   r, iteration forms, options) on the caller's stream, outside any capture,
+   while the shapes met are timed; its concurrent lanes then replay the
+   choices, each with its own split-K scratch.  There the split-or-FP64 choice
+   stays with the batch's throughput cost model (many calls in flight hide
+   each call's latency), and only the FP64 kernels of the products it leaves
+   on the FP64 pipe are measured.  A tuned kernel may sum in
    another order than the built-in one: results agree to rounding, not bit for
    bit.  Returns 0, -1 (NULL handle) or -2 (enable not 0/1).
 

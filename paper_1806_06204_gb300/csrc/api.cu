@@ -20,6 +20,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -62,6 +63,10 @@ struct BatchSlot {
   int* exps = nullptr;
   size_t exp_elems = 0;
   int* err = nullptr;
+  // the handle's kernel choices as this lane replays them, with the lane's own
+  // scratch for split-K partial sums (lanes run concurrently)
+  std::unique_ptr<GemmTuner> tuner;
+  uint64_t tuner_gen = ~0ull;
 };
 
 struct BatchGraph {
@@ -1421,7 +1426,8 @@ int zolo_pd_batched(zolo_handle_t h, int count, const double* const* A, const in
   if (count < 0) return -2;
   if (count == 0) return 0;
   if (!A || !m || !n || !lda || !Qp || !ldq || !H || !ldh || !opts || !info) return -3;
-  // the lanes run concurrently and are graph-captured: built-in kernel rules only
+  // kernel choices come from the handle's tuner (per lane below); none is timed
+  // while the lanes are queued
   TunerScope no_tuner(nullptr);
   for (int i = 0; i < count; ++i) {
     std::memset(&info[i], 0, sizeof(zolo_info_t));
@@ -1560,6 +1566,54 @@ int zolo_pd_batched(zolo_handle_t h, int count, const double* const* A, const in
       h->hrec_count = (size_t)count * kRecDoubles;
     }
   }
+  // ---- kernel choices (zolo_autotune).  With tuning on, one matrix of every
+  // distinct configuration (sizes, r, iteration forms, options) is decomposed
+  // first on the caller's stream, outside any capture, in lane 0's workspace,
+  // while the handle's tuner times the contraction shapes it meets; the lanes
+  // then replay the handle's choices, each with its own split-K scratch.
+  if (h->tuner.tuning) {
+    TunerScope ts(&h->tuner);
+    std::map<std::vector<int64_t>, int> seen;
+    BatchSlot& sl = h->slots[0];
+    for (int i = 0; i < count; ++i) {
+      const bool inv = use_inverse_form(opts[i].chol_form, m[i], n[i], sch[i].r);
+      std::vector<int64_t> cfg = {m[i], n[i], sch[i].r, sch[i].iters, opts[i].prec,
+                                  opts[i].ns_steps, opts[i].force_qr, inv ? 1 : 0, opts[i].estimate};
+      for (int k = 0; k < sch[i].iters; ++k) cfg.push_back(sch[i].use_qr[k] ? 1 : 0);
+      if (!seen.emplace(cfg, i).second) continue;
+      Run R{m[i], n[i], sch[i].r, {}, st};
+      R.inv_chol = inv;
+      R.narrow_panels = true;
+      layout(sl.ws, m[i], n[i], sch[i].r, false, &R.b);
+      SplitWork w{sl.slices, sl.slice_elems, sl.exps, sl.exp_elems, sl.err, 9};
+      w.throughput = true;
+      set_split_engine(opts[i].prec == ZOLO_SPLIT_BF16 ? &w : nullptr);
+      const int e = pd_enqueue(R, A[i], lda[i], Qp[i], ldq[i], H[i], ldh[i], sch[i], opts[i],
+                               alpha[i]);
+      set_split_engine(nullptr);
+      if (e) return e;
+    }
+    CK(cudaStreamSynchronize(st));
+  }
+  for (int k = 0; k < nslots; ++k) {
+    BatchSlot& sl = h->slots[k];
+    if (!sl.tuner) sl.tuner.reset(new GemmTuner());
+    if (sl.tuner_gen != h->tuner.gen) {
+      sl.tuner->choice = h->tuner.choice;
+      sl.tuner_gen = h->tuner.gen;
+    }
+    sl.tuner->tuning = false;
+    if (sl.tuner->scratch_elems < h->tuner.scratch_elems) {
+      if (sl.tuner->scratch) cudaFree(sl.tuner->scratch);
+      sl.tuner->scratch = nullptr;
+      sl.tuner->scratch_elems = 0;
+      if (cudaMalloc(&sl.tuner->scratch, h->tuner.scratch_elems * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return ZOLO_ENOMEM;
+      }
+      sl.tuner->scratch_elems = h->tuner.scratch_elems;
+    }
+  }
   if (!h->cap && cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess)
     return ZOLO_ECUDA;
   if (!h->joined && cudaEventCreateWithFlags(&h->joined, cudaEventDisableTiming) != cudaSuccess)
@@ -1570,6 +1624,7 @@ int zolo_pd_batched(zolo_handle_t h, int count, const double* const* A, const in
   key.reserve(8 + 12 * (size_t)count);
   key.push_back((uint64_t)count);
   key.push_back((uint64_t)(uintptr_t)h->brec);
+  key.push_back(h->tuner.gen);   // graphs recorded with older kernel choices are not replayed
   for (int k = 0; k < nslots; ++k) key.push_back((uint64_t)(uintptr_t)h->slots[k].ws);
   for (int i = 0; i < count; ++i) {
     const uint64_t f[] = {(uint64_t)(uintptr_t)A[i], (uint64_t)m[i], (uint64_t)n[i],
@@ -1614,6 +1669,7 @@ int zolo_pd_batched(zolo_handle_t h, int count, const double* const* A, const in
       w.stall = h->dbg_stall == ZOLO_STALL_SPLIT_GEMM;
       w.stall_ns = h->dbg_ns;
       set_split_engine(opts[i].prec == ZOLO_SPLIT_BF16 ? &w : nullptr);
+      TunerScope lane_tuner(sl.tuner.get());
       const int e = pd_enqueue(R, A[i], lda[i], Qp[i], ldq[i], H[i], ldh[i], sch[i], opts[i], alpha[i]);
       set_split_engine(nullptr);
       if (e) return e;
@@ -1807,6 +1863,7 @@ int zolo_tune_load(zolo_handle_t h, const char* path) {
   if (rc) return rc;
   for (const auto& kv : got_r) h->tuned_r[kv.first] = kv.second;
   for (const auto& kv : got_g) h->tuner.choice[kv.first] = kv.second;
+  if (!got_g.empty()) ++h->tuner.gen;
   return 0;
 }
 

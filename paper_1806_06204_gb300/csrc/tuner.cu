@@ -137,7 +137,13 @@ int tune(GemmTuner& t, const GemmArgs& g, SplitWork* split, cudaStream_t st) {
 }
 
 // The tuned or built-in choice for g (split = the split engine, if allowed).
-int choose(const GemmArgs& g, SplitWork* split, cudaStream_t st) {
+// In zolo_pd_batched's lanes (split->throughput) the GPU-throughput router alone
+// decides the split path; a tuner there only picks among the FP64 kernels of the
+// products the router leaves on the FP64 pipe (under the FP64-only key).
+int choose(const GemmArgs& g, SplitWork* split_engine, cudaStream_t st) {
+  const bool thr = split_engine && split_engine->throughput;
+  if (thr && split_preferred(g, *split_engine)) return kGemmVSplit;
+  SplitWork* split = thr ? nullptr : split_engine;
   GemmTuner* t = t_tuner;
   if (t && !t->busy) {
     const auto key = gemm_key(g, split ? split->slices_s : 0);
@@ -156,6 +162,7 @@ int choose(const GemmArgs& g, SplitWork* split, cudaStream_t st) {
       cudaGetLastError();
       if (v >= 0) {
         t->choice[key] = v;
+        ++t->gen;
         return v;
       }
     }

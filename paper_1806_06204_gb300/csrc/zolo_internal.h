@@ -136,6 +136,7 @@ cudaError_t gemm_f64(const GemmArgs& g, cudaStream_t st);
 // No tuning while the stream is being captured.
 struct GemmTuner {
   std::map<std::array<int, 7>, int> choice;
+  uint64_t gen = 0;      // bumped whenever `choice` changes (graph replay keys)
   bool tuning = false;
   bool busy = false;
   double* scratch = nullptr;

@@ -172,3 +172,34 @@ def test_in_place_product_keeps_a_safe_kernel(zb):
             assert np.max(np.abs(C.cpu().numpy() - A @ B0)) <= 1e-12
     finally:
         h.close()
+
+
+def test_batched_call_with_tuning_equals_tuned_single_calls(zb):
+    # zolo_autotune on: the batched call measures the shapes of one matrix per
+    # configuration before its lanes start, and the lanes replay those choices,
+    # each with its own split-K scratch; FP64 single calls on the same handle then
+    # use the same kernels and agree bit for bit (m < 512: the same panel kernel)
+    from paper_1806_06204_gb300 import synth
+    h = zb.Handle(0)
+    try:
+        zb.autotune(h, True)
+        specs = [(200, 150, 1e6), (96, 96, 1e10), (300, 120, 40.0), (200, 150, 3e5)]
+        mats = [synth.make_matrix(m, n, synth.geometric_sigma(n, k), seed=1070 + i)
+                for i, (m, n, k) in enumerate(specs)]
+        As = [dev(sm.A) for sm in mats]
+        os_ = [zb.opts(beta=float(sm.sigma[-1])) for sm in mats]
+        Qps, Hs, infos, st = zb.zolo_pd_batched(h, As, os_)
+        assert st == 0
+        first = [(q.cpu().numpy().copy(), x.cpu().numpy().copy()) for q, x in zip(Qps, Hs)]
+        for sm, a, o, (q, x) in zip(mats, As, os_, first):
+            assert zo.orthogonality(q) < 1e-13 and zo.backward_error_pd(sm.A, q, x) < 1e-13
+            q1, h1, _ = zb.zolo_pd(h, a, o)
+            assert np.array_equal(q, q1.cpu().numpy()) and np.array_equal(x, h1.cpu().numpy())
+        # the tuned graph is replayed with the same bits
+        zb.autotune(h, False)
+        _, _, _, st2 = zb.zolo_pd_batched(h, As, os_, Qps=Qps, Hs=Hs)
+        assert st2 == 0
+        for (q, x), q2, x2 in zip(first, Qps, Hs):
+            assert np.array_equal(q, q2.cpu().numpy()) and np.array_equal(x, x2.cpu().numpy())
+    finally:
+        h.close()
