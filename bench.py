@@ -328,8 +328,11 @@ def run_reference(args, w, rank):
 # SMs, CUDA events): the FP64 pipe's measured ceiling beside the derived peak.
 FP64_DFMA_MEASURED_TFLOPS = 1.20
 # Tensor-core products issued per FP64-equivalent flop on the split path: nine
-# slices per operand, slice pairs (s, t) with s + t <= 11.
+# BF16 slices per operand, slice pairs (s, t) with s + t <= 11: 53; eight FP16
+# slices, s + t <= 9: 36.
 SPLIT_PAIRS = 53
+SPLIT_PAIRS_OF = {"bf16": 53, "fp16": 36}
+SLICE_DTYPE = {"bf16": "bf16x9-slices->f64", "fp16": "fp16x8-slices->f64"}
 
 
 def roofline(kstats, step_ms, model_flops=None, split_pairs=SPLIT_PAIRS):
@@ -392,8 +395,9 @@ def batch_arm(args, w, h, mats, As, Qps, Hs, split, steps, warmup, local, dist):
     accuracy of every result."""
     import torch
     from paper_1806_06204_gb300 import binding as zb
+    sp = zb.ZOLO_SPLIT_FP16 if args.slices == "fp16" else zb.ZOLO_SPLIT_BF16
     os_ = [zb.opts(beta=float(sm.sigma[-1]), alpha=1.0, r=0,
-                   prec=zb.ZOLO_SPLIT_BF16 if split else zb.ZOLO_FP64, ns_steps=1 if split else 0,
+                   prec=sp if split else zb.ZOLO_FP64, ns_steps=1 if split else 0,
                    chol_form=args.chol_form)
            for sm in mats]
 
@@ -448,7 +452,7 @@ def batch_arm(args, w, h, mats, As, Qps, Hs, split, steps, warmup, local, dist):
     kstats = zb.profile_read()
     zb.profile(False)
     prof_ms = e2.elapsed_time(e3)
-    roof = roofline(kstats, prof_ms, flops)
+    roof = roofline(kstats, prof_ms, flops, split_pairs=SPLIT_PAIRS_OF[args.slices])
     roof["measured"] = ("one extra call after the timed steps with the batch's lanes "
                         "serialised and every launch bracketed by CUDA events (no graph replay): "
                         "each launch timed alone on the GPU")
@@ -531,14 +535,15 @@ def run_batch(args, w, rank, world, dist, local):
     if rank == 0:
         ns = [a.shape[1] for a in As]
         infos = arm["infos"]
-        desc = w["desc"] + (": split precision (nine BF16 slices, FP32 level sums) timed, plain "
+        sl = ("nine BF16 slices" if args.slices == "bf16" else "eight FP16 slices")
+        desc = w["desc"] + (f": split precision ({sl}, FP32 level sums) timed, plain "
                             "FP64 beside it" if prec == "both" else
-                            (": split precision (nine BF16 slices)" if head_split else
+                            (f": split precision ({sl})" if head_split else
                              ": plain FP64"))
         line = {"metric": METRIC, "value": value, "unit": "matrices/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": arm["ms_step"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "bf16x9-slices->f64" if head_split else "f64",
+                "dtype": (SLICE_DTYPE[args.slices] if head_split else "f64"),
                 "data": "synthetic",
                 "config": {"workload": args.workload, "desc": desc, "count": w["count"],
                            "n_min": min(ns), "n_max": max(ns), "prec": "split" if head_split else "fp64",
@@ -586,6 +591,9 @@ def main():
                     help="split: the iterations' products on the BF16 tensor cores (Ozaki slices); "
                          "both (batch only): split timed, FP64 beside it; auto: both for the "
                          "batch, fp64 otherwise")
+    ap.add_argument("--slices", default="bf16", choices=["bf16", "fp16"],
+                    help="split precision's slices: nine BF16 six-bit slices (53 slice-pair "
+                         "products) or eight FP16 seven-bit slices (36)")
     ap.add_argument("--fp64-steps", type=int, default=None,
                     help="timed steps of the FP64 arm with --prec both (default min(steps, 5))")
     ap.add_argument("--fp64-warmup", type=int, default=None,
@@ -667,8 +675,9 @@ def main():
     split = args.prec == "split"
     beta_scale = args.beta_scale if args.beta_scale is not None else w.get("beta_scale", 1.0)
     r_req = args.r if args.r is not None else w["r"]
+    sp = zb.ZOLO_SPLIT_FP16 if args.slices == "fp16" else zb.ZOLO_SPLIT_BF16
     o = zb.opts(beta=float(np.min(sm.sigma)) * beta_scale, alpha=1.0, r=r_req,
-                prec=zb.ZOLO_SPLIT_BF16 if split else zb.ZOLO_FP64, ns_steps=1 if split else 0,
+                prec=sp if split else zb.ZOLO_FP64, ns_steps=1 if split else 0,
                 chol_form=args.chol_form)
     m, n = w["m"], w["n"]
 
@@ -726,7 +735,7 @@ def main():
     torch.cuda.synchronize()
     kstats = zb.profile_read()
     zb.profile(False)
-    roof = roofline(kstats, e2.elapsed_time(e3), flops)
+    roof = roofline(kstats, e2.elapsed_time(e3), flops, split_pairs=SPLIT_PAIRS_OF[args.slices])
     roof["measured"] = "one extra step after the timed ones, per-launch CUDA events"
 
     # end to end through the host-buffer entry point
@@ -784,7 +793,7 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
                 "higher_is_better": True, "scaling": "strong" if shard else "weak",
                 "vs_baseline": None,
-                "dtype": "f64" if not split else "bf16x9-slices->f64",
+                "dtype": "f64" if not split else SLICE_DTYPE[args.slices],
                 "data": "synthetic",
                 "config": {"workload": args.workload, "desc": w["desc"], "m": m, "n": n,
                            "kappa": w["kappa"], "r": info.r, "r_requested": r_req,

@@ -113,6 +113,8 @@ namespace {
 
 constexpr double kEps = 2.220446049250313e-16;
 
+bool is_split(int prec) { return prec == ZOLO_SPLIT_BF16 || prec == ZOLO_SPLIT_FP16; }
+
 // Bump allocator over one device block; with base == nullptr it only sizes.
 struct Carve {
   char* base;
@@ -275,7 +277,7 @@ struct SplitScope {
   SplitWork w{};
   bool on = false;
   ~SplitScope() { set_split_engine(nullptr); }
-  int begin(zolo_handle_t h, int64_t m, int64_t n, int r, cudaStream_t st) {
+  int begin(zolo_handle_t h, int64_t m, int64_t n, int r, cudaStream_t st, int prec) {
     const size_t per = split_elems_per_entry(m, n);
     const size_t budget = (size_t)8 << 30;   // 16 GB of BF16 planes at most
     size_t want = std::max(per, std::min(per * (size_t)r, budget));
@@ -287,7 +289,8 @@ struct SplitScope {
     w.exps = h->exps;
     w.exp_elems = h->exp_elems;
     w.err = h->err;
-    w.slices_s = 9;
+    w.slices_s = prec == ZOLO_SPLIT_FP16 ? 8 : 9;
+    w.fp16 = prec == ZOLO_SPLIT_FP16;
     w.stall = h->dbg_stall == ZOLO_STALL_SPLIT_GEMM;
     w.stall_ns = h->dbg_ns;
     set_split_engine(&w);
@@ -591,7 +594,7 @@ int validate(zolo_handle_t h, const void* A, int64_t m, int64_t n, int64_t lda, 
   if (o) {
     if (o->r < ZOLO_R_TUNED || o->r > kMaxR || !std::isfinite(o->alpha) || !std::isfinite(o->beta) ||
         o->max_iter < 1 || o->max_iter > kMaxIters || o->ns_steps < 0 ||
-        o->ns_steps > 4 || (o->prec != ZOLO_FP64 && o->prec != ZOLO_SPLIT_BF16) ||
+        o->ns_steps > 4 || (o->prec != ZOLO_FP64 && !is_split(o->prec)) ||
         o->force_qr < -1 || o->force_qr > 1 || o->chol_form < 0 || o->chol_form > 2 ||
         o->estimate < 0 || o->estimate > 1 ||
         (o->alpha > 0.0 && o->beta > o->alpha))
@@ -669,9 +672,9 @@ int tune_r(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda, 
   {
     PdBufs tb;
     if (int e = ensure_ws(h, layout(nullptr, m, n, kMaxR, svd, &tb))) return e;
-    if (o.prec == ZOLO_SPLIT_BF16) {
+    if (is_split(o.prec)) {
       SplitScope pre;
-      if (int e = pre.begin(h, m, n, kMaxR, st)) return e;
+      if (int e = pre.begin(h, m, n, kMaxR, st, o.prec)) return e;
     }
   }
   cudaEvent_t t0 = nullptr, t1 = nullptr;
@@ -764,8 +767,8 @@ int pd_core(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda,
   if (out_bufs) *out_bufs = R.b;
   const PdBufs& b = R.b;
   SplitScope split;
-  if (o.prec == ZOLO_SPLIT_BF16)
-    if (int e = split.begin(h, m, n, r, st)) return e;
+  if (is_split(o.prec))
+    if (int e = split.begin(h, m, n, r, st, o.prec)) return e;
   CK(cudaMemsetAsync(b.status, 0, sizeof(int) * kStatSlots, st));
   CK(cudaMemsetAsync(b.norms, 0, sizeof(double) * kNormSlots, st));
 
@@ -1060,13 +1063,13 @@ int zolo_workspace_bytes(int64_t m, int64_t n, int r, int prec, int svd, uint64_
   if (n < 1 || n > INT32_MAX) return -2;
   if (m < n || m > INT32_MAX) return -1;
   if (r < ZOLO_R_TUNED || r > kMaxR) return -3;
-  if (prec != ZOLO_FP64 && prec != ZOLO_SPLIT_BF16) return -4;
+  if (prec != ZOLO_FP64 && !is_split(prec)) return -4;
   if (svd != 0 && svd != 1) return -5;
   if (!bytes) return -6;
   const int rr = r > 0 ? r : kMaxR;   // r chosen by the call: at most 8 shifts
   PdBufs b;
   uint64_t total = layout(nullptr, m, n, rr, svd != 0, &b);
-  if (prec == ZOLO_SPLIT_BF16) {
+  if (is_split(prec)) {
     // as SplitScope::begin asks for: slice planes (BF16), exponents (int), error flag
     const size_t per = split_elems_per_entry(m, n);
     const size_t want = std::max(per, std::min(per * (size_t)rr, (size_t)8 << 30));
@@ -1152,8 +1155,8 @@ int zolo_pd_async(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_
   if (int e = ensure_ws(h, layout(nullptr, m, n, sch.r, false, &R.b))) return info->status = e;
   layout(h->ws, m, n, sch.r, false, &R.b);
   SplitScope split;
-  if (o.prec == ZOLO_SPLIT_BF16)
-    if (int e = split.begin(h, m, n, sch.r, st)) return info->status = e;
+  if (is_split(o.prec))
+    if (int e = split.begin(h, m, n, sch.r, st, o.prec)) return info->status = e;
   if (int e = pd_enqueue(R, A, lda, Qp, ldq, H, ldh, sch, o, o.alpha)) return info->status = e;
   zolo_info_t& base = slot->base;
   std::memset(&base, 0, sizeof(base));
@@ -1387,8 +1390,8 @@ int zolo_dgemm(zolo_handle_t h, int transA, int transB, int64_t m, int64_t n, in
   if (!std::isfinite(beta)) return -12;
   if (m > 0 && n > 0 && !C) return -13;
   if (ldc < std::max<int64_t>(1, m)) return -14;
-  if (prec != ZOLO_FP64 && prec != ZOLO_SPLIT_BF16) return -15;
-  if (slices != 0 && slices != 8 && slices != 9) return -16;
+  if (prec != ZOLO_FP64 && !is_split(prec)) return -15;
+  if (slices != 0 && slices != 8 && !(slices == 9 && prec != ZOLO_SPLIT_FP16)) return -16;
   if (cudaSetDevice(h->device) != cudaSuccess) return ZOLO_ECUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   TunerScope ts(&h->tuner);
@@ -1408,6 +1411,7 @@ int zolo_dgemm(zolo_handle_t h, int transA, int transB, int64_t m, int64_t n, in
   if (int e = ensure_split(h, per, per, exps)) return e;
   if (cudaMemsetAsync(h->err, 0, sizeof(int), st) != cudaSuccess) return ZOLO_ECUDA;
   SplitWork w{h->slices, h->slice_elems, h->exps, h->exp_elems, h->err, S};
+  w.fp16 = prec == ZOLO_SPLIT_FP16;
   w.stall = h->dbg_stall == ZOLO_STALL_SPLIT_GEMM;
   w.stall_ns = h->dbg_ns;
   if (gemm_split(g, w, st) != cudaSuccess) return ZOLO_ECUDA;
@@ -1524,7 +1528,7 @@ int zolo_pd_batched(zolo_handle_t h, int count, const double* const* A, const in
     mmax = std::max(mmax, m[i]);
     nmax = std::max(nmax, n[i]);
     rmax = std::max(rmax, sch[i].r);
-    any_split |= opts[i].prec == ZOLO_SPLIT_BF16;
+    any_split |= is_split(opts[i].prec);
   }
   if ((int)h->slots.size() < nslots) h->slots.resize(nslots);
   if (!h->fork && cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming) != cudaSuccess)
@@ -1586,8 +1590,10 @@ int zolo_pd_batched(zolo_handle_t h, int count, const double* const* A, const in
       R.narrow_panels = true;
       layout(sl.ws, m[i], n[i], sch[i].r, false, &R.b);
       SplitWork w{sl.slices, sl.slice_elems, sl.exps, sl.exp_elems, sl.err, 9};
+      w.slices_s = opts[i].prec == ZOLO_SPLIT_FP16 ? 8 : 9;
+      w.fp16 = opts[i].prec == ZOLO_SPLIT_FP16;
       w.throughput = true;
-      set_split_engine(opts[i].prec == ZOLO_SPLIT_BF16 ? &w : nullptr);
+      set_split_engine(is_split(opts[i].prec) ? &w : nullptr);
       const int e = pd_enqueue(R, A[i], lda[i], Qp[i], ldq[i], H[i], ldh[i], sch[i], opts[i],
                                alpha[i]);
       set_split_engine(nullptr);
@@ -1665,10 +1671,12 @@ int zolo_pd_batched(zolo_handle_t h, int count, const double* const* A, const in
       R.b.status = reinterpret_cast<int*>(rec);
       R.b.norms = rec + 4;
       SplitWork w{sl.slices, sl.slice_elems, sl.exps, sl.exp_elems, sl.err, 9};
+      w.slices_s = opts[i].prec == ZOLO_SPLIT_FP16 ? 8 : 9;
+      w.fp16 = opts[i].prec == ZOLO_SPLIT_FP16;
       w.throughput = true;   // many lanes in flight: latency is hidden
       w.stall = h->dbg_stall == ZOLO_STALL_SPLIT_GEMM;
       w.stall_ns = h->dbg_ns;
-      set_split_engine(opts[i].prec == ZOLO_SPLIT_BF16 ? &w : nullptr);
+      set_split_engine(is_split(opts[i].prec) ? &w : nullptr);
       TunerScope lane_tuner(sl.tuner.get());
       const int e = pd_enqueue(R, A[i], lda[i], Qp[i], ldq[i], H[i], ldh[i], sch[i], opts[i], alpha[i]);
       set_split_engine(nullptr);
@@ -1762,7 +1770,7 @@ int zolo_pd_batched(zolo_handle_t h, int count, const double* const* A, const in
       inf.ms = ms;
     } else if (stv[kStatNonFinite]) {
       e = ZOLO_ENONFINITE;
-    } else if (timeout && opts[i].prec == ZOLO_SPLIT_BF16) {
+    } else if (timeout && is_split(opts[i].prec)) {
       e = ZOLO_ETIMEOUT;
     }
     inf.status = e;
@@ -1840,7 +1848,7 @@ int zolo_tune_load(zolo_handle_t h, const char* path) {
       long long a, b, c, d;
       int r;
       if (std::fscanf(f, "%lld %lld %lld %lld %d", &a, &b, &c, &d, &r) != 5 || r < 1 ||
-          r > kMaxR || a < 1 || b < 1 || a < b || (c != ZOLO_FP64 && c != ZOLO_SPLIT_BF16) ||
+          r > kMaxR || a < 1 || b < 1 || a < b || (c != ZOLO_FP64 && !is_split((int)c)) ||
           d < 0 || d > 400)
         rc = ZOLO_EINVAL;
       else
@@ -1850,7 +1858,7 @@ int zolo_tune_load(zolo_handle_t h, const char* path) {
       if (std::fscanf(f, "%d %d %d %d %d %d %d", &k[0], &k[1], &k[2], &k[3], &k[4], &k[5], &v) !=
               7 ||
           k[0] < 1 || k[1] < 1 || k[2] < 1 || k[3] < 1 || k[3] > kGemmMaxBatch || k[4] < 0 ||
-          k[4] > 255 || (k[5] != 0 && k[5] != 8 && k[5] != 9) ||
+          k[4] > 255 || (k[5] != 0 && k[5] != 8 && k[5] != 9 && k[5] != 108) ||
           !gemm_variant_allowed({k[0], k[1], k[2], k[3], k[4], k[5], 0}, v))
         rc = ZOLO_EINVAL;
       else

@@ -19,8 +19,21 @@
 // applies 2^(e_i + f_j) through the exponent field, alpha and beta in FP64.
 // Accuracy: |C - AB| <~ 8 sqrt(K) 2^-6S max|A_i.| max|B_.j|, dominated by the
 // rounding of N against a row maximum in [1/4, 1/2) (S = 9: FP64 grade).
+//
+// FP16 form (F16 = true): FP16 has three more significand bits than BF16 but
+// cannot hold a digit pre-scaled by 2^-7s (its range ends at 2^-24), so its
+// slices are the raw balanced base-128 digits, |d_s| <= 64 (exact in FP16).
+// S = 8 slices (56 bits) and the pairs with s + t <= S + 1 = 9: 36 slice-pair
+// products instead of 53.  Every level L = 2..9 keeps its own accumulator of
+// raw integer products, |d_s d_t| <= 2^12, exact in FP32 over K-chunks of 512
+// (8 pairs x 512 x 2^12 = 2^24); the epilogue adds levels 2..7 to an int64 of
+// 2^-49 units (shifted by 49 - 7L) and levels 8 and 9 to one float in 2^-56
+// units, joined as iacc + f 2^-7 before the scale 2^(e_i + f_j - 49).  The
+// error is the BF16 form's (CPU model: 1.43e-15 against 1.40e-15 of the row and
+// column maxima on the same operands).
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <climits>
 #include <cmath>
@@ -35,11 +48,16 @@
 namespace zolo {
 namespace {
 
-constexpr int kBeta = 6;
+constexpr int kBeta = 6;          // BF16 form: base-64 digits
 constexpr int kTileM = 128;
-constexpr int kBK = 64;            // one 128-byte swizzle row of BF16
-constexpr int kChunkK = 2048;      // exact-accumulation span of the level sums
-constexpr int kAcc = 8;            // TMEM accumulators: levels 2..8 exact, levels >= 9 merged
+constexpr int kBK = 64;            // one 128-byte swizzle row of 16-bit elements
+constexpr int kAcc = 8;            // TMEM accumulators (BF16: levels 2..8 exact, >= 9 merged;
+                                   // FP16: one per level 2..9)
+// digit width, exact-accumulation span of a level's sums, and the largest
+// 0-based level s + t kept (1-based S + 2 for BF16, S + 1 for FP16)
+template <bool F16> __host__ __device__ constexpr int digit_bits() { return F16 ? 7 : kBeta; }
+template <bool F16> __host__ __device__ constexpr int chunk_k() { return F16 ? 512 : 2048; }
+template <bool F16, int S> __host__ __device__ constexpr int max_level0() { return F16 ? S - 1 : S; }
 constexpr int kARing = 4;
 constexpr int kGroupM = 8;         // tile rows per CTA group (L2 reuse of the A slices)
 constexpr int kEpiWarps = 16;      // four per TMEM lane quarter, each owning a quarter of the columns
@@ -157,9 +175,9 @@ __global__ void col_exp_kernel(const double* __restrict__ X, int64_t ldx, int64_
   }
 }
 
-// N = round(x 2^(6S - e)) from the bit pattern (|x| < 2^(e-1), so |N| <= 2^(6S-1));
-// ties round away from zero.
-template <int S>
+// N = round(x 2^(bS - e)) from the bit pattern (|x| < 2^(e-1), so |N| <= 2^(bS-1));
+// ties round away from zero.  b = the digit width (6, or 7 for FP16).
+template <int S, int B = kBeta>
 __device__ __forceinline__ long long fixed_point(double x, int e) {
   const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
   const unsigned long long mag = bits & 0x7FFFFFFFFFFFFFFFull;
@@ -167,7 +185,7 @@ __device__ __forceinline__ long long fixed_point(double x, int e) {
   const int ef = (int)(mag >> 52);
   const unsigned long long M = (mag & ((1ull << 52) - 1)) | (ef ? (1ull << 52) : 0ull);
   const int E = ef ? ef - 1075 : -1074;          // |x| = M 2^E
-  const int k = E - e + 6 * S;                   // |x| < 2^(e-1) keeps k <= 6S - 54
+  const int k = E - e + B * S;                   // |x| < 2^(e-1) keeps k <= bS - 54
   unsigned long long F;
   if (k >= 0) F = k < 11 ? M << k : 0;
   else F = -k < 63 ? (M + (1ull << (-k - 1))) >> (-k) : 0;
@@ -178,17 +196,19 @@ __device__ __forceinline__ long long fixed_point(double x, int e) {
 // digits from the least significant one up; the leading digit takes what is
 // left, |d_1| <= 32 because |N| <= 2^(6S-1).  Each is exact in FP32 and BF16
 // (at most six significant bits).
-template <int S>
+template <int S, bool F16 = false>
 __device__ __forceinline__ void slice_values(double x, int ee, float* v) {
-  long long N = fixed_point<S>(x, ee);
+  constexpr int B = digit_bits<F16>();
+  long long N = fixed_point<S, B>(x, ee);
 #pragma unroll
   for (int s = S; s >= 2; --s) {
-    int d = (int)(N & 63);
-    d = d >= 32 ? d - 64 : d;
-    v[s - 1] = (float)d * __int_as_float((127 - kBeta * s) << 23);
-    N = (N - d) >> kBeta;
+    int d = (int)(N & ((1 << B) - 1));
+    d = d >= (1 << (B - 1)) ? d - (1 << B) : d;
+    // BF16: the digit pre-scaled by 2^-Bs; FP16: the raw digit (scaled in the epilogue)
+    v[s - 1] = F16 ? (float)d : (float)d * __int_as_float((127 - B * s) << 23);
+    N = (N - d) >> B;
   }
-  v[0] = (float)N * __int_as_float((127 - kBeta) << 23);
+  v[0] = F16 ? (float)N : (float)N * __int_as_float((127 - B) << 23);
 }
 
 // S slices of op(X), each rows_pad x K_pad BF16, K contiguous; batch entry b at
@@ -196,7 +216,7 @@ __device__ __forceinline__ void slice_values(double x, int ee, float* v) {
 // 32 x 64 tiles through shared memory: the read runs along X's contiguous
 // dimension, and each thread writes two neighbouring K entries per plane so
 // that a warp stores whole 128-byte lines.
-template <int S>
+template <int S, bool F16 = false>
 __global__ void __launch_bounds__(256)
 slice_kernel(const double* __restrict__ X, int64_t ldx, int64_t strideX, int trans,
              int rows, int K, const int* __restrict__ e_in,
@@ -236,15 +256,21 @@ slice_kernel(const double* __restrict__ X, int64_t ldx, int64_t strideX, int tra
       // element x 2^(esign ek[k]) against the row bound 2^(e_i - 1)
       const int ea = ekb ? eb[i] - esign * ekb[k] : eb[i];
       const int eb2 = ekb ? eb[i] - esign * ekb[k + 1] : eb[i];
-      slice_values<S>(tile[r][kl], ea, va);
-      slice_values<S>(tile[r][kl + 1], eb2, vb);
+      slice_values<S, F16>(tile[r][kl], ea, va);
+      slice_values<S, F16>(tile[r][kl + 1], eb2, vb);
     } else {
 #pragma unroll
       for (int s = 0; s < S; ++s) va[s] = vb[s] = 0.f;
     }
-    __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(ob + (size_t)i * K_pad + k);
+    if (F16) {   // the same 16-bit planes hold FP16 values
+      __half2* o = reinterpret_cast<__half2*>(ob + (size_t)i * K_pad + k);
 #pragma unroll
-    for (int s = 0; s < S; ++s) o[s * (plane / 2)] = __floats2bfloat162_rn(va[s], vb[s]);
+      for (int s = 0; s < S; ++s) o[s * (plane / 2)] = __floats2half2_rn(va[s], vb[s]);
+    } else {
+      __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(ob + (size_t)i * K_pad + k);
+#pragma unroll
+      for (int s = 0; s < S; ++s) o[s * (plane / 2)] = __floats2bfloat162_rn(va[s], vb[s]);
+    }
   }
 }
 
@@ -289,11 +315,12 @@ struct SmemLayout {
   static constexpr int kAlloc = kBytes + 1024;     // slack for 1024-byte alignment
 };
 
-template <int BN, int S>
+template <int BN, int S, bool F16 = false>
 __global__ void __launch_bounds__(kThreads, 1)
 split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                   const SplitEpi p) {
   using L = SmemLayout<BN, S>;
+  constexpr int kChunkK = chunk_k<F16>();
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sB = sm + L::kOffB;
@@ -383,7 +410,7 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     // and advanced by adding to their start-address field (address >> 4, 14
     // bits; shared addresses stay below 256 KB so no carry leaves the field),
     // and the slice-pair loops are unrolled.
-    const uint32_t idesc = tc::idesc_bf16_f32(kTileM, BN);
+    const uint32_t idesc = F16 ? tc::idesc_f16_f32(kTileM, BN) : tc::idesc_bf16_f32(kTileM, BN);
     const uint64_t adesc0 = tc::sdesc_k128(tc::smem_u32(sA));
     const uint64_t bdesc0 = tc::sdesc_k128(tc::smem_u32(sB));
     int kbg = 0, ia = 0;
@@ -410,10 +437,13 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
           ++ia;
           tc::tc_fence_after();
           const uint64_t ad = adesc0 + (uint64_t)((sa * L::kATile) >> 4);
+          constexpr int kTop = max_level0<F16, S>();   // largest s + t (0-based) kept
 #pragma unroll
-          for (int t = 0; t < (S - s + 1 < S ? S - s + 1 : S); ++t) {   // level (s+1)+(t+1) <= S+2
+          for (int t = 0; t < (kTop - s + 1 < S ? kTop - s + 1 : S); ++t) {
             const int lvl = s + t;                 // 0 -> level 2
-            const int acc = lvl < kAcc - 1 ? lvl : kAcc - 1;
+            // FP16: one accumulator per level (raw digits of different scales
+            // must not share one); BF16: levels >= 9 share the last
+            const int acc = F16 ? lvl : (lvl < kAcc - 1 ? lvl : kAcc - 1);
             const uint32_t d = tmem + acc * BN;
             const uint64_t bt = bd + (uint64_t)((t * L::kBTile) >> 4);
             const uint32_t first = (fresh >> acc) & 1u;
@@ -462,7 +492,18 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         for (int g = 0; g < HALF / 8; ++g) {
           float v[8];
           tc::tmem_ld8(tmem + lane_off + a * BN + half * HALF + g * 8, v);
-          if (a < kAcc - 1) {
+          if (F16) {
+            // raw integer level sums (|.| <= 2^24): levels 2..7 into 2^-49 units;
+            // levels 8 and 9 into one float in units of 2^-56 (level 9 times
+            // 2^-7, exact), whose rounding lies about 2^-56 below the leading level
+            const int L = a + 2;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              if (L <= 7) iacc[g * 8 + i] += (long long)__float2int_rn(v[i]) << (49 - 7 * L);
+              else if (L == 8) fm[g * 8 + i] += v[i];
+              else fm[g * 8 + i] += v[i] * 0x1p-7f;
+            }
+          } else if (a < kAcc - 1) {
             const int L = a + 2;
             // times 2^6L: an exact integer below 2^24
             const float up = __int_as_float((127 + kBeta * L) << 23);
@@ -495,7 +536,11 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
           if (row < (p.swap ? p.N : p.M) && col < (p.swap ? p.M : p.N)) {
             // one conversion; the power of two 2^(e_i + f_j - 48) goes into the
             // exponent field (FP64 arithmetic is scarce on this part)
-            double v = pow2_scale(fma((double)fm[j], 0x1p48, (double)iacc[j]), ei + __ldg(ebb + j) - 48);
+            double v;
+            if (F16)
+              v = pow2_scale(fma((double)fm[j], 0x1p-7, (double)iacc[j]), ei + __ldg(ebb + j) - 49);
+            else
+              v = pow2_scale(fma((double)fm[j], 0x1p48, (double)iacc[j]), ei + __ldg(ebb + j) - 48);
             if (al == -1.0) v = __longlong_as_double(__double_as_longlong(v) ^ (long long)0x8000000000000000ull);
             else if (al != 1.0) v *= al;
             if (first) {
@@ -541,22 +586,25 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// 2-D map over a (rows x K_pad) BF16 matrix, K contiguous, box 64 x box_rows, 128-byte swizzle
-bool make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t K_pad, int box_rows) {
+// 2-D map over a (rows x K_pad) BF16 or FP16 matrix, K contiguous, box 64 x box_rows,
+// 128-byte swizzle
+bool make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t K_pad, int box_rows,
+              bool f16) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return false;
   cuuint64_t dims[2] = {(cuuint64_t)K_pad, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)K_pad * 2};
   cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
   cuuint32_t es[2] = {1, 1};
-  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+  return enc(m, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+             const_cast<void*>(base), dims, strides, box, es,
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
-template <int S>
+template <int S, bool F16>
 cudaError_t slice_operand(const double* X, int64_t ldx, int64_t strideX, int trans, int rows, int K,
                           int batch, int* e, __nv_bfloat16* out, int rows_pad, int K_pad,
                           const int* ek, int esign, cudaStream_t st) {
@@ -571,12 +619,12 @@ cudaError_t slice_operand(const double* X, int64_t ldx, int64_t strideX, int tra
   }
   ProfScope ps(kProfSlice, st, 0.0, (8.0 + 2.0 * S) * batch * rows_pad * (double)K_pad);
   dim3 grid((unsigned)(K_pad / 64), (unsigned)(rows_pad / 32), batch);
-  slice_kernel<S><<<grid, dim3(32, 8), 0, st>>>(X, ldx, strideX, trans, rows, K, e, out, rows_pad,
-                                                K_pad, ek, esign);
+  slice_kernel<S, F16><<<grid, dim3(32, 8), 0, st>>>(X, ldx, strideX, trans, rows, K, e, out,
+                                                     rows_pad, K_pad, ek, esign);
   return cudaGetLastError();
 }
 
-template <int BN, int S>
+template <int BN, int S, bool F16>
 cudaError_t run_split(const GemmArgs& g, SplitWork& w, cudaStream_t st) {
   // orientation: put the larger output dimension on the 128-row tile side
   const bool swap = g.M < kTileM && g.N > g.M;
@@ -614,15 +662,15 @@ cudaError_t run_split(const GemmArgs& g, SplitWork& w, cudaStream_t st) {
         Xo, swap ? lda : ldb, swap ? sta : stb, swap ? ta : tb, swap ? M : N, K, ek, Kpad);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
-  if ((err = slice_operand<S>(Xa, lda, sta, ta, M, K, nb, ea, sa, Mpad, Kpad, ek, sign_a, st)) !=
-      cudaSuccess)
+  if ((err = slice_operand<S, F16>(Xa, lda, sta, ta, M, K, nb, ea, sa, Mpad, Kpad, ek, sign_a,
+                                   st)) != cudaSuccess)
     return err;
-  if ((err = slice_operand<S>(Xb, ldb, stb, tb, N, K, nb, eb, sb, Npad, Kpad, ek, -sign_a, st)) !=
-      cudaSuccess)
+  if ((err = slice_operand<S, F16>(Xb, ldb, stb, tb, N, K, nb, eb, sb, Npad, Kpad, ek, -sign_a,
+                                   st)) != cudaSuccess)
     return err;
   CUtensorMap mA, mB;
-  if (!make_map(&mA, sa, (int64_t)nb * S * Mpad, Kpad, kTileM) ||
-      !make_map(&mB, sb, (int64_t)nb * S * Npad, Kpad, BN))
+  if (!make_map(&mA, sa, (int64_t)nb * S * Mpad, Kpad, kTileM, F16) ||
+      !make_map(&mB, sb, (int64_t)nb * S * Npad, Kpad, BN, F16))
     return cudaErrorInvalidValue;
   SplitEpi p{};
   p.C = g.Cout; p.ldc = g.ldcout; p.strideC = g.strideCout;
@@ -635,7 +683,7 @@ cudaError_t run_split(const GemmArgs& g, SplitWork& w, cudaStream_t st) {
   p.stall = w.stall;
   p.stall_ns = w.stall_ns;
   using L = SmemLayout<BN, S>;
-  if ((err = smem_attr_once((const void*)split_gemm_kernel<BN, S>, L::kAlloc)) != cudaSuccess) {
+  if ((err = smem_attr_once((const void*)split_gemm_kernel<BN, S, F16>, L::kAlloc)) != cudaSuccess) {
     if (std::getenv("ZOLO_DEBUG"))
       std::fprintf(stderr, "zolo: cudaFuncSetAttribute(%d B): %s\n", L::kAlloc,
                    cudaGetErrorString(err));
@@ -643,11 +691,11 @@ cudaError_t run_split(const GemmArgs& g, SplitWork& w, cudaStream_t st) {
   }
   dim3 grid((unsigned)(Npad / BN), (unsigned)(Mpad / kTileM), g.reduce ? 1 : nb);
   ProfScope ps(kProfSplitGemm, st, gemm_flops(g), 0.0);
-  split_gemm_kernel<BN, S><<<grid, kThreads, L::kAlloc, st>>>(mA, mB, p);
+  split_gemm_kernel<BN, S, F16><<<grid, kThreads, L::kAlloc, st>>>(mA, mB, p);
   err = cudaGetLastError();
   if (err != cudaSuccess && std::getenv("ZOLO_DEBUG")) {
     cudaFuncAttributes fa{};
-    cudaFuncGetAttributes(&fa, split_gemm_kernel<BN, S>);
+    cudaFuncGetAttributes(&fa, split_gemm_kernel<BN, S, F16>);
     std::fprintf(stderr,
                  "zolo: split_gemm_kernel<%d,%d> launch (grid %u x %u x %u, %d threads, %d B smem): %s"
                  " [maxThreadsPerBlock %d, numRegs %d, localSizeBytes %zu, maxDynamicSmem %d]\n",
@@ -670,7 +718,8 @@ cudaError_t gemm_split(const GemmArgs& g, SplitWork& w, cudaStream_t st) {
   gs = (int)std::min<size_t>((size_t)gs, w.exp_elems / std::max<size_t>(rows, 1));
   if (gs < 1) return cudaErrorMemoryAllocation;
   auto run = [&](const GemmArgs& h) {
-    return w.slices_s == 9 ? run_split<64, 9>(h, w, st) : run_split<64, 8>(h, w, st);
+    if (w.fp16) return run_split<64, 8, true>(h, w, st);
+    return w.slices_s == 9 ? run_split<64, 9, false>(h, w, st) : run_split<64, 8, false>(h, w, st);
   };
   if (gs >= g.batch) return run(g);
   for (int b0 = 0; b0 < g.batch; b0 += gs) {
@@ -692,8 +741,9 @@ cudaError_t gemm_split(const GemmArgs& g, SplitWork& w, cudaStream_t st) {
 }
 
 void split_prepare() {
-  smem_attr_once((const void*)split_gemm_kernel<64, 8>, SmemLayout<64, 8>::kAlloc);
-  smem_attr_once((const void*)split_gemm_kernel<64, 9>, SmemLayout<64, 9>::kAlloc);
+  smem_attr_once((const void*)split_gemm_kernel<64, 8, false>, SmemLayout<64, 8>::kAlloc);
+  smem_attr_once((const void*)split_gemm_kernel<64, 9, false>, SmemLayout<64, 9>::kAlloc);
+  smem_attr_once((const void*)split_gemm_kernel<64, 8, true>, SmemLayout<64, 8>::kAlloc);
   encode_fn();
 }
 
@@ -719,7 +769,7 @@ double split_time_ratio(const GemmArgs& g, const SplitWork& w) {
     const double S = w.slices_s;
     const double bytes = g.batch * (8.0 + 2.0 * S) * (ra + rb) * kp +
                          (g.reduce ? 1 : g.batch) * 8.0 * g.M * (double)g.N * (g.beta != 0.0 ? 2 : 1);
-    const double pairs = S * (S + 1) / 2 + (S - 1);
+    const double pairs = w.fp16 ? S * (S + 1) / 2 : S * (S + 1) / 2 + (S - 1);
     const double tensor = pairs * 2.0 * ra * rb * kp * g.batch / 1.7e15;
     return (bytes / 6e12 + tensor) / (gemm_flops(g) / 1.2e12);
   }
@@ -731,7 +781,8 @@ double split_time_ratio(const GemmArgs& g, const SplitWork& w) {
   const double S = w.slices_s;
   const double slice_bytes = g.batch * (8.0 + 2.0 * S) * (ra + rb) * kp;
   const double out_bytes = (g.reduce ? 1 : g.batch) * 8.0 * g.M * (double)g.N * (g.beta != 0.0 ? 2 : 1);
-  const double pairs = S * (S + 1) / 2 + (S - 1);   // s + t <= S + 2
+  // slice pairs: s + t <= S + 2 (BF16), s + t <= S + 1 (FP16)
+  const double pairs = w.fp16 ? S * (S + 1) / 2 : S * (S + 1) / 2 + (S - 1);
   const double tensor = pairs * 2.0 * ra * rb * kp * g.batch / 0.7e15;
   const double tsplit = slice_bytes / 4e12 + out_bytes / 5e12 + tensor + 30e-6;
   return tsplit / t64;

@@ -201,5 +201,11 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
          ((uint32_t)(M >> 4) << 24);
 }
 
+// The same with A = B = FP16 (type code 0 in bits 7-9 and 10-12; both operands
+// of one kind::f16 MMA have the same type).
+__host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
 }  // namespace tc
 }  // namespace zolo

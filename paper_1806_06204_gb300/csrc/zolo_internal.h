@@ -171,6 +171,7 @@ struct SplitWork {
   size_t exp_elems;
   int* err;              // device error flag (bounded waits)
   int slices_s;          // S
+  int fp16 = 0;          // 1: FP16 raw base-128 digits (S = 8), else BF16 pre-scaled base-64 digits
   // test hook of the failure path: with stall = 1 the MMA issuer first waits,
   // for stall_ns, on an mbarrier that nothing arrives at, then takes the
   // bounded-wait error exit

@@ -114,3 +114,96 @@ def test_level_sums_are_exact_in_fp32_over_a_chunk():
     X = rng.standard_normal((5, 64)) * 10.0 ** rng.uniform(-20, 20, (5, 1))
     for d in digits(X, exponents(X, axis=1)[:, None], 9):
         assert max(abs(int(v)) for v in d.ravel()) <= 32
+
+
+# ---- the FP16 form: FP16's exponent range (down to 2^-24) cannot hold a digit
+# pre-scaled by 2^-7s, so its slices are the raw base-128 digits (|d| <= 64,
+# exact in FP16), every level L = s + t keeps its own accumulator, and the
+# scale 2^-7L is applied when the levels are joined: levels 2..7 as an int64 in
+# units of 2^-49, levels 8 and 9 into one FP32 in units of 2^-56.  S = 8 slices
+# (56 bits), levels <= S + 1 (36 slice pairs), K-chunks of 512.
+
+def digits_base(X, e, S, beta):
+    N = np.vectorize(int, otypes=[object])(np.rint(np.ldexp(X, (beta * S - e))))
+    half, full = 2 ** (beta - 1), 2 ** beta
+    out = []
+    for _ in range(S - 1):
+        d = np.vectorize(lambda v: ((v + half) % full) - half, otypes=[object])(N)
+        out.append(d)
+        N = (N - d) // full
+    out.append(N)
+    return out[::-1]
+
+
+def split_product_fp16(A, B, S=8, max_level=9, chunk=512):
+    """The FP16 form's arithmetic: per-chunk exact level sums, joined as the kernel
+    joins them (levels 2..7 in an int64 of 2^-49 units, 8 and 9 in one FP32 of
+    2^-56 units, accumulated over the chunks in FP32)."""
+    beta = 7
+    ea = exponents(A, axis=1)
+    eb = exponents(B, axis=0)
+    da = digits_base(A, ea[:, None], S, beta)
+    db = digits_base(B, eb[None, :], S, beta)
+    M, N, K = A.shape[0], B.shape[1], A.shape[1]
+    iacc = np.zeros((M, N), dtype=object)
+    fm = np.zeros((M, N), dtype=np.float32)
+    for k0 in range(0, K, chunk):
+        ks = slice(k0, min(K, k0 + chunk))
+        for L in range(2, max_level + 1):
+            lv = np.zeros((M, N), dtype=object)
+            for s in range(1, S + 1):
+                t = L - s
+                if 1 <= t <= S:
+                    lv = lv + da[s - 1][:, ks].dot(db[t - 1][ks, :])
+            # the accumulator holds an integer: exact in FP32 while |lv| <= 2^24
+            assert max(abs(int(v)) for v in lv.ravel()) <= 2 ** 24
+            if L <= 7:
+                iacc = iacc + lv * (2 ** (49 - 7 * L))
+            else:   # the accumulator's FP32 integer, times 2^-7 for level 9, added in FP32
+                v = np.vectorize(float)(lv).astype(np.float32)
+                fm = (fm + (v if L == 8 else v * np.float32(2.0 ** -7))).astype(np.float32)
+    assert max(abs(int(v)) for v in iacc.ravel()) < 2 ** 63
+    C = np.empty((M, N))
+    for i in range(M):
+        for j in range(N):
+            v = float(iacc[i, j]) + float(fm[i, j]) * 2.0 ** -7
+            C[i, j] = math.ldexp(v, int(ea[i] + eb[j]) - 49)
+    return C
+
+
+def test_fp16_form_is_fp64_grade(operands):
+    A, B = operands
+    K = A.shape[1]
+    C = split_product_fp16(A, B)
+    ref = exact_product(A, B)
+    scale = np.max(np.abs(A), axis=1)[:, None] * np.max(np.abs(B), axis=0)[None, :]
+    err = np.max(np.abs(C - ref) / scale)
+    # same grade as the BF16 form's bound (8 sqrt(K) 2^-54)
+    assert err <= 8 * math.sqrt(K) * 2.0 ** -54
+    assert err <= 2e-16 * math.sqrt(K)
+
+
+def test_fp16_form_level_sums_exact_over_a_512_chunk():
+    # |d| <= 64: a level of p <= 8 pairs over 512 terms stays within 2^24
+    for level in range(2, 10):
+        p = min(level - 1, 8, 17 - level)
+        assert p * 512 * 64 * 64 <= 2 ** 24
+    rng = np.random.default_rng(14)
+    X = rng.standard_normal((5, 64)) * 10.0 ** rng.uniform(-20, 20, (5, 1))
+    for d in digits_base(X, exponents(X, axis=1)[:, None], 8, 7):
+        assert max(abs(int(v)) for v in d.ravel()) <= 64
+    # the worst case of the model's own accumulators (checked inside) with operands
+    # at the digit bound over a whole chunk
+    A = np.full((2, 512), 0.4999)
+    B = np.full((512, 2), -0.4999)
+    C = split_product_fp16(A, B)
+    assert abs(C[0, 0] - exact_product(A, B)[0, 0]) <= 512 * 2.0 ** -52
+
+
+def test_fp16_form_without_level_9_is_worse(operands):
+    A, B = operands
+    ref = exact_product(A, B)
+    scale = np.max(np.abs(A), axis=1)[:, None] * np.max(np.abs(B), axis=0)[None, :]
+    keep = np.max(np.abs(split_product_fp16(A, B, max_level=9) - ref) / scale)
+    drop = np.max(np.abs(split_product_fp16(A, B, max_level=8) - ref) / scale)
+    assert drop > 4 * keep
