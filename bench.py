@@ -388,14 +388,15 @@ def roofline(kstats, step_ms, model_flops=None, split_pairs=SPLIT_PAIRS):
     return roof
 
 
-def batch_arm(args, w, h, mats, As, Qps, Hs, split, steps, warmup, local, dist):
+def batch_arm(args, w, h, mats, As, Qps, Hs, split, steps, warmup, local, dist, slices=None):
     """One precision of the batch: warm-up, K timed zolo_pd_batched calls (CUDA
     events on the calling stream, barrier and synchronise on both sides), then
     one more call with per-launch events for the kernel classes, and the
     accuracy of every result."""
     import torch
     from paper_1806_06204_gb300 import binding as zb
-    sp = zb.ZOLO_SPLIT_FP16 if args.slices == "fp16" else zb.ZOLO_SPLIT_BF16
+    slices = slices or args.slices
+    sp = zb.ZOLO_SPLIT_FP16 if slices == "fp16" else zb.ZOLO_SPLIT_BF16
     os_ = [zb.opts(beta=float(sm.sigma[-1]), alpha=1.0, r=0,
                    prec=sp if split else zb.ZOLO_FP64, ns_steps=1 if split else 0,
                    chol_form=args.chol_form)
@@ -452,7 +453,7 @@ def batch_arm(args, w, h, mats, As, Qps, Hs, split, steps, warmup, local, dist):
     kstats = zb.profile_read()
     zb.profile(False)
     prof_ms = e2.elapsed_time(e3)
-    roof = roofline(kstats, prof_ms, flops, split_pairs=SPLIT_PAIRS_OF[args.slices])
+    roof = roofline(kstats, prof_ms, flops, split_pairs=SPLIT_PAIRS_OF[slices])
     roof["measured"] = ("one extra call after the timed steps with the batch's lanes "
                         "serialised and every launch bracketed by CUDA events (no graph replay): "
                         "each launch timed alone on the GPU")
@@ -480,7 +481,11 @@ def run_batch(args, w, rank, world, dist, local):
     import torch
     from paper_1806_06204_gb300 import binding as zb, synth
     prec = args.prec if args.prec != "auto" else "both"
+    if args.count:   # the first `count` matrices of the same seeded batch (for profiling)
+        w = dict(w, count=args.count)
     mats = synth.batch(w["count"], seed=4000 + 100000 * rank)
+    if args.count:
+        mats = mats[:args.count]
     As = [torch.from_numpy(sm.A).cuda() for sm in mats]
     Qps = [zb.empty_colmajor(a.shape[0], a.shape[1]) for a in As]
     Hs = [zb.empty_colmajor(a.shape[1], a.shape[1]) for a in As]
@@ -488,11 +493,16 @@ def run_batch(args, w, rank, world, dist, local):
     head_split = prec in ("split", "both")
     arm = batch_arm(args, w, h, mats, As, Qps, Hs, head_split, args.steps, args.warmup, local,
                     dist)
-    fp64 = None
+    fp64 = other = None
     if prec == "both":
         fs = args.fp64_steps if args.fp64_steps is not None else max(1, min(args.steps, 5))
         fw = args.fp64_warmup if args.fp64_warmup is not None else min(args.warmup, 3)
         fp64 = batch_arm(args, w, h, mats, As, Qps, Hs, False, fs, fw, local, dist)
+        if not args.no_other_slices:
+            # the other slice format on the same matrices, for comparison
+            oth = "fp16" if args.slices == "bf16" else "bf16"
+            other = batch_arm(args, w, h, mats, As, Qps, Hs, True, fs, fw, local, dist, slices=oth)
+            other["slices"] = oth
     value = world * w["count"] / (arm["ms_step"] / 1000.0)
     os_ = arm["os"]
 
@@ -571,8 +581,21 @@ def run_batch(args, w, rank, world, dist, local):
                             "kernel_ms": {k: round(v["ms"], 3) for k, v in fp64["kstats"].items()
                                           if v["launches"]},
                             "clocks": fp64["clocks"]}
+        if other is not None:
+            ov = world * w["count"] / (other["ms_step"] / 1000.0)
+            line[other["slices"] + "_slices"] = {
+                "value": ov, "unit": "matrices/s", "dtype": SLICE_DTYPE[other["slices"]],
+                "ms_per_step": other["ms_step"], "steps": other["steps"],
+                "warmup": other["warmup"],
+                "split_over_fp64": ov / line["fp64_value"] if fp64 is not None else None,
+                "eff_tflops": world * other["flops"] / (other["ms_step"] / 1000.0) / 1e12,
+                "accuracy": other["acc"], "roofline": other["roof"],
+                "gpu_launches": other["launches"],
+                "kernel_ms": {k: round(v["ms"], 3) for k, v in other["kstats"].items()
+                              if v["launches"]},
+                "clocks": other["clocks"]}
         print(json.dumps(line), flush=True)
-        bad = [a for a in (arm, fp64) if a is not None and not a["acc"]["bar_met"]]
+        bad = [a for a in (arm, fp64, other) if a is not None and not a["acc"]["bar_met"]]
         if bad:
             print("accuracy bar (1e-13) not met", file=sys.stderr)
             h.close()
@@ -594,6 +617,10 @@ def main():
     ap.add_argument("--slices", default="bf16", choices=["bf16", "fp16"],
                     help="split precision's slices: nine BF16 six-bit slices (53 slice-pair "
                          "products) or eight FP16 seven-bit slices (36)")
+    ap.add_argument("--count", type=int, default=None,
+                    help="batch workload: only its first COUNT matrices (for profiler captures)")
+    ap.add_argument("--no-other-slices", action="store_true",
+                    help="with --prec both: skip the arm of the other slice format")
     ap.add_argument("--fp64-steps", type=int, default=None,
                     help="timed steps of the FP64 arm with --prec both (default min(steps, 5))")
     ap.add_argument("--fp64-warmup", type=int, default=None,

@@ -1,5 +1,6 @@
 """Time one building-block GEMM of libzolo: C = op(A) op(B) in FP64 (DFMA) or
-split precision (nine BF16 slices on the tensor cores), through zolo_dgemm.
+split precision (nine BF16 or eight FP16 slices on the tensor cores), through
+zolo_dgemm.
 
     python -m paper_1806_06204_gb300.profile_gemm --m 4096 --n 4096 --k 4096 --prec split
 
@@ -8,7 +9,7 @@ CUDA events on the current stream.  `--tune-cache F`: the FP64 kernel comes
 from the tuning file F when it holds this shape; otherwise the warm-up call
 measures the candidates (zolo_autotune) and F is written with the choice.  Prints one JSON line: milliseconds per
 call, FP64-equivalent TFLOP/s (2MNK per call), and for the split path the BF16
-tensor TFLOP/s actually issued (53 slice-pair products).  Also the launch
+tensor TFLOP/s actually issued (53 or 36 slice-pair products).  Also the launch
 target for kernel profilers: each call is one row-exponent + slicing pass per
 operand and one GEMM kernel (split), or one GEMM kernel (FP64).
 """
@@ -26,6 +27,7 @@ def main():
     ap.add_argument("--n", type=int, default=4096)
     ap.add_argument("--k", type=int, default=4096)
     ap.add_argument("--prec", choices=["fp64", "split"], default="split")
+    ap.add_argument("--slices", choices=["bf16", "fp16"], default="bf16")
     ap.add_argument("--transA", action="store_true")
     ap.add_argument("--transB", action="store_true")
     ap.add_argument("--reps", type=int, default=3)
@@ -40,7 +42,8 @@ def main():
     A = torch.randn(shape_a[::-1], dtype=torch.float64, device="cuda", generator=g).t()
     B = torch.randn(shape_b[::-1], dtype=torch.float64, device="cuda", generator=g).t()
     C = zb.empty_colmajor(args.m, args.n)
-    prec = zb.ZOLO_SPLIT_BF16 if args.prec == "split" else zb.ZOLO_FP64
+    prec = ((zb.ZOLO_SPLIT_FP16 if args.slices == "fp16" else zb.ZOLO_SPLIT_BF16)
+            if args.prec == "split" else zb.ZOLO_FP64)
     h = zb.Handle(torch.cuda.current_device())
     if args.tune_cache:
         import os
@@ -49,7 +52,8 @@ def main():
         zb.autotune(h, True)
 
     def call():
-        zb.zolo_dgemm(h, A, B, C, transA=args.transA, transB=args.transB, prec=prec, slices=9)
+        zb.zolo_dgemm(h, A, B, C, transA=args.transA, transB=args.transB, prec=prec,
+                      slices=8 if args.slices == "fp16" else 9)
 
     call()
     torch.cuda.synchronize()
@@ -75,7 +79,10 @@ def main():
     out = {"m": args.m, "n": args.n, "k": args.k, "prec": args.prec, "ms_per_call": ms,
            "fp64_equiv_tflops": flops / ms / 1e9}
     if args.prec == "split":
-        out["bf16_issued_tflops"] = 53 * flops / ms / 1e9
+        # slice-pair products issued: 53 (nine BF16 slices), 36 (eight FP16 slices)
+        pairs = 36 if args.slices == "fp16" else 53
+        out["slices"] = args.slices
+        out["tensor_issued_tflops"] = pairs * flops / ms / 1e9
     if kernel:
         out["tuned_kernel"] = kernel
     ref = A @ B if not (args.transA or args.transB) else None
