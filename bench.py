@@ -490,6 +490,8 @@ def run_batch(args, w, rank, world, dist, local):
     Qps = [zb.empty_colmajor(a.shape[0], a.shape[1]) for a in As]
     Hs = [zb.empty_colmajor(a.shape[1], a.shape[1]) for a in As]
     h = zb.Handle(local)
+    if args.no_graph:
+        zb.batch_graphs(h, False)
     head_split = prec in ("split", "both")
     arm = batch_arm(args, w, h, mats, As, Qps, Hs, head_split, args.steps, args.warmup, local,
                     dist)
@@ -617,6 +619,9 @@ def main():
     ap.add_argument("--slices", default="bf16", choices=["bf16", "fp16"],
                     help="split precision's slices: nine BF16 six-bit slices (53 slice-pair "
                          "products) or eight FP16 seven-bit slices (36)")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="batch workload: queue the lanes directly every step instead of replaying "
+                         "a recorded CUDA graph (for kernel profilers)")
     ap.add_argument("--count", type=int, default=None,
                     help="batch workload: only its first COUNT matrices (for profiler captures)")
     ap.add_argument("--no-other-slices", action="store_true",

@@ -259,6 +259,13 @@ int zolo_pd_batched(zolo_handle_t handle, int count, const double* const* A, con
                     double* const* H, const int64_t* ldh, const zolo_opts_t* opts,
                     zolo_info_t* info, void* stream);
 
+/* zolo_batch_graphs(h, 0): zolo_pd_batched on this handle queues its lanes'
+   work directly on every call instead of recording it as a CUDA graph and
+   replaying it (for tools that cannot follow a stream capture, such as kernel
+   profilers; the same kernels run, one launch each).  1 (the default) records
+   and replays.  Returns 0, -1 (NULL handle) or -2 (enable not 0/1). */
+int zolo_batch_graphs(zolo_handle_t handle, int enable);
+
 /* As zolo_pd / zolo_svd, but every matrix pointer is a HOST pointer: the call
    copies A to the device, computes, and copies the results back (pageable or
    pinned host memory; pinned is faster).  Device buffers come from the

@@ -98,6 +98,8 @@ def _load():
     lib.zolo_shift_range.restype = I
     lib.zolo_pd_sharded.argtypes = pd_args + [I, I, SUM_FN, P]
     lib.zolo_pd_sharded.restype = I
+    lib.zolo_batch_graphs.argtypes = [P, I]
+    lib.zolo_batch_graphs.restype = I
     lib.zolo_debug_stall.argtypes = [P, I, I64]
     lib.zolo_debug_stall.restype = I
     lib.zolo_autotune.argtypes = [P, I]
@@ -124,7 +126,7 @@ EXPORTED = ["zolo_opts_default", "zolo_create", "zolo_destroy", "zolo_coefficien
             "zolo_dgemm", "zolo_dgemm_noalloc", "zolo_pd_batched", "zolo_tuned_r",
             "zolo_tune_save", "zolo_tune_load", "zolo_autotune",
             "zolo_workspace_bytes", "zolo_debug_stall", "zolo_shift_range",
-            "zolo_pd_sharded", "zolo_pd_async"]
+            "zolo_pd_sharded", "zolo_pd_async", "zolo_batch_graphs"]
 
 
 def kernel_launches() -> int:
@@ -225,6 +227,13 @@ def autotune(handle, enable: bool) -> None:
 
 ZOLO_STALL_SPLIT_GEMM = 1
 ZOLO_STALL_JACOBI32 = 2
+
+
+def batch_graphs(handle, enable: bool) -> None:
+    """zolo_pd_batched: record and replay a CUDA graph (True, default) or queue directly."""
+    e = LIB.zolo_batch_graphs(handle.ptr, int(enable))
+    if e:
+        raise ZoloError(e, "zolo_batch_graphs")
 
 
 def debug_stall(handle, where: int, ns: int = 0) -> None:

@@ -107,6 +107,7 @@ struct zolo_handle_s {
   cudaEvent_t ph_ev[kPhaseEvents] = {};   // phase boundaries of one call
   AsyncSlot* async = nullptr;              // pinned ring of zolo_pd_async records
   int async_next = 0;
+  bool batch_graphs = true;                // zolo_pd_batched records and replays a graph
 };
 
 namespace {
@@ -1696,7 +1697,7 @@ int zolo_pd_batched(zolo_handle_t h, int count, const double* const* A, const in
   CK(cudaStreamWaitEvent(cap, h->joined, 0));
   // with per-kernel profiling on, the work is queued directly (events cannot
   // bracket the nodes of a graph)
-  const bool use_graph = !profiling_enabled();
+  const bool use_graph = !profiling_enabled() && h->batch_graphs;
   if (!use_graph) exec = nullptr;
   uint64_t graph_launches = 0;
   for (BatchGraph& g : h->graphs)
@@ -1783,6 +1784,13 @@ int zolo_pd_batched(zolo_handle_t h, int count, const double* const* A, const in
     for (int i = 0; i < count; ++i) info[i].ms = ms;
   }
   return worst;
+}
+
+int zolo_batch_graphs(zolo_handle_t h, int enable) {
+  if (!h) return -1;
+  if (enable != 0 && enable != 1) return -2;
+  h->batch_graphs = enable != 0;
+  return 0;
 }
 
 int zolo_debug_stall(zolo_handle_t h, int where, int64_t ns) {

@@ -340,28 +340,43 @@ qr_panel_smem_kernel(double* W, int64_t strideW, int64_t ldw, int64_t m, int64_t
     for (int64_t r = (r0 > c + 1 ? r0 : c + 1) + tid; r < r1; r += kT) col[r - lo] *= scal;
     if (tid == 0 && c >= lo && c < hi) col[c - lo] = s_beta;
     __syncthreads();
-    // ---- 3. partial dots of v with the later panel columns and the earlier reflectors
-    double acc[NB];
+    // ---- 3. dots of v with the other panel columns (the later ones for the
+    //         update, the earlier reflectors for T): warp w takes the four columns
+    //         4w..4w+3 over all my rows, lanes striding the rows, so each dot is
+    //         reduced over 32 lanes (a four-value reduce-scatter, six adds a
+    //         lane) instead of over every thread of the CTA
+    static_assert(NB == 4 * kWarps, "four dot products per warp");
+    {
+      double a4[4] = {0.0, 0.0, 0.0, 0.0};
+      const int q0 = 4 * warp;
+      for (int64_t r = r0 + lane; r < r1; r += 32) {
+        const double v = (r == c) ? 1.0 : col[r - lo];
 #pragma unroll
-    for (int q = 0; q < NB; ++q) acc[q] = 0.0;
-    for (int64_t r = r0 + tid; r < r1; r += kT) {
-      const double v = (r == c) ? 1.0 : col[r - lo];
-#pragma unroll
-      for (int q = 0; q < NB; ++q) {
-        if (q < nbp && q != i) {
-          // earlier reflector q: support rows [c0+q, m+c0+q]; r >= c > c0+q
-          const double o = (q > i || r <= m + c0 + q) ? Ws[q * Rs + (r - lo)] : 0.0;
-          acc[q] = fma(v, o, acc[q]);
+        for (int k = 0; k < 4; ++k) {
+          const int q = q0 + k;
+          if (q < nbp && q != i) {
+            // earlier reflector q: support rows [c0+q, m+c0+q]; r >= c > c0+q
+            const double o = (q > i || r <= m + c0 + q) ? Ws[q * Rs + (r - lo)] : 0.0;
+            a4[k] = fma(v, o, a4[k]);
+          }
         }
       }
-    }
-    static_assert(NB == 32, "one dot product per lane");
-    red[warp][lane] = warp_reduce_scatter32(acc, lane);
-    __syncthreads();
-    if (tid < NB) {
-      double t = 0.0;
-      for (int w = 0; w < kWarps; ++w) t += red[w][tid];
-      part[buf][tid] = t;
+      // lanes with bit 16 keep values 2, 3 and send 0, 1 (and the reverse), then
+      // bit 8 halves again; three butterflies finish the remaining value
+      const bool up16 = (lane & 16) != 0, up8 = (lane & 8) != 0;
+      const double k0 = up16 ? a4[2] : a4[0], k1 = up16 ? a4[3] : a4[1];
+      const double s0 = up16 ? a4[0] : a4[2], s1 = up16 ? a4[1] : a4[3];
+      const double b0 = k0 + __shfl_xor_sync(0xffffffffu, s0, 16);
+      const double b1 = k1 + __shfl_xor_sync(0xffffffffu, s1, 16);
+      double t = (up8 ? b1 : b0) + __shfl_xor_sync(0xffffffffu, up8 ? b0 : b1, 8);
+      t += __shfl_xor_sync(0xffffffffu, t, 4);
+      t += __shfl_xor_sync(0xffffffffu, t, 2);
+      t += __shfl_xor_sync(0xffffffffu, t, 1);
+      // lane 8 (2 * up16 + up8) holds column q0 + that index's dot
+      if ((lane & 7) == 0) {
+        const int q = q0 + 2 * (up16 ? 1 : 0) + (up8 ? 1 : 0);
+        part[buf][q] = (q < nbp && q != i) ? t : 0.0;
+      }
     }
     cluster.sync();
     if (tid < NB) {

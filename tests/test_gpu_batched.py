@@ -168,3 +168,25 @@ def test_batched_empty_and_bad_arguments(zb, handle):
     o = zb.opts(beta=0.05, alpha=sm.sigma.max(), posteriori=True)
     _, _, infos, st = zb.zolo_pd_batched(handle, [dev(sm.A)], [o], check=False)
     assert st == -10 and infos[0].status == -10
+
+
+def test_batched_without_graph_equals_graph_replay(zb):
+    # zolo_batch_graphs(h, 0): the lanes' work is queued directly (for profilers);
+    # the same kernels give the same bits as the recorded graph's replay
+    h = zb.Handle(0)
+    try:
+        mats = _case([(160, 160), (96, 64), (300, 200)], [1e7, 1e3, 1e11], 700)
+        As = [dev(sm.A) for sm in mats]
+        os = [zb.opts(beta=0.5 * sm.sigma.min(), alpha=sm.sigma.max(),
+                      prec=p) for sm, p in zip(mats, (0, 1, 2))]
+        Q1, H1, _, st = zb.zolo_pd_batched(h, As, os)
+        Q1, H1 = zb.zolo_pd_batched(h, As, os, Qps=Q1, Hs=H1)[:2]   # replayed
+        assert st == 0
+        zb.batch_graphs(h, False)
+        Q2, H2, _, st2 = zb.zolo_pd_batched(h, As, os)
+        assert st2 == 0
+        for a, b, c, d in zip(Q1, Q2, H1, H2):
+            assert np.array_equal(a.cpu().numpy(), b.cpu().numpy())
+            assert np.array_equal(c.cpu().numpy(), d.cpu().numpy())
+    finally:
+        h.close()
