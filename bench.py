@@ -335,6 +335,17 @@ SPLIT_PAIRS_OF = {"bf16": 53, "fp16": 36}
 SLICE_DTYPE = {"bf16": "bf16x9-slices->f64", "fp16": "fp16x8-slices->f64"}
 
 
+# DRAM bytes per algorithmic byte of a kernel class, from an ncu capture of that
+# class (dram__bytes_read.sum + dram__bytes_write.sum over the bytes its launches
+# state); bench.py scales it by the bytes its own launches state.  Set to None
+# when the kernel changes.
+TRAFFIC_PER_STATED_BYTE = {
+    # qr_panel_smem_kernel, 20 launches at n = 960, r = 5: 1.336 MB read, 0
+    # written, of 2.54 MB stated (profiles/traffic_batch4_split.md)
+    "qr_panel": 0.526,
+}
+
+
 def roofline(kstats, step_ms, model_flops=None, split_pairs=SPLIT_PAIRS):
     """Roofline entry of the dominant kernel class (by device time in one step).
 
@@ -382,6 +393,13 @@ def roofline(kstats, step_ms, model_flops=None, split_pairs=SPLIT_PAIRS):
         gbs = dom["bytes"] / sec / 1e9
         roof = {"bound": "hbm", "kernel": dom_name, "achieved": gbs, "peak": peak, "unit": "GB/s",
                 "frac": gbs / peak, "traffic": None, "work_basis": "bytes stated by the launches"}
+    ratio = TRAFFIC_PER_STATED_BYTE.get(dom_name)
+    if ratio is not None and dom["bytes"] > 0:
+        roof["traffic"] = ratio * dom["bytes"] / dom["launches"]
+        roof["traffic_source"] = ("DRAM bytes per launch: ncu capture of the class "
+                                  "(profiles/traffic_batch4_split.md) scaled by the algorithmic "
+                                  "bytes these launches state")
+        roof["algorithmic_bytes_per_launch"] = dom["bytes"] / dom["launches"]
     roof["launches"] = dom["launches"]
     roof["avg_launch_ms"] = dom["ms"] / dom["launches"]
     roof["share_of_step"] = dom["ms"] / step_ms

@@ -64,3 +64,12 @@ def test_oracle_sample_times_two_sizes_and_scales_by_the_model():
     v, spent, desc = bench.oracle_sample(w)
     assert v > 0 and spent > 0
     assert "256x96" not in desc and "96x96" in desc and "64x64" in desc
+
+
+def test_roofline_traffic_scales_the_captured_ratio():
+    kstats = {"qr_panel": {"launches": 4, "ms": 8.0, "flops": 4e9, "bytes": 8e6},
+              "gemm_split": {"launches": 4, "ms": 2.0, "flops": 1e10, "bytes": 0.0}}
+    roof = bench.roofline(kstats, 12.0, model_flops=1e10)
+    assert roof["kernel"] == "qr_panel"
+    assert roof["traffic"] == pytest.approx(bench.TRAFFIC_PER_STATED_BYTE["qr_panel"] * 2e6)
+    assert roof["algorithmic_bytes_per_launch"] == pytest.approx(2e6)
