@@ -28,6 +28,7 @@ chol_diag_kernel(double* Z, int64_t strideZ, int64_t n, int64_t k0, int nbk, dou
   // kept transposed in the strictly lower part, its diagonal in Dinv.
   __shared__ double S[NB][NB + 1];
   __shared__ double Dinv[NB];
+  __shared__ double s_rd;
   __shared__ int s_fail;
   double* Zj = Z + blockIdx.x * strideZ;
   double* Ij = Rinv + blockIdx.x * strideRinv + (k0 / NB) * (int64_t)(NB * NB);
@@ -38,19 +39,25 @@ chol_diag_kernel(double* Z, int64_t strideZ, int64_t n, int64_t k0, int nbk, dou
     S[i][k] = (i <= k && k < nbk) ? Zj[(k0 + i) + (k0 + k) * n] : 0.0;
   }
   __syncthreads();
+  // FP64 division is a long dependent sequence on this part: each pivot's
+  // reciprocal is formed once, by the thread that takes the square root, and the
+  // row is scaled by multiplication (and the inverse below reuses it)
   for (int j = 0; j < nbk; ++j) {
     if (tid == 0) {
       const double d = S[j][j];
+      double sd = 1.0;
       if (!(d > 0.0) || !isfinite(d)) {
         s_fail = 1;
-        S[j][j] = 1.0;
       } else {
-        S[j][j] = sqrt(d);
+        sd = sqrt(d);
       }
+      S[j][j] = sd;
+      s_rd = 1.0 / sd;
+      Dinv[j] = s_rd;
     }
     __syncthreads();
-    const double djj = S[j][j];
-    for (int k = j + 1 + tid; k < nbk; k += kDiagThreads) S[j][k] /= djj;
+    const double rjj = s_rd;
+    for (int k = j + 1 + tid; k < nbk; k += kDiagThreads) S[j][k] *= rjj;
     __syncthreads();
     for (int e = tid; e < nbk * nbk; e += kDiagThreads) {
       const int i = e % nbk, k = e / nbk;
@@ -58,16 +65,24 @@ chol_diag_kernel(double* Z, int64_t strideZ, int64_t n, int64_t k0, int nbk, dou
     }
     __syncthreads();
   }
-  // inverse of the upper-triangular block, column k by thread k:
+  // inverse of the upper-triangular block, column k by the four threads
+  // 4k..4k+3 (each sums every fourth term, a shuffle joins them):
   // Inv(k,k) = 1/R(k,k);  Inv(i,k) = -sum_{l=i+1..k} R(i,l) Inv(l,k) / R(i,i)
-  if (tid < nbk) {
-    const int k = tid;
-    const double dk = 1.0 / S[k][k];
-    Dinv[k] = dk;
-    for (int i = k - 1; i >= 0; --i) {
-      double s = S[i][k] * dk;
-      for (int l = i + 1; l < k; ++l) s = fma(S[i][l], S[k][l], s);
-      S[k][i] = -s / S[i][i];
+  static_assert(kDiagThreads >= 4 * NB, "four threads per column of the inverse");
+  {
+    const int k = tid >> 2, sub = tid & 3;
+    const unsigned grp = 0xFu << (tid & 28);   // the four lanes of this column
+    if (k < nbk) {
+      const double dk = Dinv[k];
+      for (int i = k - 1; i >= 0; --i) {
+        double s = 0.0;
+        for (int l = i + 1 + sub; l < k; l += 4) s = fma(S[i][l], S[k][l], s);
+        s += __shfl_xor_sync(grp, s, 1);
+        s += __shfl_xor_sync(grp, s, 2);
+        s = fma(S[i][k], dk, s);
+        if (sub == 0) S[k][i] = -s * Dinv[i];
+        __syncwarp(grp);   // the next row's terms read this entry
+      }
     }
   }
   __syncthreads();

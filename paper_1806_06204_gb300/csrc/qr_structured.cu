@@ -257,6 +257,21 @@ tb_merge_kernel(const double* __restrict__ G, int64_t strideG, double* __restric
 // of V is needed.  Rows per CTA: ceil((m + NB) / CG) <= kSmemPanelRows.
 constexpr int kSmemPanelRows = 768;
 
+// A one-CTA "cluster" needs no cluster barrier and no distributed shared memory:
+// the panel kernels of one CTA per shift (the batched call's common case) use a
+// CTA barrier and their own partial sums.
+template <int CG>
+__device__ __forceinline__ void panel_sync(cooperative_groups::cluster_group& cluster) {
+  if constexpr (CG == 1) __syncthreads();
+  else cluster.sync();
+}
+template <int CG>
+__device__ __forceinline__ const double* panel_part(cooperative_groups::cluster_group& cluster,
+                                                    double* p, int rank) {
+  if constexpr (CG == 1) return p;
+  else return cluster.map_shared_rank(p, rank);
+}
+
 template <int NB, int CG>
 __global__ void __cluster_dims__(CG, 1, 1) __launch_bounds__(256)
 qr_panel_smem_kernel(double* W, int64_t strideW, int64_t ldw, int64_t m, int64_t c0, int nbp,
@@ -314,11 +329,11 @@ qr_panel_smem_kernel(double* W, int64_t strideW, int64_t ldw, int64_t m, int64_t
       part[buf][NB] = t;
       part[buf][NB + 1] = (c >= lo && c < hi) ? col[c - lo] : 0.0;
     }
-    cluster.sync();
+    panel_sync<CG>(cluster);
     if (tid == 0) {
       double sum = 0.0, alpha = 0.0;
       for (int rk = 0; rk < CG; ++rk) {
-        const double* rp = cluster.map_shared_rank(&part[buf][0], rk);
+        const double* rp = panel_part<CG>(cluster, &part[buf][0], rk);
         sum += rp[NB];
         alpha += rp[NB + 1];
       }
@@ -378,10 +393,10 @@ qr_panel_smem_kernel(double* W, int64_t strideW, int64_t ldw, int64_t m, int64_t
         part[buf][q] = (q < nbp && q != i) ? t : 0.0;
       }
     }
-    cluster.sync();
+    panel_sync<CG>(cluster);
     if (tid < NB) {
       double t = 0.0;
-      for (int rk = 0; rk < CG; ++rk) t += cluster.map_shared_rank(&part[buf][0], rk)[tid];
+      for (int rk = 0; rk < CG; ++rk) t += panel_part<CG>(cluster, &part[buf][0], rk)[tid];
       dots[tid] = t;
     }
     __syncthreads();
@@ -418,7 +433,7 @@ qr_panel_smem_kernel(double* W, int64_t strideW, int64_t ldw, int64_t m, int64_t
   }
   if (rank == 0)
     for (int e = tid; e < NB * NB; e += kT) Tp[e] = Ts[e % NB][e / NB];
-  cluster.sync();   // no CTA leaves while another may still read its partials
+  panel_sync<CG>(cluster);   // no CTA leaves while another may still read its partials
 }
 
 // ------------------------------------------------------- skinny products
