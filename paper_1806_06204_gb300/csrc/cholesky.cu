@@ -59,9 +59,15 @@ chol_diag_kernel(double* Z, int64_t strideZ, int64_t n, int64_t k0, int nbk, dou
     const double rjj = s_rd;
     for (int k = j + 1 + tid; k < nbk; k += kDiagThreads) S[j][k] *= rjj;
     __syncthreads();
-    for (int e = tid; e < nbk * nbk; e += kDiagThreads) {
-      const int i = e % nbk, k = e / nbk;
-      if (i > j && i <= k) S[i][k] = fma(-S[j][i], S[j][k], S[i][k]);
+    // trailing update of rows j+1.. : thread (row i, column group g) takes the
+    // columns k = g, g + 4, ... of row i at and right of the diagonal
+    {
+      static_assert(kDiagThreads == 4 * NB, "four threads per row of the block");
+      const int i = tid >> 2, g = tid & 3;
+      if (i > j && i < nbk) {
+        const double sji = S[j][i];
+        for (int k = i + ((g - i) & 3); k < nbk; k += 4) S[i][k] = fma(-sji, S[j][k], S[i][k]);
+      }
     }
     __syncthreads();
   }
