@@ -95,7 +95,8 @@ def test_split_pd_meets_invariants_and_matches_oracle(zb, handle, m, n, kappa, r
     assert zo.backward_error_pd(sm.A, Qp, H) <= 1e-13
     assert zo.orthogonality(Qp) <= 1e-13
     assert np.array_equal(H, H.T)
-    assert np.linalg.norm(H - Ho) <= 1e-12 * np.linalg.norm(Ho)
+    # H is well conditioned (its perturbation is Qp's times A): FP64's tolerance
+    assert np.linalg.norm(H - Ho) <= 1e-13 * np.linalg.norm(Ho)
 
 
 @pytest.mark.parametrize("prec", [1, 2])
