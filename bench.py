@@ -475,6 +475,13 @@ def batch_arm(args, w, h, mats, As, Qps, Hs, split, steps, warmup, local, dist, 
     roof["measured"] = ("one extra call after the timed steps with the batch's lanes "
                         "serialised and every launch bracketed by CUDA events (no graph replay): "
                         "each launch timed alone on the GPU")
+    # the same class inside the timed steps, where 32 lanes overlap: its work over
+    # the whole timed step is a lower bound of its rate there (it runs at most that long)
+    work = roof["achieved"] * roof["launches"] * roof["avg_launch_ms"] / 1000.0
+    rate = work / (ms_step / 1000.0)
+    roof["in_step_lower_bound"] = {
+        "achieved": rate, "frac": rate / roof["peak"],
+        "basis": "the class's work divided by the whole timed step (its lanes overlap there)"}
 
     # accuracy of every result, on the device with torch (a check, not timed)
     bwd, orth = 0.0, 0.0
