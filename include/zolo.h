@@ -44,7 +44,8 @@ enum {
   ZOLO_EIO = 8,        /* a tuning-cache file could not be written or read      */
   ZOLO_EINVAL = 9,     /* a tuning-cache file is malformed or from another GPU  */
   ZOLO_ECOMM = 10,     /* the caller's sum over ranks (zolo_pd_sharded) failed  */
-  ZOLO_EPENDING = 11   /* zolo_pd_async: the stream has not reached the end yet */
+  ZOLO_EPENDING = 11,  /* zolo_pd_async: the stream has not reached the end yet */
+  ZOLO_EGUARD = 12     /* zolo_debug_guards: a kernel wrote outside its buffer  */
 };
 
 /* Arithmetic of the contractions.  ZOLO_FP64: plain FP64 on the FP64 FMA pipe.
@@ -373,6 +374,19 @@ int zolo_tune_load(zolo_handle_t handle, const char* path);
        barrier when they see the error flag).
    where = 0 switches it off.  Returns 0, -1 (NULL handle), -2 (where) or -3
    (ns). */
+/* zolo_debug_guards(h, 1): a checking mode for the workspace (no counterpart in
+   the paper; a substitute for a memory checker).  In zolo_pd, zolo_svd and
+   zolo_pd_sharded calls on h, every buffer carved from the handle's workspace
+   is followed by a 4 KB guard zone filled with 0xFF bytes (an FP64 NaN
+   pattern), and the regions that normally share memory (the QR, Cholesky and
+   eigensolver buffers) are laid out one after another; after the iterations,
+   H and (zolo_svd) the eigendecomposition, a kernel checks every zone, and a
+   changed byte makes the call return ZOLO_EGUARD.  More workspace, slower;
+   results are unchanged.  The slice planes of the split path and the batched,
+   asynchronous and host entry points' own buffers are not guarded.  Returns
+   0, -1 (NULL handle) or -2 (enable not 0/1). */
+int zolo_debug_guards(zolo_handle_t handle, int enable);
+
 #define ZOLO_STALL_SPLIT_GEMM 1
 #define ZOLO_STALL_JACOBI32 2
 int zolo_debug_stall(zolo_handle_t handle, int where, int64_t ns);

@@ -24,7 +24,7 @@ ZOLO_R_TUNED = -1
 
 ERRORS = {1: "ZOLO_ENONFINITE", 2: "ZOLO_ECHOL", 3: "ZOLO_ENOTCONV", 4: "ZOLO_ECUDA",
           5: "ZOLO_ENOMEM", 6: "ZOLO_EEIG", 7: "ZOLO_ETIMEOUT", 8: "ZOLO_EIO", 9: "ZOLO_EINVAL",
-          10: "ZOLO_ECOMM", 11: "ZOLO_EPENDING"}
+          10: "ZOLO_ECOMM", 11: "ZOLO_EPENDING", 12: "ZOLO_EGUARD"}
 ZOLO_EPENDING = 11
 ZOLO_PHASES = 8
 PHASE_NAMES = ["bounds", "qr", "chol", "newton_schulz", "H", "estimates", "eig", "U"]
@@ -98,6 +98,8 @@ def _load():
     lib.zolo_shift_range.restype = I
     lib.zolo_pd_sharded.argtypes = pd_args + [I, I, SUM_FN, P]
     lib.zolo_pd_sharded.restype = I
+    lib.zolo_debug_guards.argtypes = [P, I]
+    lib.zolo_debug_guards.restype = I
     lib.zolo_batch_graphs.argtypes = [P, I]
     lib.zolo_batch_graphs.restype = I
     lib.zolo_debug_stall.argtypes = [P, I, I64]
@@ -126,7 +128,7 @@ EXPORTED = ["zolo_opts_default", "zolo_create", "zolo_destroy", "zolo_coefficien
             "zolo_dgemm", "zolo_dgemm_noalloc", "zolo_pd_batched", "zolo_tuned_r",
             "zolo_tune_save", "zolo_tune_load", "zolo_autotune",
             "zolo_workspace_bytes", "zolo_debug_stall", "zolo_shift_range",
-            "zolo_pd_sharded", "zolo_pd_async", "zolo_batch_graphs"]
+            "zolo_pd_sharded", "zolo_pd_async", "zolo_batch_graphs", "zolo_debug_guards"]
 
 
 def kernel_launches() -> int:
@@ -227,6 +229,13 @@ def autotune(handle, enable: bool) -> None:
 
 ZOLO_STALL_SPLIT_GEMM = 1
 ZOLO_STALL_JACOBI32 = 2
+
+
+def debug_guards(handle, enable: bool) -> None:
+    """Guard zones around the workspace's buffers, checked after each call (zolo.h)."""
+    e = LIB.zolo_debug_guards(handle.ptr, int(enable))
+    if e:
+        raise ZoloError(e, "zolo_debug_guards")
 
 
 def batch_graphs(handle, enable: bool) -> None:

@@ -108,6 +108,8 @@ struct zolo_handle_s {
   AsyncSlot* async = nullptr;              // pinned ring of zolo_pd_async records
   int async_next = 0;
   bool batch_graphs = true;                // zolo_pd_batched records and replays a graph
+  bool guards = false;                     // zolo_debug_guards
+  int* guard_flag = nullptr;               // set by the guard check
 };
 
 namespace {
@@ -115,6 +117,14 @@ namespace {
 constexpr double kEps = 2.220446049250313e-16;
 
 bool is_split(int prec) { return prec == ZOLO_SPLIT_BF16 || prec == ZOLO_SPLIT_FP16; }
+
+// Guard zones (zolo_debug_guards): in a call made with them on, every buffer
+// carved from the workspace is followed by kGuardBytes of 0xFF (an FP64 NaN
+// pattern) and the QR, Cholesky and eigensolver regions stop sharing memory;
+// the zones of the last layout placed in the workspace are listed here.
+constexpr size_t kGuardBytes = 4096;
+thread_local bool t_guard_on = false;
+thread_local std::vector<std::pair<size_t, size_t>> t_guards;   // (offset, bytes)
 
 // Bump allocator over one device block; with base == nullptr it only sizes.
 struct Carve {
@@ -126,6 +136,11 @@ struct Carve {
     off = (off + 255) & ~size_t(255);
     T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
     off += count * sizeof(T);
+    if (t_guard_on) {
+      off = (off + 255) & ~size_t(255);
+      if (base) t_guards.emplace_back(off, kGuardBytes);
+      off += kGuardBytes;
+    }
     return p;
   }
 };
@@ -144,6 +159,7 @@ struct PdBufs {
 // Workspace layout for (m, n, r).  The QR, Cholesky and eigensolver regions
 // are never live at the same time and share one union region.
 size_t layout(void* base, int64_t m, int64_t n, int r, bool svd, PdBufs* b) {
+  if (base && t_guard_on) t_guards.clear();
   Carve c(base);
   PdBufs t{};
   t.X = c.take<double>(m * n);
@@ -161,7 +177,7 @@ size_t layout(void* base, int64_t m, int64_t n, int r, bool svd, PdBufs* b) {
   // QR region
   {
     Carve q(base);
-    q.off = union_start;
+    q.off = t_guard_on ? c.off : union_start;   // guard mode: no sharing
     const int64_t npan = (n + kQrNB - 1) / kQrNB;
     t.qr.strideW = (m + n) * n;
     t.qr.W = q.take<double>(r * t.qr.strideW);
@@ -185,7 +201,7 @@ size_t layout(void* base, int64_t m, int64_t n, int r, bool svd, PdBufs* b) {
   // Cholesky region
   {
     Carve q(base);
-    q.off = union_start;
+    q.off = t_guard_on ? c.off : union_start;   // guard mode: no sharing
     const int64_t nblk = (n + kCholNB - 1) / kCholNB;
     t.ch.strideZ = n * n;
     t.ch.Z = q.take<double>(r * t.ch.strideZ);
@@ -200,7 +216,7 @@ size_t layout(void* base, int64_t m, int64_t n, int r, bool svd, PdBufs* b) {
   // eigensolver region
   if (svd) {
     Carve q(base);
-    q.off = union_start;
+    q.off = t_guard_on ? c.off : union_start;   // guard mode: no sharing
     const int64_t nblk = (n + kCholNB - 1) / kCholNB;
     t.eig.R = q.take<double>(n * n);
     t.eig.X = q.take<double>(n * n);
@@ -233,6 +249,47 @@ int ensure_ws(zolo_handle_t h, size_t bytes) {
   h->ws_bytes = bytes;
   return 0;
 }
+
+// Fill the listed guard zones of the workspace and clear the flag (guard mode).
+int guards_arm(zolo_handle_t h, cudaStream_t st) {
+  if (!t_guard_on) return 0;
+  if (!h->guard_flag && cudaMalloc(&h->guard_flag, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    h->guard_flag = nullptr;
+    return ZOLO_ENOMEM;
+  }
+  if (cudaMemsetAsync(h->guard_flag, 0, sizeof(int), st) != cudaSuccess) return ZOLO_ECUDA;
+  for (const auto& g : t_guards)
+    if (guard_fill(static_cast<char*>(h->ws) + g.first, g.second, st) != cudaSuccess)
+      return ZOLO_ECUDA;
+  return 0;
+}
+
+// Check every listed zone still holds 0xFF; ZOLO_EGUARD if not (synchronises).
+int guards_check(zolo_handle_t h, cudaStream_t st) {
+  if (!t_guard_on || !h->guard_flag) return 0;
+  for (const auto& g : t_guards)
+    if (guard_check(static_cast<const char*>(h->ws) + g.first, g.second, h->guard_flag, st) !=
+        cudaSuccess)
+      return ZOLO_ECUDA;
+  int f = 0;
+  if (cudaMemcpyAsync(&f, h->guard_flag, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return ZOLO_ECUDA;
+  return f ? ZOLO_EGUARD : 0;
+}
+
+// Guard mode for the calls of one entry point on this thread.
+struct GuardScope {
+  explicit GuardScope(bool on) {
+    t_guard_on = on;
+    t_guards.clear();
+  }
+  ~GuardScope() {
+    t_guard_on = false;
+    t_guards.clear();
+  }
+};
 
 // Slice-plane elements for the largest contraction of a decomposition of an
 // m x n matrix (one batch entry, S = 9, the widest slicing used).
@@ -767,6 +824,7 @@ int pd_core(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda,
   layout(h->ws, m, n, r, svd, &R.b);
   if (out_bufs) *out_bufs = R.b;
   const PdBufs& b = R.b;
+  if (int e = guards_arm(h, st)) return e;
   SplitScope split;
   if (is_split(o.prec))
     if (int e = split.begin(h, m, n, r, st, o.prec)) return e;
@@ -880,6 +938,7 @@ int pd_core(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda,
     if (int e = enqueue_estimates(b, A, lda, Qp, ldq, H, ldh, m, n, st)) return e;
   }
   // final status and norms
+  if (int e = guards_check(h, st)) return e;
   double hn[kNormSlots];
   CK(cudaMemcpyAsync(hn, b.norms, sizeof(hn), cudaMemcpyDeviceToHost, st));
   if (int e = read_status(R, hstat)) return e;
@@ -1035,6 +1094,7 @@ int zolo_destroy(zolo_handle_t h) {
   if (h->hrec) cudaFreeHost(h->hrec);
   if (h->e0) cudaEventDestroy(h->e0);
   if (h->e1) cudaEventDestroy(h->e1);
+  if (h->guard_flag) cudaFree(h->guard_flag);
   for (cudaEvent_t ev : h->ph_ev)
     if (ev) cudaEventDestroy(ev);
   if (h->async) {
@@ -1100,6 +1160,7 @@ int zolo_pd(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda,
   if (cudaSetDevice(h->device) != cudaSuccess) return info->status = ZOLO_ECUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   TunerScope ts(&h->tuner);
+  GuardScope guard(h->guards);
   PhaseClock pc;
   pc.start(h, st);
   cudaEventRecord(h->e0, st);
@@ -1212,6 +1273,7 @@ int zolo_pd_sharded(zolo_handle_t h, const double* A, int64_t m, int64_t n, int6
   if (cudaSetDevice(h->device) != cudaSuccess) return info->status = ZOLO_ECUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   TunerScope ts(&h->tuner);
+  GuardScope guard(h->guards);
   ShardCtx sh;
   sh.rank = rank;
   sh.nranks = nranks;
@@ -1243,6 +1305,7 @@ int zolo_svd(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda
   if (cudaSetDevice(h->device) != cudaSuccess) return info->status = ZOLO_ECUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   TunerScope ts(&h->tuner);
+  GuardScope guard(h->guards);
   cudaEventRecord(h->e0, st);
   // Qp and H go to internal buffers carved ahead of the union region; their
   // offsets do not depend on r, and sizing with r = 8 when r is chosen by the
@@ -1293,6 +1356,7 @@ int zolo_svd(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda
         e = ZOLO_ECUDA;
       if (cudaStreamSynchronize(st) != cudaSuccess) e = ZOLO_ECUDA;
     }
+    if (e == 0) e = guards_check(h, st);   // the eigensolver's buffers too
   }
   pc.stop();
   cudaEventRecord(h->e1, st);
@@ -1786,6 +1850,13 @@ int zolo_pd_batched(zolo_handle_t h, int count, const double* const* A, const in
   return worst;
 }
 
+int zolo_debug_guards(zolo_handle_t h, int enable) {
+  if (!h) return -1;
+  if (enable != 0 && enable != 1) return -2;
+  h->guards = enable != 0;
+  return 0;
+}
+
 int zolo_batch_graphs(zolo_handle_t h, int enable) {
   if (!h) return -1;
   if (enable != 0 && enable != 1) return -2;
@@ -1896,6 +1967,8 @@ const char* zolo_strerror(int code) {
     case ZOLO_EIO: return "tuning-cache file could not be written or read";
     case ZOLO_EINVAL: return "tuning-cache file malformed or written on another GPU";
     case ZOLO_ECOMM: return "the caller's sum over ranks reported a failure";
+    case ZOLO_EPENDING: return "the asynchronous call has not completed";
+    case ZOLO_EGUARD: return "a kernel wrote outside its workspace buffer (guard zone changed)";
     default: return code < 0 ? "illegal argument" : "unknown error";
   }
 }

@@ -120,6 +120,15 @@ __global__ void weighted_sum_kernel(const double* __restrict__ T, int64_t ldt, i
   }
 }
 
+__global__ void guard_check_kernel(const unsigned char* __restrict__ p, size_t bytes,
+                                   int* __restrict__ flag) {
+  bool bad = false;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < bytes;
+       e += (size_t)gridDim.x * blockDim.x)
+    bad |= p[e] != 0xFF;
+  if (bad) atomicOr(flag, 1);
+}
+
 __global__ void flag_to_double_kernel(const int* __restrict__ flag, double* __restrict__ out) {
   *out = *flag ? 1.0 : 0.0;
 }
@@ -332,6 +341,17 @@ cudaError_t weighted_sum(const double* T, int64_t ldt, int64_t strideT, const do
   ProfScope ps(kProfCombine, st, 2.0 * (double)m * n * nt, 8.0 * (double)m * n * (nt + 1));
   weighted_sum_kernel<<<grid_for(m * n), kThreads, 0, st>>>(T, ldt, strideT, pack(coef, nt), nt, S,
                                                              lds, m, n);
+  return cudaGetLastError();
+}
+
+cudaError_t guard_fill(void* p, size_t bytes, cudaStream_t st) {
+  return cudaMemsetAsync(p, 0xFF, bytes, st);
+}
+
+cudaError_t guard_check(const void* p, size_t bytes, int* flag, cudaStream_t st) {
+  ProfScope ps(kProfOther, st);
+  guard_check_kernel<<<(unsigned)((bytes + 255) / 256 < 64 ? (bytes + 255) / 256 : 64), 256, 0, st>>>(
+      static_cast<const unsigned char*>(p), bytes, flag);
   return cudaGetLastError();
 }
 

@@ -223,6 +223,9 @@ cudaError_t combine(const double* X, int64_t ldx, double* Xn, int64_t ldxn, int6
 // S = sum_t coef_t T_t, T_t at T + t * strideT (ld ldt), t < nt <= 8
 cudaError_t weighted_sum(const double* T, int64_t ldt, int64_t strideT, const double* coef, int nt,
                          double* S, int64_t lds, int64_t m, int64_t n, cudaStream_t st);
+// guard zones: fill with 0xFF bytes; set *flag if any byte differs
+cudaError_t guard_fill(void* p, size_t bytes, cudaStream_t st);
+cudaError_t guard_check(const void* p, size_t bytes, int* flag, cudaStream_t st);
 // *out = (*flag != 0) as a double
 cudaError_t flag_to_double(const int* flag, double* out, cudaStream_t st);
 // H = (M + M^T) / 2
