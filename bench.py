@@ -329,10 +329,21 @@ def run_reference(args, w, rank):
 FP64_DFMA_MEASURED_TFLOPS = 1.20
 # Tensor-core products issued per FP64-equivalent flop on the split path: nine
 # BF16 slices per operand, slice pairs (s, t) with s + t <= 11: 53; eight FP16
-# slices, s + t <= 9: 36.
+# slices, s + t <= 9: 36; eleven FP8 (E4M3) slices, s + t <= 13: 76.  The FP8
+# products run at twice the 16-bit rate (nominal 4.5 against 2.25 PFLOP/s), so
+# their peak is the measured BF16 peak times 2.
 SPLIT_PAIRS = 53
-SPLIT_PAIRS_OF = {"bf16": 53, "fp16": 36}
-SLICE_DTYPE = {"bf16": "bf16x9-slices->f64", "fp16": "fp16x8-slices->f64"}
+SPLIT_PAIRS_OF = {"bf16": 53, "fp16": 36, "fp8": 76}
+SLICE_PEAK_RATIO = {"bf16": 1.0, "fp16": 1.0, "fp8": 2.0}
+SLICE_DTYPE = {"bf16": "bf16x9-slices->f64", "fp16": "fp16x8-slices->f64",
+               "fp8": "e4m3x11-slices->f64"}
+SLICE_DESC = {"bf16": "nine BF16 slices", "fp16": "eight FP16 slices",
+              "fp8": "eleven FP8 (E4M3) slices"}
+
+
+def split_prec(zb, slices):
+    return {"bf16": zb.ZOLO_SPLIT_BF16, "fp16": zb.ZOLO_SPLIT_FP16,
+            "fp8": zb.ZOLO_SPLIT_FP8}[slices]
 
 
 # DRAM bytes per algorithmic byte of a kernel class, from an ncu capture of that
@@ -346,14 +357,15 @@ TRAFFIC_PER_STATED_BYTE = {
 }
 
 
-def roofline(kstats, step_ms, model_flops=None, split_pairs=SPLIT_PAIRS):
+def roofline(kstats, step_ms, model_flops=None, split_pairs=SPLIT_PAIRS, peak_ratio=1.0):
     """Roofline entry of the dominant kernel class (by device time in one step).
 
     With model_flops (the Zolo-PD flops of the step), the algorithmic work of a
     flop-carrying class is the model's, shared out between the classes in
     proportion to the flops each launch site states for its launch; achieved =
     that share / the class's device time.  On the split path a model flop is
-    issued as `split_pairs` BF16 tensor-core products.  The flops the launches
+    issued as `split_pairs` tensor-core products of the slice type, whose peak is
+    `peak_ratio` times the measured BF16 one.  The flops the launches
     state themselves (padding, T factors, the explicit Q's full rows included)
     are kept beside it as `issued_*`."""
     dom_name, dom = max(((k, v) for k, v in kstats.items() if v["launches"] > 0),
@@ -371,12 +383,14 @@ def roofline(kstats, step_ms, model_flops=None, split_pairs=SPLIT_PAIRS):
         basis = "flops stated by the launches"
     if bound == "tensor":
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-        peak = peaks["bf16_tflops_sustained"]
+        peak = peaks["bf16_tflops_sustained"] * peak_ratio
         achieved = work * split_pairs / sec / 1e12
         roof = {"bound": "tensor", "kernel": dom_name, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)",
-                "work_basis": basis + f"; x{split_pairs} BF16 slice-pair products per flop",
+                "peak_source": ("MEASURED_PEAKS.json bf16_tflops_sustained (of measured)" +
+                                (f" x {peak_ratio:g} (nominal FP8/BF16 ratio)"
+                                 if peak_ratio != 1.0 else "")),
+                "work_basis": basis + f"; x{split_pairs} slice-pair products per flop",
                 "fp64_equivalent_tflops": work / sec / 1e12,
                 "issued_tflops": dom["flops"] * split_pairs / sec / 1e12}
     elif bound == "alu":
@@ -414,7 +428,7 @@ def batch_arm(args, w, h, mats, As, Qps, Hs, split, steps, warmup, local, dist, 
     import torch
     from paper_1806_06204_gb300 import binding as zb
     slices = slices or args.slices
-    sp = zb.ZOLO_SPLIT_FP16 if slices == "fp16" else zb.ZOLO_SPLIT_BF16
+    sp = split_prec(zb, slices)
     os_ = [zb.opts(beta=float(sm.sigma[-1]), alpha=1.0, r=0,
                    prec=sp if split else zb.ZOLO_FP64, ns_steps=1 if split else 0,
                    chol_form=args.chol_form)
@@ -471,7 +485,8 @@ def batch_arm(args, w, h, mats, As, Qps, Hs, split, steps, warmup, local, dist, 
     kstats = zb.profile_read()
     zb.profile(False)
     prof_ms = e2.elapsed_time(e3)
-    roof = roofline(kstats, prof_ms, flops, split_pairs=SPLIT_PAIRS_OF[slices])
+    roof = roofline(kstats, prof_ms, flops, split_pairs=SPLIT_PAIRS_OF[slices],
+                    peak_ratio=SLICE_PEAK_RATIO[slices])
     roof["measured"] = ("one extra call after the timed steps with the batch's lanes "
                         "serialised and every launch bracketed by CUDA events (no graph replay): "
                         "each launch timed alone on the GPU")
@@ -520,16 +535,21 @@ def run_batch(args, w, rank, world, dist, local):
     head_split = prec in ("split", "both")
     arm = batch_arm(args, w, h, mats, As, Qps, Hs, head_split, args.steps, args.warmup, local,
                     dist)
-    fp64 = other = None
+    fp64 = None
+    others = []
     if prec == "both":
         fs = args.fp64_steps if args.fp64_steps is not None else max(1, min(args.steps, 5))
         fw = args.fp64_warmup if args.fp64_warmup is not None else min(args.warmup, 3)
         fp64 = batch_arm(args, w, h, mats, As, Qps, Hs, False, fs, fw, local, dist)
         if not args.no_other_slices:
-            # the other slice format on the same matrices, for comparison
-            oth = "fp16" if args.slices == "bf16" else "bf16"
-            other = batch_arm(args, w, h, mats, As, Qps, Hs, True, fs, fw, local, dist, slices=oth)
-            other["slices"] = oth
+            # the other slice forms on the same matrices, for comparison
+            for oth in SLICE_DTYPE:
+                if oth == args.slices:
+                    continue
+                other = batch_arm(args, w, h, mats, As, Qps, Hs, True, fs, fw, local, dist,
+                                  slices=oth)
+                other["slices"] = oth
+                others.append(other)
     value = world * w["count"] / (arm["ms_step"] / 1000.0)
     os_ = arm["os"]
 
@@ -572,7 +592,7 @@ def run_batch(args, w, rank, world, dist, local):
     if rank == 0:
         ns = [a.shape[1] for a in As]
         infos = arm["infos"]
-        sl = ("nine BF16 slices" if args.slices == "bf16" else "eight FP16 slices")
+        sl = SLICE_DESC[args.slices]
         desc = w["desc"] + (f": split precision ({sl}, FP32 level sums) timed, plain "
                             "FP64 beside it" if prec == "both" else
                             (f": split precision ({sl})" if head_split else
@@ -608,7 +628,7 @@ def run_batch(args, w, rank, world, dist, local):
                             "kernel_ms": {k: round(v["ms"], 3) for k, v in fp64["kstats"].items()
                                           if v["launches"]},
                             "clocks": fp64["clocks"]}
-        if other is not None:
+        for other in others:
             ov = world * w["count"] / (other["ms_step"] / 1000.0)
             line[other["slices"] + "_slices"] = {
                 "value": ov, "unit": "matrices/s", "dtype": SLICE_DTYPE[other["slices"]],
@@ -622,7 +642,7 @@ def run_batch(args, w, rank, world, dist, local):
                               if v["launches"]},
                 "clocks": other["clocks"]}
         print(json.dumps(line), flush=True)
-        bad = [a for a in (arm, fp64, other) if a is not None and not a["acc"]["bar_met"]]
+        bad = [a for a in (arm, fp64, *others) if a is not None and not a["acc"]["bar_met"]]
         if bad:
             print("accuracy bar (1e-13) not met", file=sys.stderr)
             h.close()
@@ -641,16 +661,17 @@ def main():
                     help="split: the iterations' products on the BF16 tensor cores (Ozaki slices); "
                          "both (batch only): split timed, FP64 beside it; auto: both for the "
                          "batch, fp64 otherwise")
-    ap.add_argument("--slices", default="bf16", choices=["bf16", "fp16"],
+    ap.add_argument("--slices", default="bf16", choices=sorted(SLICE_DTYPE),
                     help="split precision's slices: nine BF16 six-bit slices (53 slice-pair "
-                         "products) or eight FP16 seven-bit slices (36)")
+                         "products), eight FP16 seven-bit slices (36) or eleven FP8 "
+                         "five-bit slices (76 at twice the rate)")
     ap.add_argument("--no-graph", action="store_true",
                     help="batch workload: queue the lanes directly every step instead of replaying "
                          "a recorded CUDA graph (for kernel profilers)")
     ap.add_argument("--count", type=int, default=None,
                     help="batch workload: only its first COUNT matrices (for profiler captures)")
     ap.add_argument("--no-other-slices", action="store_true",
-                    help="with --prec both: skip the arm of the other slice format")
+                    help="with --prec both: skip the arms of the other slice forms")
     ap.add_argument("--fp64-steps", type=int, default=None,
                     help="timed steps of the FP64 arm with --prec both (default min(steps, 5))")
     ap.add_argument("--fp64-warmup", type=int, default=None,
@@ -732,7 +753,7 @@ def main():
     split = args.prec == "split"
     beta_scale = args.beta_scale if args.beta_scale is not None else w.get("beta_scale", 1.0)
     r_req = args.r if args.r is not None else w["r"]
-    sp = zb.ZOLO_SPLIT_FP16 if args.slices == "fp16" else zb.ZOLO_SPLIT_BF16
+    sp = split_prec(zb, args.slices)
     o = zb.opts(beta=float(np.min(sm.sigma)) * beta_scale, alpha=1.0, r=r_req,
                 prec=sp if split else zb.ZOLO_FP64, ns_steps=1 if split else 0,
                 chol_form=args.chol_form)
@@ -792,7 +813,8 @@ def main():
     torch.cuda.synchronize()
     kstats = zb.profile_read()
     zb.profile(False)
-    roof = roofline(kstats, e2.elapsed_time(e3), flops, split_pairs=SPLIT_PAIRS_OF[args.slices])
+    roof = roofline(kstats, e2.elapsed_time(e3), flops, split_pairs=SPLIT_PAIRS_OF[args.slices],
+                    peak_ratio=SLICE_PEAK_RATIO[args.slices])
     roof["measured"] = "one extra step after the timed ones, per-launch CUDA events"
 
     # end to end through the host-buffer entry point

@@ -55,10 +55,11 @@ enum {
    factorisations, diagonal blocks and coefficients stay FP64.
    ZOLO_SPLIT_FP16: the same on the FP16 tensor cores with 8 slices of 7-bit
    integer digits and 36 slice-pair products instead of 53 (the same error
-   grade; inner dimensions up to about 60000).  An FP8 form is not offered:
-   E4M3's 4-bit digits need 14 slices and about 118 slice pairs, more work at
-   FP8's doubled rate than the BF16 form's 53. */
-enum { ZOLO_FP64 = 0, ZOLO_SPLIT_BF16 = 1, ZOLO_SPLIT_FP16 = 2 };
+   grade; inner dimensions up to about 60000).
+   ZOLO_SPLIT_FP8: the same on the FP8 (E4M3) tensor cores with 11 slices of
+   5-bit integer digits and 76 slice-pair products at twice the BF16 rate
+   (the same error grade; inner dimensions up to about 110000). */
+enum { ZOLO_FP64 = 0, ZOLO_SPLIT_BF16 = 1, ZOLO_SPLIT_FP16 = 2, ZOLO_SPLIT_FP8 = 3 };
 
 typedef struct {
   int r;           /* order parameter, 1..8 (Eq. 6: type (2r+1, 2r)); 0 = the
@@ -83,7 +84,7 @@ typedef struct {
                       ||X_{k+1}-X_k||_F/||X_{k+1}||_F > eps^(1/(2r+1))        */
   int ns_steps;    /* Newton-Schulz steps X <- 1.5X - 0.5X(X^T X) after the
                       iteration (not in the paper), 0..4                      */
-  int prec;        /* ZOLO_FP64, ZOLO_SPLIT_BF16 or ZOLO_SPLIT_FP16            */
+  int prec;        /* ZOLO_FP64, ZOLO_SPLIT_BF16, _FP16 or _FP8                */
   int force_qr;    /* -1: QR form while (1+c_1)/(l^2+c_1) > 100, then the
                       Cholesky form; 0: Cholesky form always; 1: QR always     */
   int chol_form;   /* how a Cholesky-form iteration applies the r factors
@@ -281,8 +282,9 @@ int zolo_svd_host(zolo_handle_t handle, const double* A, int64_t m, int64_t n, i
 /* C = alpha op(A) op(B) + beta C for device FP64 matrices (column-major,
    op = identity or transpose: trans = 0 / 1), the contraction the iterations
    run on.  prec = ZOLO_FP64 (DFMA), ZOLO_SPLIT_BF16 with `slices` = 8 or 9
-   (0 = 8) six-bit slices per operand on the tensor cores, or ZOLO_SPLIT_FP16
-   (`slices` 0 or 8: eight seven-bit slices).  Not in the paper as
+   (0 = 8) six-bit slices per operand on the tensor cores, ZOLO_SPLIT_FP16
+   (`slices` 0 or 8: eight seven-bit slices) or ZOLO_SPLIT_FP8 (`slices` 0 or
+   11: eleven five-bit slices).  Not in the paper as
    an interface; it exposes the building block for testing and reuse.
    Synchronises the stream before returning. */
 int zolo_dgemm(zolo_handle_t handle, int transA, int transB, int64_t m, int64_t n, int64_t k,
@@ -367,7 +369,7 @@ int zolo_tune_load(zolo_handle_t handle, const char* path);
    calls on this handle make the named kernel first wait, for `ns` nanoseconds
    (0 .. 1e9), on a barrier or flag that nothing completes:
      ZOLO_STALL_SPLIT_GEMM: the MMA-issuing thread of every split-precision
-       product (opts.prec = ZOLO_SPLIT_BF16 or FP16, zolo_dgemm's split path),
+       product (opts.prec = ZOLO_SPLIT_BF16, FP16 or FP8, zolo_dgemm's split path),
        on an mbarrier no thread or copy arrives at;
      ZOLO_STALL_JACOBI32: block 0 of the first FP32 sweep of zolo_svd's
        eigensolver, on a flag no thread sets (the other blocks leave the grid

@@ -20,6 +20,7 @@ ZOLO_MAX_ITERS = 8
 ZOLO_FP64 = 0
 ZOLO_SPLIT_BF16 = 1
 ZOLO_SPLIT_FP16 = 2
+ZOLO_SPLIT_FP8 = 3
 ZOLO_R_TUNED = -1
 
 ERRORS = {1: "ZOLO_ENONFINITE", 2: "ZOLO_ECHOL", 3: "ZOLO_ENOTCONV", 4: "ZOLO_ECUDA",

@@ -90,7 +90,7 @@ struct zolo_handle_s {
   size_t ws_bytes = 0;
   void* io = nullptr;
   size_t io_bytes = 0;
-  void* slices = nullptr;     // split-precision slice planes (BF16)
+  void* slices = nullptr;     // split-precision slice planes (16-bit units)
   size_t slice_elems = 0;
   int* exps = nullptr;        // slice exponents
   size_t exp_elems = 0;
@@ -116,7 +116,16 @@ namespace {
 
 constexpr double kEps = 2.220446049250313e-16;
 
-bool is_split(int prec) { return prec == ZOLO_SPLIT_BF16 || prec == ZOLO_SPLIT_FP16; }
+bool is_split(int prec) {
+  return prec == ZOLO_SPLIT_BF16 || prec == ZOLO_SPLIT_FP16 || prec == ZOLO_SPLIT_FP8;
+}
+// The slice form and count of a split precision.
+int split_form(int prec) {
+  return prec == ZOLO_SPLIT_FP8 ? kFormFP8 : prec == ZOLO_SPLIT_FP16 ? kFormFP16 : kFormBF16;
+}
+int split_slices(int prec) {
+  return prec == ZOLO_SPLIT_FP8 ? 11 : prec == ZOLO_SPLIT_FP16 ? 8 : 9;
+}
 
 // Guard zones (zolo_debug_guards): in a call made with them on, every buffer
 // carved from the workspace is followed by kGuardBytes of 0xFF (an FP64 NaN
@@ -291,13 +300,16 @@ struct GuardScope {
   }
 };
 
-// Slice-plane elements for the largest contraction of a decomposition of an
-// m x n matrix (one batch entry, S = 9, the widest slicing used).
+// Slice-plane units for the largest contraction of a decomposition of an
+// m x n matrix (one batch entry, the larger of the BF16 form's nine slices and
+// the FP8 form's eleven, whose K runs are padded to 128).
 size_t split_elems_per_entry(int64_t m, int64_t n) {
   const int64_t shapes[][3] = {{kQrNB, n, m + kQrNB}, {m + kQrNB, n, kQrNB}, {m, n, n},
                                {n, n, m}, {m, kCholNB, n}, {m, n, n}};
   size_t mx = 0;
-  for (auto& sh : shapes) mx = std::max(mx, split_slice_elems(sh[0], sh[1], sh[2], 1, 9));
+  for (auto& sh : shapes)
+    mx = std::max({mx, split_slice_elems(sh[0], sh[1], sh[2], 1, 9, kFormBF16),
+                   split_slice_elems(sh[0], sh[1], sh[2], 1, 11, kFormFP8)});
   return mx;
 }
 
@@ -347,8 +359,8 @@ struct SplitScope {
     w.exps = h->exps;
     w.exp_elems = h->exp_elems;
     w.err = h->err;
-    w.slices_s = prec == ZOLO_SPLIT_FP16 ? 8 : 9;
-    w.fp16 = prec == ZOLO_SPLIT_FP16;
+    w.slices_s = split_slices(prec);
+    w.form = split_form(prec);
     w.stall = h->dbg_stall == ZOLO_STALL_SPLIT_GEMM;
     w.stall_ns = h->dbg_ns;
     set_split_engine(&w);
@@ -906,7 +918,7 @@ int pd_core(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda,
       ++it;
     }
   }
-  // Newton-Schulz refinement steps (nine slices on the split path, as the iteration)
+  // Newton-Schulz refinement steps (on the split path in the iteration's slice form)
   if (pc && o.ns_steps > 0) pc->mark(ZOLO_PHASE_NS);
   for (int s = 0; s < o.ns_steps; ++s) {
     GemmArgs g;
@@ -1456,7 +1468,8 @@ int zolo_dgemm(zolo_handle_t h, int transA, int transB, int64_t m, int64_t n, in
   if (m > 0 && n > 0 && !C) return -13;
   if (ldc < std::max<int64_t>(1, m)) return -14;
   if (prec != ZOLO_FP64 && !is_split(prec)) return -15;
-  if (slices != 0 && slices != 8 && !(slices == 9 && prec != ZOLO_SPLIT_FP16)) return -16;
+  if (slices != 0 && slices != split_slices(prec) && !(prec == ZOLO_SPLIT_BF16 && slices == 8))
+    return -16;
   if (cudaSetDevice(h->device) != cudaSuccess) return ZOLO_ECUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   TunerScope ts(&h->tuner);
@@ -1470,13 +1483,13 @@ int zolo_dgemm(zolo_handle_t h, int transA, int transB, int64_t m, int64_t n, in
     if (gemm_f64(g, st) != cudaSuccess) return ZOLO_ECUDA;
     return cudaStreamSynchronize(st) == cudaSuccess ? 0 : ZOLO_ECUDA;
   }
-  const int S = slices ? slices : 8;
-  const size_t per = split_slice_elems(m, n, k, 1, S);
+  const int S = slices ? slices : prec == ZOLO_SPLIT_BF16 ? 8 : split_slices(prec);
+  const size_t per = split_slice_elems(m, n, k, 1, S, split_form(prec));
   const size_t exps = (size_t)2 * (size_t)(std::max(m, n) + m + n + 512);
   if (int e = ensure_split(h, per, per, exps)) return e;
   if (cudaMemsetAsync(h->err, 0, sizeof(int), st) != cudaSuccess) return ZOLO_ECUDA;
   SplitWork w{h->slices, h->slice_elems, h->exps, h->exp_elems, h->err, S};
-  w.fp16 = prec == ZOLO_SPLIT_FP16;
+  w.form = split_form(prec);
   w.stall = h->dbg_stall == ZOLO_STALL_SPLIT_GEMM;
   w.stall_ns = h->dbg_ns;
   if (gemm_split(g, w, st) != cudaSuccess) return ZOLO_ECUDA;
@@ -1655,8 +1668,8 @@ int zolo_pd_batched(zolo_handle_t h, int count, const double* const* A, const in
       R.narrow_panels = true;
       layout(sl.ws, m[i], n[i], sch[i].r, false, &R.b);
       SplitWork w{sl.slices, sl.slice_elems, sl.exps, sl.exp_elems, sl.err, 9};
-      w.slices_s = opts[i].prec == ZOLO_SPLIT_FP16 ? 8 : 9;
-      w.fp16 = opts[i].prec == ZOLO_SPLIT_FP16;
+      w.slices_s = split_slices(opts[i].prec);
+      w.form = split_form(opts[i].prec);
       w.throughput = true;
       set_split_engine(is_split(opts[i].prec) ? &w : nullptr);
       const int e = pd_enqueue(R, A[i], lda[i], Qp[i], ldq[i], H[i], ldh[i], sch[i], opts[i],
@@ -1736,8 +1749,8 @@ int zolo_pd_batched(zolo_handle_t h, int count, const double* const* A, const in
       R.b.status = reinterpret_cast<int*>(rec);
       R.b.norms = rec + 4;
       SplitWork w{sl.slices, sl.slice_elems, sl.exps, sl.exp_elems, sl.err, 9};
-      w.slices_s = opts[i].prec == ZOLO_SPLIT_FP16 ? 8 : 9;
-      w.fp16 = opts[i].prec == ZOLO_SPLIT_FP16;
+      w.slices_s = split_slices(opts[i].prec);
+      w.form = split_form(opts[i].prec);
       w.throughput = true;   // many lanes in flight: latency is hidden
       w.stall = h->dbg_stall == ZOLO_STALL_SPLIT_GEMM;
       w.stall_ns = h->dbg_ns;
@@ -1937,7 +1950,7 @@ int zolo_tune_load(zolo_handle_t h, const char* path) {
       if (std::fscanf(f, "%d %d %d %d %d %d %d", &k[0], &k[1], &k[2], &k[3], &k[4], &k[5], &v) !=
               7 ||
           k[0] < 1 || k[1] < 1 || k[2] < 1 || k[3] < 1 || k[3] > kGemmMaxBatch || k[4] < 0 ||
-          k[4] > 255 || (k[5] != 0 && k[5] != 8 && k[5] != 9 && k[5] != 108) ||
+          k[4] > 255 || (k[5] != 0 && k[5] != 8 && k[5] != 9 && k[5] != 108 && k[5] != 211) ||
           !gemm_variant_allowed({k[0], k[1], k[2], k[3], k[4], k[5], 0}, v))
         rc = ZOLO_EINVAL;
       else

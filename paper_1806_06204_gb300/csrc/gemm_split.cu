@@ -20,7 +20,7 @@
 // Accuracy: |C - AB| <~ 8 sqrt(K) 2^-6S max|A_i.| max|B_.j|, dominated by the
 // rounding of N against a row maximum in [1/4, 1/2) (S = 9: FP64 grade).
 //
-// FP16 form (F16 = true): FP16 has three more significand bits than BF16 but
+// FP16 form: FP16 has three more significand bits than BF16 but
 // cannot hold a digit pre-scaled by 2^-7s (its range ends at 2^-24), so its
 // slices are the raw balanced base-128 digits, |d_s| <= 64 (exact in FP16).
 // S = 8 slices (56 bits) and the pairs with s + t <= S + 1 = 9: 36 slice-pair
@@ -31,9 +31,24 @@
 // units, joined as iacc + f 2^-7 before the scale 2^(e_i + f_j - 49).  The
 // error is the BF16 form's (CPU model: 1.43e-15 against 1.40e-15 of the row and
 // column maxima on the same operands).
+//
+// FP8 form (E4M3, tcgen05 kind::f8f6f4): E4M3 holds every integer |d| <= 16
+// exactly but nothing pre-scaled below 2^-9, so its slices are raw balanced
+// base-32 digits, |d_s| <= 16: S = 11 slices (55 bits) and the pairs with
+// s + t <= S + 2 = 13 (76 slice pairs, 38 16-bit-product equivalents at FP8's
+// doubled rate; dropping level 13 would multiply the error by five).
+// |d_s d_t| <= 2^8, so a level of p <= 11 pairs stays exact in FP32 over
+// K-chunks of 4096.  Each of the 12 levels keeps its own accumulator of BN = 32
+// columns (384 of TMEM's 512); the epilogue adds levels 2..9 to an int64 of
+// 2^-48 units and levels 10..13 to one float in 2^-65 units, joined as
+// iacc + f 2^-17.  A K block is 128 one-byte elements, the same 128-byte
+// swizzled rows as the 16-bit forms, and one MMA takes K = 32 (32 bytes), so
+// the shared-memory layout and descriptors are the 16-bit forms' byte for byte.
+// The slice planes take 11 bytes per element against 18.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include <climits>
 #include <cmath>
@@ -50,14 +65,26 @@ namespace {
 
 constexpr int kBeta = 6;          // BF16 form: base-64 digits
 constexpr int kTileM = 128;
-constexpr int kBK = 64;            // one 128-byte swizzle row of 16-bit elements
-constexpr int kAcc = 8;            // TMEM accumulators (BF16: levels 2..8 exact, >= 9 merged;
-                                   // FP16: one per level 2..9)
-// digit width, exact-accumulation span of a level's sums, and the largest
-// 0-based level s + t kept (1-based S + 2 for BF16, S + 1 for FP16)
-template <bool F16> __host__ __device__ constexpr int digit_bits() { return F16 ? 7 : kBeta; }
-template <bool F16> __host__ __device__ constexpr int chunk_k() { return F16 ? 512 : 2048; }
-template <bool F16, int S> __host__ __device__ constexpr int max_level0() { return F16 ? S - 1 : S; }
+constexpr int kRowBytes = 128;     // one 128-byte swizzle row of K per tile row
+// The slice forms: digit width, element bytes (K elements per 128-byte row),
+// exact-accumulation span of a level's sums, TMEM accumulators, tile width BN
+// and the largest 0-based level s + t kept (1-based S + 2 for BF16 and FP8,
+// S + 1 for FP16).  BF16: levels 2..8 exact, >= 9 merged in the last
+// accumulator; FP16 and FP8: one accumulator per level.
+template <int FORM> struct Form;
+template <> struct Form<kFormBF16> {
+  static constexpr int kBits = 6, kElem = 2, kChunkK = 2048, kAcc = 8, kBN = 64;
+  __host__ __device__ static constexpr int top(int S) { return S; }
+};
+template <> struct Form<kFormFP16> {
+  static constexpr int kBits = 7, kElem = 2, kChunkK = 512, kAcc = 8, kBN = 64;
+  __host__ __device__ static constexpr int top(int S) { return S - 1; }
+};
+template <> struct Form<kFormFP8> {
+  static constexpr int kBits = 5, kElem = 1, kChunkK = 4096, kAcc = 12, kBN = 32;
+  __host__ __device__ static constexpr int top(int S) { return S; }
+};
+template <int FORM> __host__ __device__ constexpr int form_bk() { return kRowBytes / Form<FORM>::kElem; }
 constexpr int kARing = 4;
 constexpr int kGroupM = 8;         // tile rows per CTA group (L2 reuse of the A slices)
 constexpr int kEpiWarps = 16;      // four per TMEM lane quarter, each owning a quarter of the columns
@@ -196,38 +223,42 @@ __device__ __forceinline__ long long fixed_point(double x, int e) {
 // digits from the least significant one up; the leading digit takes what is
 // left, |d_1| <= 32 because |N| <= 2^(6S-1).  Each is exact in FP32 and BF16
 // (at most six significant bits).
-template <int S, bool F16 = false>
+template <int S, int FORM>
 __device__ __forceinline__ void slice_values(double x, int ee, float* v) {
-  constexpr int B = digit_bits<F16>();
+  constexpr int B = Form<FORM>::kBits;
+  constexpr bool raw = FORM != kFormBF16;
   long long N = fixed_point<S, B>(x, ee);
 #pragma unroll
   for (int s = S; s >= 2; --s) {
     int d = (int)(N & ((1 << B) - 1));
     d = d >= (1 << (B - 1)) ? d - (1 << B) : d;
-    // BF16: the digit pre-scaled by 2^-Bs; FP16: the raw digit (scaled in the epilogue)
-    v[s - 1] = F16 ? (float)d : (float)d * __int_as_float((127 - B * s) << 23);
+    // BF16: the digit pre-scaled by 2^-Bs; FP16 and FP8: the raw digit (scaled
+    // in the epilogue)
+    v[s - 1] = raw ? (float)d : (float)d * __int_as_float((127 - B * s) << 23);
     N = (N - d) >> B;
   }
-  v[0] = F16 ? (float)N : (float)N * __int_as_float((127 - B) << 23);
+  v[0] = raw ? (float)N : (float)N * __int_as_float((127 - B) << 23);
 }
 
-// S slices of op(X), each rows_pad x K_pad BF16, K contiguous; batch entry b at
-// out + b * S * rows_pad * K_pad, slice s (1-based) at + (s-1) * rows_pad * K_pad.
-// 32 x 64 tiles through shared memory: the read runs along X's contiguous
-// dimension, and each thread writes two neighbouring K entries per plane so
-// that a warp stores whole 128-byte lines.
-template <int S, bool F16 = false>
+// S slices of op(X), each rows_pad x K_pad elements of the form's type (BF16,
+// FP16 or E4M3), K contiguous; batch entry b at out + b * S * rows_pad * K_pad,
+// slice s (1-based) at + (s-1) * rows_pad * K_pad elements.  32 x 64 tiles
+// through shared memory: the read runs along X's contiguous dimension, and each
+// thread writes two neighbouring K entries per plane so that a warp stores whole
+// 128-byte (16-bit forms) or 64-byte (FP8) lines.
+template <int S, int FORM>
 __global__ void __launch_bounds__(256)
 slice_kernel(const double* __restrict__ X, int64_t ldx, int64_t strideX, int trans,
              int rows, int K, const int* __restrict__ e_in,
-             __nv_bfloat16* __restrict__ out, int rows_pad, int K_pad,
+             uint8_t* __restrict__ out, int rows_pad, int K_pad,
              const int* __restrict__ ek, int esign) {
+  constexpr int kE = Form<FORM>::kElem;
   __shared__ double tile[32][65];                 // [row][k]
   const double* Xb = X + blockIdx.z * strideX;
   const int* eb = e_in + blockIdx.z * rows_pad;
   const int* ekb = ek ? ek + blockIdx.z * K_pad : nullptr;
-  const size_t plane = (size_t)rows_pad * K_pad;
-  __nv_bfloat16* ob = out + (size_t)blockIdx.z * S * plane;
+  const size_t plane = (size_t)rows_pad * K_pad;  // elements
+  uint8_t* ob = out + (size_t)blockIdx.z * S * plane * kE;
   const int i0 = blockIdx.y * 32, k0 = blockIdx.x * 64;
   const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
   if (!trans) {     // rows contiguous: tx runs along i
@@ -256,20 +287,26 @@ slice_kernel(const double* __restrict__ X, int64_t ldx, int64_t strideX, int tra
       // element x 2^(esign ek[k]) against the row bound 2^(e_i - 1)
       const int ea = ekb ? eb[i] - esign * ekb[k] : eb[i];
       const int eb2 = ekb ? eb[i] - esign * ekb[k + 1] : eb[i];
-      slice_values<S, F16>(tile[r][kl], ea, va);
-      slice_values<S, F16>(tile[r][kl + 1], eb2, vb);
+      slice_values<S, FORM>(tile[r][kl], ea, va);
+      slice_values<S, FORM>(tile[r][kl + 1], eb2, vb);
     } else {
 #pragma unroll
       for (int s = 0; s < S; ++s) va[s] = vb[s] = 0.f;
     }
-    if (F16) {   // the same 16-bit planes hold FP16 values
-      __half2* o = reinterpret_cast<__half2*>(ob + (size_t)i * K_pad + k);
+    uint8_t* o = ob + ((size_t)i * K_pad + k) * kE;
+    if (FORM == kFormFP8) {   // two E4M3 bytes per plane (|d| <= 16: exact)
 #pragma unroll
-      for (int s = 0; s < S; ++s) o[s * (plane / 2)] = __floats2half2_rn(va[s], vb[s]);
+      for (int s = 0; s < S; ++s)
+        *reinterpret_cast<__nv_fp8x2_storage_t*>(o + s * plane) =
+            __nv_cvt_float2_to_fp8x2(make_float2(va[s], vb[s]), __NV_SATFINITE, __NV_E4M3);
+    } else if (FORM == kFormFP16) {
+#pragma unroll
+      for (int s = 0; s < S; ++s)
+        *reinterpret_cast<__half2*>(o + s * plane * 2) = __floats2half2_rn(va[s], vb[s]);
     } else {
-      __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(ob + (size_t)i * K_pad + k);
 #pragma unroll
-      for (int s = 0; s < S; ++s) o[s * (plane / 2)] = __floats2bfloat162_rn(va[s], vb[s]);
+      for (int s = 0; s < S; ++s)
+        *reinterpret_cast<__nv_bfloat162*>(o + s * plane * 2) = __floats2bfloat162_rn(va[s], vb[s]);
     }
   }
 }
@@ -304,7 +341,7 @@ struct SplitEpi {
 
 template <int BN, int S>
 struct SmemLayout {
-  static constexpr int kBTile = BN * 128;          // bytes of one B slice tile (BN x 64 BF16)
+  static constexpr int kBTile = BN * 128;          // bytes of one B slice tile (BN rows of 128 bytes)
   static constexpr int kBStage = S * kBTile;
   static constexpr int kATile = kTileM * 128;      // 16 KB
   static constexpr int kOffB = 0;
@@ -315,12 +352,16 @@ struct SmemLayout {
   static constexpr int kAlloc = kBytes + 1024;     // slack for 1024-byte alignment
 };
 
-template <int BN, int S, bool F16 = false>
+template <int BN, int S, int FORM>
 __global__ void __launch_bounds__(kThreads, 1)
 split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                   const SplitEpi p) {
   using L = SmemLayout<BN, S>;
-  constexpr int kChunkK = chunk_k<F16>();
+  using F = Form<FORM>;
+  constexpr int kChunkK = F::kChunkK;
+  constexpr int kBK = form_bk<FORM>();
+  constexpr int kAcc = F::kAcc;
+  static_assert(kAcc * BN <= 512, "the level accumulators must fit in TMEM");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sB = sm + L::kOffB;
@@ -406,11 +447,13 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
-    // One thread issues 180 MMAs per K block: the descriptors are formed once
-    // and advanced by adding to their start-address field (address >> 4, 14
-    // bits; shared addresses stay below 256 KB so no carry leaves the field),
-    // and the slice-pair loops are unrolled.
-    const uint32_t idesc = F16 ? tc::idesc_f16_f32(kTileM, BN) : tc::idesc_bf16_f32(kTileM, BN);
+    // One thread issues 4 MMAs per slice pair and K block (32 bytes of K each):
+    // the descriptors are formed once and advanced by adding to their
+    // start-address field (address >> 4, 14 bits; shared addresses stay below
+    // 256 KB so no carry leaves the field), and the slice-pair loops are unrolled.
+    const uint32_t idesc = FORM == kFormFP8    ? tc::idesc_e4m3_f32(kTileM, BN)
+                           : FORM == kFormFP16 ? tc::idesc_f16_f32(kTileM, BN)
+                                               : tc::idesc_bf16_f32(kTileM, BN);
     const uint64_t adesc0 = tc::sdesc_k128(tc::smem_u32(sA));
     const uint64_t bdesc0 = tc::sdesc_k128(tc::smem_u32(sB));
     int kbg = 0, ia = 0;
@@ -437,19 +480,22 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
           ++ia;
           tc::tc_fence_after();
           const uint64_t ad = adesc0 + (uint64_t)((sa * L::kATile) >> 4);
-          constexpr int kTop = max_level0<F16, S>();   // largest s + t (0-based) kept
+          constexpr int kTop = F::top(S);   // largest s + t (0-based) kept
 #pragma unroll
           for (int t = 0; t < (kTop - s + 1 < S ? kTop - s + 1 : S); ++t) {
             const int lvl = s + t;                 // 0 -> level 2
-            // FP16: one accumulator per level (raw digits of different scales
-            // must not share one); BF16: levels >= 9 share the last
-            const int acc = F16 ? lvl : (lvl < kAcc - 1 ? lvl : kAcc - 1);
+            // FP16 and FP8: one accumulator per level (raw digits of different
+            // scales must not share one); BF16: levels >= 9 share the last
+            const int acc = FORM != kFormBF16 ? lvl : (lvl < kAcc - 1 ? lvl : kAcc - 1);
             const uint32_t d = tmem + acc * BN;
             const uint64_t bt = bd + (uint64_t)((t * L::kBTile) >> 4);
             const uint32_t first = (fresh >> acc) & 1u;
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk)
-              tc::mma_bf16(d, ad + 2 * kk, bt + 2 * kk, idesc, (first && kk == 0) ? 0u : 1u);
+            for (int kk = 0; kk < kRowBytes / 32; ++kk) {
+              const uint32_t accum = (first && kk == 0) ? 0u : 1u;
+              if (FORM == kFormFP8) tc::mma_f8(d, ad + 2 * kk, bt + 2 * kk, idesc, accum);
+              else tc::mma_bf16(d, ad + 2 * kk, bt + 2 * kk, idesc, accum);
+            }
             fresh &= ~(1u << acc);
           }
           tc::mma_commit(&aempty[sa]);
@@ -492,7 +538,18 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         for (int g = 0; g < HALF / 8; ++g) {
           float v[8];
           tc::tmem_ld8(tmem + lane_off + a * BN + half * HALF + g * 8, v);
-          if (F16) {
+          if (FORM == kFormFP8) {
+            // raw integer level sums (|.| <= 2^24): levels 2..9 into 2^-48 units
+            // (level 2 of a 4096-chunk is below 2^20: 2^58 per chunk, so about
+            // 29 chunks fit); levels 10..13 into one float in units of 2^-65
+            // (times 2^(65 - 5L), exact)
+            const int L = a + 2;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              if (L <= 9) iacc[g * 8 + i] += (long long)__float2int_rn(v[i]) << (48 - 5 * L);
+              else fm[g * 8 + i] += v[i] * __int_as_float((127 + 65 - 5 * L) << 23);
+            }
+          } else if (FORM == kFormFP16) {
             // raw integer level sums (|.| <= 2^24): levels 2..7 into 2^-49 units;
             // levels 8 and 9 into one float in units of 2^-56 (level 9 times
             // 2^-7, exact), whose rounding lies about 2^-56 below the leading level
@@ -537,7 +594,9 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
             // one conversion; the power of two 2^(e_i + f_j - 48) goes into the
             // exponent field (FP64 arithmetic is scarce on this part)
             double v;
-            if (F16)
+            if (FORM == kFormFP8)
+              v = pow2_scale(fma((double)fm[j], 0x1p-17, (double)iacc[j]), ei + __ldg(ebb + j) - 48);
+            else if (FORM == kFormFP16)
               v = pow2_scale(fma((double)fm[j], 0x1p-7, (double)iacc[j]), ei + __ldg(ebb + j) - 49);
             else
               v = pow2_scale(fma((double)fm[j], 0x1p48, (double)iacc[j]), ei + __ldg(ebb + j) - 48);
@@ -586,17 +645,21 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// 2-D map over a (rows x K_pad) BF16 or FP16 matrix, K contiguous, box 64 x box_rows,
+// 2-D map over a (rows x K_pad) matrix of the form's slice type, K contiguous,
+// box of one 128-byte row (64 16-bit or 128 one-byte elements) x box_rows,
 // 128-byte swizzle
-bool make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t K_pad, int box_rows,
-              bool f16) {
+template <int FORM>
+bool make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t K_pad, int box_rows) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return false;
   cuuint64_t dims[2] = {(cuuint64_t)K_pad, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)K_pad * 2};
-  cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
+  cuuint64_t strides[1] = {(cuuint64_t)K_pad * Form<FORM>::kElem};
+  cuuint32_t box[2] = {(cuuint32_t)form_bk<FORM>(), (cuuint32_t)box_rows};
   cuuint32_t es[2] = {1, 1};
-  return enc(m, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+  const CUtensorMapDataType ty = FORM == kFormFP8    ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                 : FORM == kFormFP16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                     : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  return enc(m, ty, 2,
              const_cast<void*>(base), dims, strides, box, es,
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
@@ -604,9 +667,9 @@ bool make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t K_pad, int
 
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
-template <int S, bool F16>
+template <int S, int FORM>
 cudaError_t slice_operand(const double* X, int64_t ldx, int64_t strideX, int trans, int rows, int K,
-                          int batch, int* e, __nv_bfloat16* out, int rows_pad, int K_pad,
+                          int batch, int* e, uint8_t* out, int rows_pad, int K_pad,
                           const int* ek, int esign, cudaStream_t st) {
   {
     ProfScope ps(kProfSlice, st, 0.0, 8.0 * batch * rows * (double)K);
@@ -617,27 +680,31 @@ cudaError_t slice_operand(const double* X, int64_t ldx, int64_t strideX, int tra
       row_exp_kernel<<<dim3((rows_pad + 7) / 8, 1, batch), dim3(32, 8), 0, st>>>(
           X, ldx, strideX, 1, rows, K, e, rows_pad, ek, esign, K_pad);
   }
-  ProfScope ps(kProfSlice, st, 0.0, (8.0 + 2.0 * S) * batch * rows_pad * (double)K_pad);
+  ProfScope ps(kProfSlice, st, 0.0,
+               (8.0 + (double)Form<FORM>::kElem * S) * batch * rows_pad * (double)K_pad);
   dim3 grid((unsigned)(K_pad / 64), (unsigned)(rows_pad / 32), batch);
-  slice_kernel<S, F16><<<grid, dim3(32, 8), 0, st>>>(X, ldx, strideX, trans, rows, K, e, out,
-                                                     rows_pad, K_pad, ek, esign);
+  slice_kernel<S, FORM><<<grid, dim3(32, 8), 0, st>>>(X, ldx, strideX, trans, rows, K, e, out,
+                                                      rows_pad, K_pad, ek, esign);
   return cudaGetLastError();
 }
 
-template <int BN, int S, bool F16>
+template <int BN, int S, int FORM>
 cudaError_t run_split(const GemmArgs& g, SplitWork& w, cudaStream_t st) {
+  constexpr int kE = Form<FORM>::kElem;
   // orientation: put the larger output dimension on the 128-row tile side
   const bool swap = g.M < kTileM && g.N > g.M;
   const int M = swap ? g.N : g.M, N = swap ? g.M : g.N, K = g.K;
-  const int Mpad = (int)round_up(M, kTileM), Npad = (int)round_up(N, BN), Kpad = (int)round_up(K, kBK);
+  const int Mpad = (int)round_up(M, kTileM), Npad = (int)round_up(N, BN),
+            Kpad = (int)round_up(K, form_bk<FORM>());
   const int nb = g.batch;
   const size_t need_a = (size_t)nb * S * Mpad * Kpad, need_b = (size_t)nb * S * Npad * Kpad;
   const bool keq = g.k_equilibrate != 0;
-  if (need_a + need_b > w.slice_elems ||
+  // the workspace counts 16-bit units
+  if ((need_a + need_b) * kE > w.slice_elems * 2 ||
       (size_t)nb * (Mpad + Npad + (keq ? Kpad : 0)) > w.exp_elems)
     return cudaErrorMemoryAllocation;
-  __nv_bfloat16* sa = static_cast<__nv_bfloat16*>(w.slices);
-  __nv_bfloat16* sb = sa + need_a;
+  uint8_t* sa = static_cast<uint8_t*>(w.slices);
+  uint8_t* sb = sa + need_a * kE;
   int* ea = w.exps;
   int* eb = w.exps + (size_t)nb * Mpad;
   int* ek = keq ? eb + (size_t)nb * Npad : nullptr;
@@ -662,15 +729,15 @@ cudaError_t run_split(const GemmArgs& g, SplitWork& w, cudaStream_t st) {
         Xo, swap ? lda : ldb, swap ? sta : stb, swap ? ta : tb, swap ? M : N, K, ek, Kpad);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
-  if ((err = slice_operand<S, F16>(Xa, lda, sta, ta, M, K, nb, ea, sa, Mpad, Kpad, ek, sign_a,
-                                   st)) != cudaSuccess)
+  if ((err = slice_operand<S, FORM>(Xa, lda, sta, ta, M, K, nb, ea, sa, Mpad, Kpad, ek, sign_a,
+                                    st)) != cudaSuccess)
     return err;
-  if ((err = slice_operand<S, F16>(Xb, ldb, stb, tb, N, K, nb, eb, sb, Npad, Kpad, ek, -sign_a,
-                                   st)) != cudaSuccess)
+  if ((err = slice_operand<S, FORM>(Xb, ldb, stb, tb, N, K, nb, eb, sb, Npad, Kpad, ek, -sign_a,
+                                    st)) != cudaSuccess)
     return err;
   CUtensorMap mA, mB;
-  if (!make_map(&mA, sa, (int64_t)nb * S * Mpad, Kpad, kTileM, F16) ||
-      !make_map(&mB, sb, (int64_t)nb * S * Npad, Kpad, BN, F16))
+  if (!make_map<FORM>(&mA, sa, (int64_t)nb * S * Mpad, Kpad, kTileM) ||
+      !make_map<FORM>(&mB, sb, (int64_t)nb * S * Npad, Kpad, BN))
     return cudaErrorInvalidValue;
   SplitEpi p{};
   p.C = g.Cout; p.ldc = g.ldcout; p.strideC = g.strideCout;
@@ -683,7 +750,7 @@ cudaError_t run_split(const GemmArgs& g, SplitWork& w, cudaStream_t st) {
   p.stall = w.stall;
   p.stall_ns = w.stall_ns;
   using L = SmemLayout<BN, S>;
-  if ((err = smem_attr_once((const void*)split_gemm_kernel<BN, S, F16>, L::kAlloc)) != cudaSuccess) {
+  if ((err = smem_attr_once((const void*)split_gemm_kernel<BN, S, FORM>, L::kAlloc)) != cudaSuccess) {
     if (std::getenv("ZOLO_DEBUG"))
       std::fprintf(stderr, "zolo: cudaFuncSetAttribute(%d B): %s\n", L::kAlloc,
                    cudaGetErrorString(err));
@@ -691,11 +758,11 @@ cudaError_t run_split(const GemmArgs& g, SplitWork& w, cudaStream_t st) {
   }
   dim3 grid((unsigned)(Npad / BN), (unsigned)(Mpad / kTileM), g.reduce ? 1 : nb);
   ProfScope ps(kProfSplitGemm, st, gemm_flops(g), 0.0);
-  split_gemm_kernel<BN, S, F16><<<grid, kThreads, L::kAlloc, st>>>(mA, mB, p);
+  split_gemm_kernel<BN, S, FORM><<<grid, kThreads, L::kAlloc, st>>>(mA, mB, p);
   err = cudaGetLastError();
   if (err != cudaSuccess && std::getenv("ZOLO_DEBUG")) {
     cudaFuncAttributes fa{};
-    cudaFuncGetAttributes(&fa, split_gemm_kernel<BN, S, F16>);
+    cudaFuncGetAttributes(&fa, split_gemm_kernel<BN, S, FORM>);
     std::fprintf(stderr,
                  "zolo: split_gemm_kernel<%d,%d> launch (grid %u x %u x %u, %d threads, %d B smem): %s"
                  " [maxThreadsPerBlock %d, numRegs %d, localSizeBytes %zu, maxDynamicSmem %d]\n",
@@ -712,14 +779,16 @@ cudaError_t gemm_split(const GemmArgs& g, SplitWork& w, cudaStream_t st) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
   if (g.K <= 0 || g.batch > kGemmMaxBatch) return gemm_f64(g, st);
   // batch entries per launch that the slice workspace and the exponent array hold
-  const size_t per = split_slice_elems(g.M, g.N, g.K, 1, w.slices_s);
-  const size_t rows = split_exp_elems(g.M, g.N, g.K, 1, g.k_equilibrate);
+  const size_t per = split_slice_elems(g.M, g.N, g.K, 1, w.slices_s, w.form);
+  const size_t rows = split_exp_elems(g.M, g.N, g.K, 1, g.k_equilibrate, w.form);
   int gs = (int)std::min<size_t>(g.batch, w.slice_elems / std::max<size_t>(per, 1));
   gs = (int)std::min<size_t>((size_t)gs, w.exp_elems / std::max<size_t>(rows, 1));
   if (gs < 1) return cudaErrorMemoryAllocation;
   auto run = [&](const GemmArgs& h) {
-    if (w.fp16) return run_split<64, 8, true>(h, w, st);
-    return w.slices_s == 9 ? run_split<64, 9, false>(h, w, st) : run_split<64, 8, false>(h, w, st);
+    if (w.form == kFormFP8) return run_split<Form<kFormFP8>::kBN, 11, kFormFP8>(h, w, st);
+    if (w.form == kFormFP16) return run_split<64, 8, kFormFP16>(h, w, st);
+    return w.slices_s == 9 ? run_split<64, 9, kFormBF16>(h, w, st)
+                           : run_split<64, 8, kFormBF16>(h, w, st);
   };
   if (gs >= g.batch) return run(g);
   for (int b0 = 0; b0 < g.batch; b0 += gs) {
@@ -741,9 +810,11 @@ cudaError_t gemm_split(const GemmArgs& g, SplitWork& w, cudaStream_t st) {
 }
 
 void split_prepare() {
-  smem_attr_once((const void*)split_gemm_kernel<64, 8, false>, SmemLayout<64, 8>::kAlloc);
-  smem_attr_once((const void*)split_gemm_kernel<64, 9, false>, SmemLayout<64, 9>::kAlloc);
-  smem_attr_once((const void*)split_gemm_kernel<64, 8, true>, SmemLayout<64, 8>::kAlloc);
+  smem_attr_once((const void*)split_gemm_kernel<64, 8, kFormBF16>, SmemLayout<64, 8>::kAlloc);
+  smem_attr_once((const void*)split_gemm_kernel<64, 9, kFormBF16>, SmemLayout<64, 9>::kAlloc);
+  smem_attr_once((const void*)split_gemm_kernel<64, 8, kFormFP16>, SmemLayout<64, 8>::kAlloc);
+  smem_attr_once((const void*)split_gemm_kernel<Form<kFormFP8>::kBN, 11, kFormFP8>,
+                 SmemLayout<Form<kFormFP8>::kBN, 11>::kAlloc);
   encode_fn();
 }
 
@@ -757,50 +828,66 @@ SplitWork* get_split_engine() { return t_split; }
 // launch latency).
 bool split_preferred(const GemmArgs& g, const SplitWork& w) { return split_time_ratio(g, w) < 1.0; }
 
+namespace {
+// The padded tile sides, slice bytes per element and slice-pair products (in
+// 16-bit-MMA equivalents: FP8 runs at twice the rate) of one call in a form.
+struct SplitShape {
+  double ra, rb, kp, elem_bytes, pairs;
+};
+SplitShape split_shape(const GemmArgs& g, const SplitWork& w) {
+  const bool swap = g.M < kTileM && g.N > g.M;
+  const bool fp8 = w.form == kFormFP8;
+  const double S = w.slices_s;
+  SplitShape sh;
+  sh.ra = (double)round_up(swap ? g.N : g.M, kTileM);
+  sh.rb = (double)round_up(swap ? g.M : g.N, fp8 ? Form<kFormFP8>::kBN : 64);
+  sh.kp = (double)round_up(g.K, fp8 ? form_bk<kFormFP8>() : form_bk<kFormBF16>());
+  sh.elem_bytes = fp8 ? 1.0 : 2.0;
+  // slice pairs: s + t <= S + 2 (BF16, FP8), s + t <= S + 1 (FP16)
+  const double pairs = w.form == kFormFP16 ? S * (S + 1) / 2 : S * (S + 1) / 2 + (S - 1);
+  sh.pairs = fp8 ? pairs / 2 : pairs;
+  return sh;
+}
+}  // namespace
+
 double split_time_ratio(const GemmArgs& g, const SplitWork& w) {
+  const SplitShape sh = split_shape(g, w);
+  const double S = w.slices_s;
+  const double slice_bytes = g.batch * (8.0 + sh.elem_bytes * S) * (sh.ra + sh.rb) * sh.kp;
+  const double out_bytes = (g.reduce ? 1 : g.batch) * 8.0 * g.M * (double)g.N * (g.beta != 0.0 ? 2 : 1);
+  const double products = sh.pairs * 2.0 * sh.ra * sh.rb * sh.kp * g.batch;
   if (w.throughput) {
     // GPU-seconds of each path when other calls fill the rest of the chip: the
     // FP64 pipe at its measured 1.2 TFLOP/s, the slice-pair products at 1.7 PFLOP/s
     // of BF16 issue, the slicing and output traffic at 6 TB/s
-    const bool swap = g.M < kTileM && g.N > g.M;
-    const double ra = (double)round_up(swap ? g.N : g.M, kTileM);
-    const double rb = (double)round_up(swap ? g.M : g.N, 64);
-    const double kp = (double)round_up(g.K, kBK);
-    const double S = w.slices_s;
-    const double bytes = g.batch * (8.0 + 2.0 * S) * (ra + rb) * kp +
-                         (g.reduce ? 1 : g.batch) * 8.0 * g.M * (double)g.N * (g.beta != 0.0 ? 2 : 1);
-    const double pairs = w.fp16 ? S * (S + 1) / 2 : S * (S + 1) / 2 + (S - 1);
-    const double tensor = pairs * 2.0 * ra * rb * kp * g.batch / 1.7e15;
-    return (bytes / 6e12 + tensor) / (gemm_flops(g) / 1.2e12);
+    return ((slice_bytes + out_bytes) / 6e12 + products / 1.7e15) / (gemm_flops(g) / 1.2e12);
   }
   const double t64 = gemm_flops(g) / 0.9e12;
-  const bool swap = g.M < kTileM && g.N > g.M;
-  const double ra = (double)round_up(swap ? g.N : g.M, kTileM);
-  const double rb = (double)round_up(swap ? g.M : g.N, 64);
-  const double kp = (double)round_up(g.K, kBK);
-  const double S = w.slices_s;
-  const double slice_bytes = g.batch * (8.0 + 2.0 * S) * (ra + rb) * kp;
-  const double out_bytes = (g.reduce ? 1 : g.batch) * 8.0 * g.M * (double)g.N * (g.beta != 0.0 ? 2 : 1);
-  // slice pairs: s + t <= S + 2 (BF16), s + t <= S + 1 (FP16)
-  const double pairs = w.fp16 ? S * (S + 1) / 2 : S * (S + 1) / 2 + (S - 1);
-  const double tensor = pairs * 2.0 * ra * rb * kp * g.batch / 0.7e15;
-  const double tsplit = slice_bytes / 4e12 + out_bytes / 5e12 + tensor + 30e-6;
+  const double tsplit = slice_bytes / 4e12 + out_bytes / 5e12 + products / 0.7e15 + 30e-6;
   return tsplit / t64;
 }
 
 // Exponents run_split writes: one per padded tile row and column of every batch
 // entry, plus one per padded inner index with the equilibration.
-size_t split_exp_elems(int64_t M, int64_t N, int64_t K, int batch, int k_equilibrate) {
+size_t split_exp_elems(int64_t M, int64_t N, int64_t K, int batch, int k_equilibrate, int form) {
   const bool swap = M < kTileM && N > M;
+  const bool fp8 = form == kFormFP8;
   const int64_t rows = swap ? N : M, cols = swap ? M : N;
-  return (size_t)batch *
-         (size_t)(round_up(rows, kTileM) + round_up(cols, 64) + (k_equilibrate ? round_up(K, kBK) : 0));
+  const int64_t bk = fp8 ? form_bk<kFormFP8>() : form_bk<kFormBF16>();
+  return (size_t)batch * (size_t)(round_up(rows, kTileM) + round_up(cols, fp8 ? Form<kFormFP8>::kBN : 64) +
+                                  (k_equilibrate ? round_up(K, bk) : 0));
 }
 
-size_t split_slice_elems(int64_t M, int64_t N, int64_t K, int batch, int S) {
+// Slice planes of one call, in 16-bit units (two FP8 slices per unit).
+size_t split_slice_elems(int64_t M, int64_t N, int64_t K, int batch, int S, int form) {
   const bool swap = M < kTileM && N > M;
+  const bool fp8 = form == kFormFP8;
   const int64_t rows = swap ? N : M, cols = swap ? M : N;
-  return (size_t)batch * S * (round_up(rows, kTileM) + round_up(cols, 64)) * round_up(K, kBK);
+  const int64_t bk = fp8 ? form_bk<kFormFP8>() : form_bk<kFormBF16>();
+  const size_t elems = (size_t)batch * S *
+                       (round_up(rows, kTileM) + round_up(cols, fp8 ? Form<kFormFP8>::kBN : 64)) *
+                       round_up(K, bk);
+  return fp8 ? (elems + 1) / 2 : elems;
 }
 
 }  // namespace zolo

@@ -141,6 +141,20 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64
       : "memory");
 }
 
+// D[tmem] (+)= A[smem] * B[smem]^T, kind::f8f6f4 with E4M3 inputs (K = 32 per
+// instruction, 32 bytes: the same descriptor step as one kind::f16 MMA).
+__device__ __forceinline__ void mma_f8(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                       uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n"
+      ".reg .pred p;\n"
+      "setp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n"
+      "}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
 // The mbarrier receives one arrival when all previously issued tcgen05.mma of
 // this thread have completed.
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -204,6 +218,13 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
 // The same with A = B = FP16 (type code 0 in bits 7-9 and 10-12; both operands
 // of one kind::f16 MMA have the same type).
 __host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Instruction descriptor, kind::f8f6f4: D = F32 (bits 4-5 = 1), A = B = E4M3
+// (type code 0 in bits 7-9 and 10-12), both K-major, N >> 3 (17-22), M >> 4
+// (24-28).
+__host__ __device__ constexpr uint32_t idesc_e4m3_f32(int M, int N) {
   return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 

@@ -146,8 +146,9 @@ int choose(const GemmArgs& g, SplitWork* split_engine, cudaStream_t st) {
   SplitWork* split = thr ? nullptr : split_engine;
   GemmTuner* t = t_tuner;
   if (t && !t->busy) {
-    // the split path's slice format in the key: S, plus 100 for FP16 digits
-    const auto key = gemm_key(g, split ? split->slices_s + (split->fp16 ? 100 : 0) : 0);
+    // the split path's slice format in the key: S, plus 100 per form (FP16 108,
+    // FP8 211)
+    const auto key = gemm_key(g, split ? split->slices_s + 100 * split->form : 0);
     const auto hit = t->choice.find(key);
     if (hit != t->choice.end() && gemm_variant_allowed(key, hit->second)) {
       // a split-K choice (e.g. loaded from a file) needs its partial sums' scratch

@@ -163,15 +163,20 @@ double gemm_flops(const GemmArgs& g);
 
 // --------------------------------------------------- split-precision GEMM
 // Same contract as gemm_f64 (c_upper / b_lower are computed in full), on the
-// BF16 tensor cores with S = 8 or 9 six-bit slices per operand.
+// tensor cores with the operands cut into S slices of one of three forms.
+enum : int {
+  kFormBF16 = 0,   // S = 8 or 9 pre-scaled base-64 digits in BF16
+  kFormFP16 = 1,   // S = 8 raw base-128 digits in FP16
+  kFormFP8 = 2     // S = 11 raw base-32 digits in E4M3
+};
 struct SplitWork {
-  void* slices;          // BF16 slice planes
-  size_t slice_elems;
+  void* slices;          // slice planes
+  size_t slice_elems;    // their size in 16-bit units
   int* exps;             // per-row / per-column power-of-two exponents
   size_t exp_elems;
   int* err;              // device error flag (bounded waits)
   int slices_s;          // S
-  int fp16 = 0;          // 1: FP16 raw base-128 digits (S = 8), else BF16 pre-scaled base-64 digits
+  int form = kFormBF16;
   // test hook of the failure path: with stall = 1 the MMA issuer first waits,
   // for stall_ns, on an mbarrier that nothing arrives at, then takes the
   // bounded-wait error exit
@@ -184,10 +189,11 @@ struct SplitWork {
   bool throughput = false;
 };
 cudaError_t gemm_split(const GemmArgs& g, SplitWork& w, cudaStream_t st);
-// slice elements one call of the given shape needs
-size_t split_slice_elems(int64_t M, int64_t N, int64_t K, int batch, int S);
+// slice planes (16-bit units) one call of the given shape needs in a form
+size_t split_slice_elems(int64_t M, int64_t N, int64_t K, int batch, int S, int form = kFormBF16);
 // exponent entries (ints) one call of the given shape needs
-size_t split_exp_elems(int64_t M, int64_t N, int64_t K, int batch, int k_equilibrate);
+size_t split_exp_elems(int64_t M, int64_t N, int64_t K, int batch, int k_equilibrate,
+                       int form = kFormBF16);
 // The engine every contraction of the current call goes through: FP64 (DFMA)
 // when no split workspace is installed, the split tensor-core path otherwise.
 void set_split_engine(SplitWork* w);

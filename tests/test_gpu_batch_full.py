@@ -1,6 +1,6 @@
 """The benchmark's own batch at its full size: the 512 square matrices (n from 64
 to 1024, kappa log-uniform in [1e2, 1e12], r from Table 1's rule) in one
-zolo_pd_batched call, FP64 and both split forms.  Every result meets the
+zolo_pd_batched call, FP64 and the three split forms.  Every result meets the
 invariants the contract fixes (backward error and orthogonality <= 1e-13, H
 exactly symmetric); the members the CPU oracle decomposes in seconds (n <= 128)
 (n = 64) are compared with it entry by entry: H to 1e-13 of its norm, Qp within the
@@ -36,7 +36,7 @@ def batch():
     return mats, [torch.from_numpy(sm.A).cuda() for sm in mats]
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
 def test_full_batch_meets_the_bar_and_matches_the_oracle(zb, batch, prec):
     import torch
     mats, As = batch

@@ -146,10 +146,11 @@ def test_batched_estimates_beta_as_the_single_call_does(zb, handle):
 
 
 def test_batched_split_precision_invariants(zb, handle):
-    # BF16 and FP16 slices side by side in one batch
-    shapes = [(256, 256), (192, 128), (128, 128), (600, 300)]
-    mats = _case(shapes, [1e8, 1e3, 1e14, 1e10], 300)
-    precs = [zb.ZOLO_SPLIT_BF16, zb.ZOLO_SPLIT_FP16, zb.ZOLO_SPLIT_BF16, zb.ZOLO_SPLIT_FP16]
+    # BF16, FP16 and FP8 slices side by side in one batch
+    shapes = [(256, 256), (192, 128), (128, 128), (600, 300), (320, 200)]
+    mats = _case(shapes, [1e8, 1e3, 1e14, 1e10, 1e12], 300)
+    precs = [zb.ZOLO_SPLIT_BF16, zb.ZOLO_SPLIT_FP16, zb.ZOLO_SPLIT_FP8, zb.ZOLO_SPLIT_FP16,
+             zb.ZOLO_SPLIT_FP8]
     os = [zb.opts(beta=0.9 * sm.sigma.min() / sm.sigma.max(), alpha=sm.sigma.max(),
                   prec=p) for sm, p in zip(mats, precs)]
     As = [dev(sm.A) for sm in mats]

@@ -3,7 +3,8 @@
 The BF16 form's product of S six-bit slices per operand carries an error of at
 most about 2 K 2^-6S max_k|A_ik| max_k|B_kj| per entry (truncation of each
 operand after S digits); the FP16 form's eight seven-bit slices (36 slice pairs)
-reach the same grade as nine BF16 slices.  Integer matrices whose digits fit are
+and the FP8 form's eleven five-bit slices (76 slice pairs) reach the same
+grade as nine BF16 slices.  Integer matrices whose digits fit are
 multiplied exactly.  The full decomposition in either split form must meet the
 same invariants as FP64."""
 import math
@@ -46,7 +47,7 @@ def opnp(X, t):
 
 @pytest.mark.parametrize("m,n,k,ta,tb", [(64, 64, 64, 0, 0), (200, 130, 300, 0, 1), (33, 257, 1100, 1, 0),
                                          (129, 65, 2100, 1, 1), (1, 5, 7, 0, 0), (300, 16, 40, 0, 0)])
-@pytest.mark.parametrize("prec,S", [(0, 0), (1, 8), (1, 9), (2, 8)])
+@pytest.mark.parametrize("prec,S", [(0, 0), (1, 8), (1, 9), (2, 8), (3, 11)])
 def test_dgemm_matches_numpy(zb, handle, m, n, k, ta, tb, prec, S):
     rng = np.random.default_rng(m * 7 + n + k)
     A = rng.standard_normal((k, m) if ta else (m, k)) * np.exp(rng.uniform(-3, 3, (1, 1)))
@@ -63,26 +64,27 @@ def test_dgemm_matches_numpy(zb, handle, m, n, k, ta, tb, prec, S):
     else:
         amax = np.max(np.abs(opnp(A, ta)), axis=1, keepdims=True)
         bmax = np.max(np.abs(opnp(B, tb)), axis=0, keepdims=True)
-        bits = 6 * S if prec == 1 else 54   # FP16: the grade of nine BF16 slices
+        bits = 6 * S if prec == 1 else 54   # FP16, FP8: the grade of nine BF16 slices
         tol = 2.0 * k * 2.0 ** (-bits) * abs(alpha) * amax * bmax * 4 + 1e-15 * np.abs(ref) + 1e-300
     assert np.all(np.abs(got - ref) <= tol), np.max(np.abs(got - ref) / tol)
 
 
-@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("prec", [1, 2, 3])
 def test_split_integer_products_are_exact(zb, handle, prec):
-    # entries with one digit (|d| < 64 after the row scale): every slice product is
-    # an integer sum below 2^24 within a chunk, so the tensor-core result is exact
+    # entries of at most two digits (|x| < 64: one base-64 or base-128 digit, two
+    # base-32 ones, after the row scale): every slice product is an integer sum
+    # below 2^24 within a chunk and no level is dropped, so the result is exact
     rng = np.random.default_rng(5)
     A = rng.integers(-63, 64, (256, 1024)).astype(np.float64)
     B = rng.integers(-63, 64, (1024, 192)).astype(np.float64)
-    C = zb.zolo_dgemm(handle, dev(A), dev(B), prec=prec, slices=8)
+    C = zb.zolo_dgemm(handle, dev(A), dev(B), prec=prec, slices=8 if prec < 3 else 0)
     assert np.array_equal(C.cpu().numpy(), A @ B)
 
 
 @pytest.mark.parametrize("m,n,kappa,r,form", [(256, 256, 1e8, 3, 1), (300, 160, 1e6, 6, 1),
                                               (384, 384, 1e12, 8, 1), (384, 384, 1e12, 8, 2),
                                               (800, 200, 1e6, 6, 0)])
-@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("prec", [1, 2, 3])
 def test_split_pd_meets_invariants_and_matches_oracle(zb, handle, m, n, kappa, r, form, prec):
     # form 2 / the 800 x 200 auto case: Cholesky-form iterations through W = sum_j a_j Z_j^{-1}
     sm = synth.make_matrix(m, n, synth.geometric_sigma(n, kappa), seed=3100 + m)
@@ -99,7 +101,7 @@ def test_split_pd_meets_invariants_and_matches_oracle(zb, handle, m, n, kappa, r
     assert np.linalg.norm(H - Ho) <= 1e-13 * np.linalg.norm(Ho)
 
 
-@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("prec", [1, 2, 3])
 def test_split_svd_sigma(zb, handle, prec):
     sm = synth.square_geometric(256, 1e8, seed=1000)
     U, S, V, info = zb.zolo_svd(handle, dev(sm.A), zb.opts(beta=1e-8, r=3, prec=prec,

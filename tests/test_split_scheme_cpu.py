@@ -207,3 +207,96 @@ def test_fp16_form_without_level_9_is_worse(operands):
     keep = np.max(np.abs(split_product_fp16(A, B, max_level=9) - ref) / scale)
     drop = np.max(np.abs(split_product_fp16(A, B, max_level=8) - ref) / scale)
     assert drop > 4 * keep
+
+
+# ---- the FP8 (E4M3) form: E4M3 holds every integer |d| <= 16 exactly but nothing
+# pre-scaled below 2^-9, so its slices are raw balanced base-32 digits
+# (|d| <= 16), S = 11 slices (55 bits), levels L = s + t <= S + 2 = 13 (76 slice
+# pairs), one accumulator per level, K-chunks of 4096; the epilogue adds levels
+# 2..9 to an int64 of 2^-48 units and levels 10..13 to one FP32 of 2^-65 units,
+# joined as iacc + f 2^-17.
+
+def split_product_fp8(A, B, S=11, max_level=13, chunk=4096):
+    """The FP8 form's arithmetic, joined as the kernel joins it."""
+    beta = 5
+    ea = exponents(A, axis=1)
+    eb = exponents(B, axis=0)
+    da = digits_base(A, ea[:, None], S, beta)
+    db = digits_base(B, eb[None, :], S, beta)
+    M, N, K = A.shape[0], B.shape[1], A.shape[1]
+    iacc = np.zeros((M, N), dtype=object)
+    fm = np.zeros((M, N), dtype=np.float32)
+    for k0 in range(0, K, chunk):
+        ks = slice(k0, min(K, k0 + chunk))
+        for L in range(2, max_level + 1):
+            lv = np.zeros((M, N), dtype=object)
+            for s in range(1, S + 1):
+                t = L - s
+                if 1 <= t <= S:
+                    lv = lv + da[s - 1][:, ks].dot(db[t - 1][ks, :])
+            assert max(abs(int(v)) for v in lv.ravel()) <= 2 ** 24
+            if L <= 9:
+                iacc = iacc + lv * (2 ** (48 - 5 * L))
+            else:   # the FP32 integer times 2^(65 - 5L), exact, added in FP32
+                v = np.vectorize(float)(lv).astype(np.float32)
+                fm = (fm + v * np.float32(2.0 ** (65 - 5 * L))).astype(np.float32)
+        assert max(abs(int(v)) for v in iacc.ravel()) < 2 ** 63
+    C = np.empty((M, N))
+    for i in range(M):
+        for j in range(N):
+            v = float(iacc[i, j]) + float(fm[i, j]) * 2.0 ** -17
+            C[i, j] = math.ldexp(v, int(ea[i] + eb[j]) - 48)
+    return C
+
+
+def test_fp8_form_is_fp64_grade(operands):
+    A, B = operands
+    K = A.shape[1]
+    C = split_product_fp8(A, B)
+    ref = exact_product(A, B)
+    scale = np.max(np.abs(A), axis=1)[:, None] * np.max(np.abs(B), axis=0)[None, :]
+    err = np.max(np.abs(C - ref) / scale)
+    assert err <= 8 * math.sqrt(K) * 2.0 ** -54
+    assert err <= 2e-16 * math.sqrt(K)
+
+
+def test_fp8_form_keeps_level_13():
+    # with levels <= S + 1 only, the dropped level-13 pairs dominate the error
+    rng = np.random.default_rng(15)
+    A = rng.standard_normal((6, 200))
+    B = rng.standard_normal((200, 5))
+    ref = exact_product(A, B)
+    scale = np.max(np.abs(A), axis=1)[:, None] * np.max(np.abs(B), axis=0)[None, :]
+    e_keep = np.max(np.abs(split_product_fp8(A, B) - ref) / scale)
+    e_drop = np.max(np.abs(split_product_fp8(A, B, max_level=12) - ref) / scale)
+    assert e_drop > 2 * e_keep
+    assert sum(1 for s in range(1, 12) for t in range(1, 12) if s + t <= 13) == 76
+
+
+def test_fp8_digits_are_exact_in_e4m3():
+    torch = pytest.importorskip("torch")
+    if not hasattr(torch, "float8_e4m3fn"):
+        pytest.skip("no E4M3 dtype in this torch")
+    d = torch.arange(-16, 17, dtype=torch.float32)
+    assert torch.equal(d.to(torch.float8_e4m3fn).to(torch.float32), d)
+    assert torch.float8_e4m3fn is not None and float(torch.tensor(17.0).to(torch.float8_e4m3fn)) != 17.0
+    rng = np.random.default_rng(16)
+    X = rng.standard_normal((5, 64)) * 10.0 ** rng.uniform(-20, 20, (5, 1))
+    for dg in digits_base(X, exponents(X, axis=1)[:, None], 11, 5):
+        assert max(abs(int(v)) for v in dg.ravel()) <= 16
+
+
+def test_fp8_form_level_sums_exact_over_a_4096_chunk():
+    # |d| <= 16: a level of p <= 11 pairs over 4096 terms stays within 2^24
+    for level in range(2, 14):
+        p = min(level - 1, 11, 23 - level)
+        assert p * 4096 * 16 * 16 <= 2 ** 24
+    # the int64 of 2^-48 units: levels 2..9 of one chunk at the digit bound stay
+    # below 2^58.1, so about 29 chunks (K ~ 110000) fit
+    per_chunk = sum(min(L - 1, 11) * 4096 * 256 * 2 ** (48 - 5 * L) for L in range(2, 10))
+    assert 29 * per_chunk < 2 ** 63
+    # the model's own accumulators (checked inside) at the digit bound over two chunks
+    A = np.full((1, 8192), 0.4999)
+    B = np.full((8192, 1), -0.4999)
+    C = split_product_fp8(A, B)
+    assert abs(C[0, 0] - exact_product(A, B)[0, 0]) <= 8192 * 2.0 ** -52
