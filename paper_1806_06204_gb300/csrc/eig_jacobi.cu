@@ -16,10 +16,13 @@
 // barrier).  Z is then made orthonormal in FP64 (Cholesky QR), X = R^T Z is
 // formed in FP64, and FP64 sweeps (one launch per round, one CTA per column
 // pair) finish from cosines ~1e-5 in a few quadratically convergent sweeps.
-// FP32 sweeps stop when no cosine exceeds 8e-6 (25 sweeps at most).  FP64 sweeps
-// stop when no pair has |x_p . x_q| > 8 eps ||x_p|| ||x_q||, or once two sweeps
-// have started with every cosine below sqrt(n) eps (the rounding level of an
-// n-term dot product).
+// FP32 sweeps stop when fewer than n rotations (cosines above 8e-6) were needed
+// in a sweep (25 sweeps at most): the FP64 sweeps start from cosines of about
+// 1e-4 whatever the last FP32 sweeps do, since Z's FP32 rounding, times R^T,
+// sets them.  FP64 sweeps stop when no pair has |x_p . x_q| > 8 eps ||x_p||
+// ||x_q||, or after a sweep in which every cosine was below sqrt(n) eps (the
+// rounding level of an n-term dot product): its rotations were of that size,
+// so the next sweep would find the same rounding-level cosines again.
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
@@ -590,7 +593,7 @@ int eig_sym_jacobi(const double* H, int64_t ldh, int64_t n, double* V, int64_t l
         return 1;
       if (herr) return 3;
       ++total_sweeps;
-      if (rot == 0) break;
+      if (rot < n) break;
     }
   }
   // ---- Z orthonormal in FP64 (Cholesky QR: Z^T Z = R_z^T R_z, Z <- Z R_z^{-1})
@@ -622,7 +625,6 @@ int eig_sym_jacobi(const double* H, int64_t ldh, int64_t n, double* V, int64_t l
   // ---- FP64 sweeps
   const double tol_strict = 8.0 * kEps, tol_loose = sqrt((double)n) * kEps;
   bool converged = n == 1;
-  int quiet = 0;
   for (int sw = 0; sw < 40 && !converged; ++sw) {
     if (cudaMemsetAsync(w.status + kStatJacobiRot, 0, 2 * sizeof(int), st) != cudaSuccess) return 1;
     // fold the previous sweep's column scales in, then the squared column norms
@@ -646,7 +648,7 @@ int eig_sym_jacobi(const double* H, int64_t ldh, int64_t n, double* V, int64_t l
     float maxcos;
     memcpy(&maxcos, &rs[1], sizeof(float));
     if (rs[0] == 0) converged = true;
-    else if (maxcos <= tol_loose && ++quiet >= 2) converged = true;
+    else if (maxcos <= tol_loose) converged = true;
   }
   *sweeps = total_sweeps;
   if (!converged) return 2;

@@ -1,6 +1,6 @@
 """Time one building-block GEMM of libzolo: C = op(A) op(B) in FP64 (DFMA) or
-split precision (nine BF16 or eight FP16 slices on the tensor cores), through
-zolo_dgemm.
+split precision (nine BF16, eight FP16 or eleven FP8 slices on the tensor cores),
+through zolo_dgemm.
 
     python -m paper_1806_06204_gb300.profile_gemm --m 4096 --n 4096 --k 4096 --prec split
 
@@ -9,7 +9,8 @@ CUDA events on the current stream.  `--tune-cache F`: the FP64 kernel comes
 from the tuning file F when it holds this shape; otherwise the warm-up call
 measures the candidates (zolo_autotune) and F is written with the choice.  Prints one JSON line: milliseconds per
 call, FP64-equivalent TFLOP/s (2MNK per call), and for the split path the BF16
-tensor TFLOP/s actually issued (53 or 36 slice-pair products).  Also the launch
+tensor TFLOP/s actually issued (53, 36 or 76 slice-pair products; FP8 at twice
+the rate).  Also the launch
 target for kernel profilers: each call is one row-exponent + slicing pass per
 operand and one GEMM kernel (split), or one GEMM kernel (FP64).
 """
@@ -27,7 +28,7 @@ def main():
     ap.add_argument("--n", type=int, default=4096)
     ap.add_argument("--k", type=int, default=4096)
     ap.add_argument("--prec", choices=["fp64", "split"], default="split")
-    ap.add_argument("--slices", choices=["bf16", "fp16"], default="bf16")
+    ap.add_argument("--slices", choices=["bf16", "fp16", "fp8"], default="bf16")
     ap.add_argument("--transA", action="store_true")
     ap.add_argument("--transB", action="store_true")
     ap.add_argument("--reps", type=int, default=3)
@@ -42,8 +43,8 @@ def main():
     A = torch.randn(shape_a[::-1], dtype=torch.float64, device="cuda", generator=g).t()
     B = torch.randn(shape_b[::-1], dtype=torch.float64, device="cuda", generator=g).t()
     C = zb.empty_colmajor(args.m, args.n)
-    prec = ((zb.ZOLO_SPLIT_FP16 if args.slices == "fp16" else zb.ZOLO_SPLIT_BF16)
-            if args.prec == "split" else zb.ZOLO_FP64)
+    prec = ({"bf16": zb.ZOLO_SPLIT_BF16, "fp16": zb.ZOLO_SPLIT_FP16,
+             "fp8": zb.ZOLO_SPLIT_FP8}[args.slices] if args.prec == "split" else zb.ZOLO_FP64)
     h = zb.Handle(torch.cuda.current_device())
     if args.tune_cache:
         import os
@@ -53,7 +54,7 @@ def main():
 
     def call():
         zb.zolo_dgemm(h, A, B, C, transA=args.transA, transB=args.transB, prec=prec,
-                      slices=8 if args.slices == "fp16" else 9)
+                      slices={"bf16": 9, "fp16": 8, "fp8": 11}[args.slices])
 
     call()
     torch.cuda.synchronize()
@@ -79,8 +80,9 @@ def main():
     out = {"m": args.m, "n": args.n, "k": args.k, "prec": args.prec, "ms_per_call": ms,
            "fp64_equiv_tflops": flops / ms / 1e9}
     if args.prec == "split":
-        # slice-pair products issued: 53 (nine BF16 slices), 36 (eight FP16 slices)
-        pairs = 36 if args.slices == "fp16" else 53
+        # slice-pair products issued: 53 (nine BF16 slices), 36 (eight FP16
+        # slices), 76 (eleven FP8 slices, whose peak is twice the 16-bit one)
+        pairs = {"bf16": 53, "fp16": 36, "fp8": 76}[args.slices]
         out["slices"] = args.slices
         out["tensor_issued_tflops"] = pairs * flops / ms / 1e9
     if kernel:
