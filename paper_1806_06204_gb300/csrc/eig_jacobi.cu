@@ -52,10 +52,16 @@ __device__ __forceinline__ double warp_sum(double v) {
 // FP64 operations per row and pair instead of five (the FP64 pipe is the bound).
 // Near convergence c = 1 - O(t^2), so the scales stay within rounding of 1 over
 // a sweep; the caller folds them into the columns between sweeps.
+// An FP64 instruction occupies its sub-partition's FP64 unit for a whole warp
+// slot however few lanes are active, so the block's 256 partial dot products
+// are summed by one warp (7 + 5 warp instructions instead of 5 per warp plus 8
+// on one lane), and the warp that sums them and forms the rotation changes with
+// the block index: the scalar work spreads over the SM's four sub-partitions
+// instead of all landing on the one that holds warp 0.
 __global__ void __launch_bounds__(kJacThreads)
 jacobi_round_kernel(double* X, int64_t ldx, int64_t m, int n_even, int n_real, int round, double tol,
                     int* status, double* nrm2, double* dsc) {
-  __shared__ double red[kJacThreads / 32];
+  __shared__ double part[kJacThreads];
   __shared__ double s_al, s_be;
   __shared__ int s_rot;
   const int i = blockIdx.x;
@@ -67,46 +73,50 @@ jacobi_round_kernel(double* X, int64_t ldx, int64_t m, int n_even, int n_real, i
   double* xq = X + q * ldx;
   double g = 0.0;
   for (int64_t r = threadIdx.x; r < m; r += kJacThreads) g = fma(xp[r], xq[r], g);
-  g = warp_sum(g);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) red[w] = g;
+  part[threadIdx.x] = g;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    // One lane's scalar work costs whole FP64 warp instructions on this part, so
-    // only what fixes the rotation exactly is FP64: the cosine test and the angle
-    // are formed in FP32 (an angle off by 1e-7 only slows convergence by that
-    // factor), while c = (1 + t^2)^(-1/2) for the t actually applied, the norm
-    // and scale updates are FP64 (Newton steps from FP32 seeds).
-    double sg = 0.0;
-    for (int k = 0; k < kJacThreads / 32; ++k) sg += red[k];
-    const double dp = dsc[p], dq = dsc[q];
-    sg *= dp * dq;                                  // cross product of the true columns
-    const double sa = nrm2[p], sb = nrm2[q];
-    const float fa = (float)sa, fb = (float)sb;     // below float range: left as converged
-    const float cosv = (fa > 0.f && fb > 0.f) ? fabsf((float)sg) * rsqrtf(fa) * rsqrtf(fb) : 0.f;
-    atomicMax(status + kStatJacobiMaxCos, __float_as_int(cosv));
-    const int rot = (sg != 0.0) && (cosv > (float)tol);
-    if (rot) {
-      const float zeta = (float)((sb - sa) / (2.0 * sg));
-      const float az = fabsf(zeta);
-      const float tf = (az > 1e18f ? 0.5f / az : 1.f / (az + sqrtf(fmaf(az, az, 1.f))));
-      const double t = zeta >= 0.f ? (double)tf : -(double)tf;
-      const double x = fma(t, t, 1.0);
-      double c = (double)rsqrtf((float)x);
-      c = c * fma(-0.5 * x * c, c, 1.5);
-      c = c * fma(-0.5 * x * c, c, 1.5);
-      double rp = (double)(1.f / (float)dp), rq = (double)(1.f / (float)dq);
-      rp = rp * fma(-dp, rp, 2.0); rp = rp * fma(-dp, rp, 2.0);
-      rq = rq * fma(-dq, rq, 2.0); rq = rq * fma(-dq, rq, 2.0);
-      nrm2[p] = fma(-t, sg, sa);
-      nrm2[q] = fma(t, sg, sb);
-      dsc[p] = c * dp;
-      dsc[q] = c * dq;
-      s_al = t * (dq * rp);
-      s_be = t * (dp * rq);
-      atomicAdd(status + kStatJacobiRot, 1);
+  const int lead = blockIdx.x & (kJacThreads / 32 - 1);   // the warp that forms the rotation
+  if ((int)(threadIdx.x >> 5) == lead) {
+    const int l = threadIdx.x & 31;
+    double sg = part[l];
+#pragma unroll
+    for (int k = 1; k < kJacThreads / 32; ++k) sg += part[l + 32 * k];
+    sg = warp_sum(sg);
+    if (l == 0) {
+      // One lane's scalar work costs whole FP64 warp instructions on this part, so
+      // only what fixes the rotation exactly is FP64: the cosine test and the angle
+      // are formed in FP32 (an angle off by 1e-7 only slows convergence by that
+      // factor), while c = (1 + t^2)^(-1/2) for the t actually applied, the norm
+      // and scale updates are FP64 (Newton steps from FP32 seeds).
+      const double dp = dsc[p], dq = dsc[q];
+      sg *= dp * dq;                                  // cross product of the true columns
+      const double sa = nrm2[p], sb = nrm2[q];
+      const float fa = (float)sa, fb = (float)sb;     // below float range: left as converged
+      const float cosv = (fa > 0.f && fb > 0.f) ? fabsf((float)sg) * rsqrtf(fa) * rsqrtf(fb) : 0.f;
+      atomicMax(status + kStatJacobiMaxCos, __float_as_int(cosv));
+      const int rot = (sg != 0.0) && (cosv > (float)tol);
+      if (rot) {
+        const float zeta = (float)((sb - sa) / (2.0 * sg));
+        const float az = fabsf(zeta);
+        const float tf = (az > 1e18f ? 0.5f / az : 1.f / (az + sqrtf(fmaf(az, az, 1.f))));
+        const double t = zeta >= 0.f ? (double)tf : -(double)tf;
+        const double x = fma(t, t, 1.0);
+        double c = (double)rsqrtf((float)x);
+        c = c * fma(-0.5 * x * c, c, 1.5);
+        c = c * fma(-0.5 * x * c, c, 1.5);
+        double rp = (double)(1.f / (float)dp), rq = (double)(1.f / (float)dq);
+        rp = rp * fma(-dp, rp, 2.0); rp = rp * fma(-dp, rp, 2.0);
+        rq = rq * fma(-dq, rq, 2.0); rq = rq * fma(-dq, rq, 2.0);
+        nrm2[p] = fma(-t, sg, sa);
+        nrm2[q] = fma(t, sg, sb);
+        dsc[p] = c * dp;
+        dsc[q] = c * dq;
+        s_al = t * (dq * rp);
+        s_be = t * (dp * rq);
+        atomicAdd(status + kStatJacobiRot, 1);
+      }
+      s_rot = rot;
     }
-    s_rot = rot;
   }
   __syncthreads();
   if (!s_rot) return;

@@ -74,6 +74,7 @@ qr_panel_cluster_kernel(double* W, int64_t strideW, int64_t ldw, int64_t m, int6
   __shared__ double part[2][NB + 2];        // [0, NB): dots, NB: norm^2, NB+1: alpha
   __shared__ double red[kWarps][NB + 2];
   __shared__ double dots[NB];
+  __shared__ double cf[NB];                // -tau dots[q]: the update's coefficients
   __shared__ double Ts[NB][NB + 1];
   __shared__ double s_tau, s_scal, s_beta;
 
@@ -102,14 +103,21 @@ qr_panel_cluster_kernel(double* W, int64_t strideW, int64_t ldw, int64_t m, int6
       const double v = col[r];
       ss = fma(v, v, ss);
     }
-    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-    if (lane == 0) red[warp][0] = ss;
+    // the block's partials are summed by warp 0 (kWarps - 1 + 5 FP64 warp
+    // instructions; a butterfly in every warp would take 5 per warp, and an FP64
+    // instruction costs its unit a whole warp slot however few lanes it uses)
+    double* flat = &red[0][0];
+    flat[tid] = ss;
     __syncthreads();
-    if (tid == 0) {
-      double t = 0.0;
-      for (int w = 0; w < kWarps; ++w) t += red[w][0];
-      part[buf][NB] = t;
-      part[buf][NB + 1] = (c >= lo && c < hi) ? col[c] : 0.0;
+    if (warp == 0) {
+      double t = flat[lane];
+#pragma unroll
+      for (int w = 1; w < kWarps; ++w) t += flat[lane + 32 * w];
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) {
+        part[buf][NB] = t;
+        part[buf][NB + 1] = (c >= lo && c < hi) ? col[c] : 0.0;
+      }
     }
     cluster.sync();
     if (tid == 0) {
@@ -175,16 +183,20 @@ qr_panel_cluster_kernel(double* W, int64_t strideW, int64_t ldw, int64_t m, int6
       double t = 0.0;
       for (int rk = 0; rk < CG; ++rk) t += cluster.map_shared_rank(&part[buf][0], rk)[tid];
       dots[tid] = t;
+      cf[tid] = -tau * t;
     }
     __syncthreads();
     // ---- 4. my rows of the later panel columns: W[:, q] -= tau * dots[q] * v
+    //         (the coefficients formed once above: the stores through pq may
+    //         alias shared memory for the compiler, so a product written here
+    //         would be redone for every row)
     for (int64_t r = r0 + tid; r < r1; r += kT) {
       const double v = Vcol[r - c0];
 #pragma unroll
       for (int q = 0; q < NB; ++q) {
         if (q > i && q < nbp) {
           double* pq = Wj + r + (c0 + q) * ldw;
-          *pq = fma(-tau * dots[q], v, *pq);
+          *pq = fma(cf[q], v, *pq);
         }
       }
     }
@@ -284,6 +296,7 @@ qr_panel_smem_kernel(double* W, int64_t strideW, int64_t ldw, int64_t m, int64_t
   __shared__ double part[2][NB + 2];          // [0, NB): dots, NB: norm^2, NB+1: alpha
   __shared__ double red[kWarps][NB + 2];
   __shared__ double dots[NB];
+  __shared__ double cf[NB];                // -tau dots[q]: the update's coefficients
   __shared__ double Ts[NB][NB + 1];
   __shared__ double s_tau, s_scal, s_beta;
 
@@ -320,14 +333,21 @@ qr_panel_smem_kernel(double* W, int64_t strideW, int64_t ldw, int64_t m, int64_t
       const double v = col[r - lo];
       ss = fma(v, v, ss);
     }
-    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-    if (lane == 0) red[warp][0] = ss;
+    // the block's partials are summed by warp 0 (kWarps - 1 + 5 FP64 warp
+    // instructions; a butterfly in every warp would take 5 per warp, and an FP64
+    // instruction costs its unit a whole warp slot however few lanes it uses)
+    double* flat = &red[0][0];
+    flat[tid] = ss;
     __syncthreads();
-    if (tid == 0) {
-      double t = 0.0;
-      for (int w = 0; w < kWarps; ++w) t += red[w][0];
-      part[buf][NB] = t;
-      part[buf][NB + 1] = (c >= lo && c < hi) ? col[c - lo] : 0.0;
+    if (warp == 0) {
+      double t = flat[lane];
+#pragma unroll
+      for (int w = 1; w < kWarps; ++w) t += flat[lane + 32 * w];
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) {
+        part[buf][NB] = t;
+        part[buf][NB + 1] = (c >= lo && c < hi) ? col[c - lo] : 0.0;
+      }
     }
     panel_sync<CG>(cluster);
     if (tid == 0) {
@@ -398,16 +418,20 @@ qr_panel_smem_kernel(double* W, int64_t strideW, int64_t ldw, int64_t m, int64_t
       double t = 0.0;
       for (int rk = 0; rk < CG; ++rk) t += panel_part<CG>(cluster, &part[buf][0], rk)[tid];
       dots[tid] = t;
+      cf[tid] = -tau * t;
     }
     __syncthreads();
     // ---- 4. my rows of the later panel columns: W[:, q] -= tau * dots[q] * v
+    //         (the coefficients formed once above: the stores to Ws may alias
+    //         dots for the compiler, so a product written here would be redone
+    //         for every row)
     for (int64_t r = r0 + tid; r < r1; r += kT) {
       const double v = (r == c) ? 1.0 : col[r - lo];
 #pragma unroll
       for (int q = 0; q < NB; ++q) {
         if (q > i && q < nbp) {
           double* pq = Ws + q * Rs + (r - lo);
-          *pq = fma(-tau * dots[q], v, *pq);
+          *pq = fma(cf[q], v, *pq);
         }
       }
     }
