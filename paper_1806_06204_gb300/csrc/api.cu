@@ -239,6 +239,7 @@ size_t layout(void* base, int64_t m, int64_t n, int r, bool svd, PdBufs* b) {
     t.eig.Z = q.take<double>(n * n);
     t.eig.tmp = q.take<double>(n * kCholNB);
     t.eig.bar = q.take<unsigned>(2);
+    t.eig.ver = q.take<int>(n + 1);
     t.eig.err = q.take<int>(1);
     c.off = std::max(c.off, q.off);
   }

@@ -42,89 +42,149 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// One round of the FP64 sweeps: one CTA per column pair.  The squared column
-// norms are tracked in nrm2 (formed afresh at the start of every sweep): a
-// rotation with t = tan(theta) changes them exactly to a - t g and b + t g, so
-// only the cross product of the pair is formed here.  The rotations are the
-// scaled ("fast") form: column j is held as dsc[j] * x~_j, the cosine goes into
-// the scales (dsc_p <- c dsc_p, dsc_q <- c dsc_q) and each stored column takes
-// one FMA, x~_p -= t (dsc_q / dsc_p) x~_q and x~_q += t (dsc_p / dsc_q) x~_p: three
-// FP64 operations per row and pair instead of five (the FP64 pipe is the bound).
-// Near convergence c = 1 - O(t^2), so the scales stay within rounding of 1 over
-// a sweep; the caller folds them into the columns between sweeps.
+// Per-column round counters of the FP64 sweep: acquire/release at GPU scope.
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Waits until *ver >= want, two seconds at most (by the global timer), giving up
+// at once when another block has set the error flag; false (and *err set) on
+// time-out.
+__device__ bool wait_round(const int* ver, int want, int* err) {
+  if (ld_acquire(ver) >= want) return true;
+  uint64_t t0;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  for (unsigned k = 0;; ++k) {
+    if (ld_acquire(ver) >= want) return true;
+    if ((k & 63u) == 63u) {
+      if (*(volatile int*)err) return false;
+      uint64_t t;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+      if (t - t0 > 2000000000ull) break;
+    }
+    __nanosleep(32);
+  }
+  atomicExch(err, 1);
+  return false;
+}
+
+// One FP64 sweep (the n_even - 1 rounds of the round-robin ordering, n_even / 2
+// column pairs each) in one cooperative launch, as a dataflow: pair (round k, i)
+// is work item k * n_even / 2 + i, block b takes the items b, b + gridDim.x, ...
+// in order, and an item starts as soon as the two items of round k - 1 that
+// held its columns are done (per-column round counters, acquire / release),
+// instead of after a launch boundary that waits for the whole round.  Every
+// block is resident (cooperative launch) and takes its items in increasing
+// order, and an item waits only for lower-numbered items, so the lowest
+// unfinished item can always run.  Columns are read through L2 (__ldcg): this
+// SM's L1 may hold a column from an earlier round.
+//
+// Per pair: the squared column norms are tracked in nrm2 (formed afresh at the
+// start of every sweep): a rotation with t = tan(theta) changes them exactly to
+// a - t g and b + t g, so only the cross product of the pair is formed.  The
+// rotations are the scaled ("fast") form: column j is held as dsc[j] * x~_j, the
+// cosine goes into the scales (dsc_p <- c dsc_p, dsc_q <- c dsc_q) and each
+// stored column takes one FMA, x~_p -= t (dsc_q / dsc_p) x~_q and
+// x~_q += t (dsc_p / dsc_q) x~_p: three FP64 operations per row and pair instead
+// of five (the FP64 pipe is the bound).  Near convergence c = 1 - O(t^2), so the
+// scales stay within rounding of 1 over a sweep; the caller folds them into the
+// columns between sweeps.
 // An FP64 instruction occupies its sub-partition's FP64 unit for a whole warp
 // slot however few lanes are active, so the block's 256 partial dot products
 // are summed by one warp (7 + 5 warp instructions instead of 5 per warp plus 8
 // on one lane), and the warp that sums them and forms the rotation changes with
-// the block index: the scalar work spreads over the SM's four sub-partitions
-// instead of all landing on the one that holds warp 0.
+// the item: the scalar work spreads over the SM's four sub-partitions.
 __global__ void __launch_bounds__(kJacThreads)
-jacobi_round_kernel(double* X, int64_t ldx, int64_t m, int n_even, int n_real, int round, double tol,
-                    int* status, double* nrm2, double* dsc) {
+jacobi_sweep_kernel(double* X, int64_t ldx, int64_t m, int n_even, int n_real, double tol,
+                    int* status, double* nrm2, double* dsc, int* ver, int* err) {
   __shared__ double part[kJacThreads];
   __shared__ double s_al, s_be;
-  __shared__ int s_rot;
-  const int i = blockIdx.x;
-  auto elem = [&](int pos) { return pos == 0 ? 0 : 1 + (pos - 1 + round) % (n_even - 1); };
-  int p = elem(i), q = elem(n_even - 1 - i);
-  if (p > q) { const int t = p; p = q; q = t; }
-  if (q >= n_real) return;
-  double* xp = X + p * ldx;
-  double* xq = X + q * ldx;
-  double g = 0.0;
-  for (int64_t r = threadIdx.x; r < m; r += kJacThreads) g = fma(xp[r], xq[r], g);
-  part[threadIdx.x] = g;
-  __syncthreads();
-  const int lead = blockIdx.x & (kJacThreads / 32 - 1);   // the warp that forms the rotation
-  if ((int)(threadIdx.x >> 5) == lead) {
-    const int l = threadIdx.x & 31;
-    double sg = part[l];
+  __shared__ int s_rot, s_ok;
+  const int npairs = n_even / 2;
+  const int64_t items = (int64_t)(n_even - 1) * npairs;
+  for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+    const int round = (int)(it / npairs), i = (int)(it - (int64_t)round * npairs);
+    auto elem = [&](int pos) { return pos == 0 ? 0 : 1 + (pos - 1 + round) % (n_even - 1); };
+    int p = elem(i), q = elem(n_even - 1 - i);
+    if (p > q) { const int t = p; p = q; q = t; }
+    const bool real = q < n_real;      // the pair with the padding column is no work
+    if (threadIdx.x == 0)
+      s_ok = wait_round(ver + p, round, err) && (!real || wait_round(ver + q, round, err));
+    __syncthreads();
+    if (!s_ok) return;
+    if (real) {
+      double* xp = X + p * ldx;
+      double* xq = X + q * ldx;
+      double g = 0.0;
+      for (int64_t r = threadIdx.x; r < m; r += kJacThreads) g = fma(__ldcg(xp + r), __ldcg(xq + r), g);
+      part[threadIdx.x] = g;
+      __syncthreads();
+      const int lead = (int)(it & (kJacThreads / 32 - 1));   // the warp that forms the rotation
+      if ((int)(threadIdx.x >> 5) == lead) {
+        const int l = threadIdx.x & 31;
+        double sg = part[l];
 #pragma unroll
-    for (int k = 1; k < kJacThreads / 32; ++k) sg += part[l + 32 * k];
-    sg = warp_sum(sg);
-    if (l == 0) {
-      // One lane's scalar work costs whole FP64 warp instructions on this part, so
-      // only what fixes the rotation exactly is FP64: the cosine test and the angle
-      // are formed in FP32 (an angle off by 1e-7 only slows convergence by that
-      // factor), while c = (1 + t^2)^(-1/2) for the t actually applied, the norm
-      // and scale updates are FP64 (Newton steps from FP32 seeds).
-      const double dp = dsc[p], dq = dsc[q];
-      sg *= dp * dq;                                  // cross product of the true columns
-      const double sa = nrm2[p], sb = nrm2[q];
-      const float fa = (float)sa, fb = (float)sb;     // below float range: left as converged
-      const float cosv = (fa > 0.f && fb > 0.f) ? fabsf((float)sg) * rsqrtf(fa) * rsqrtf(fb) : 0.f;
-      atomicMax(status + kStatJacobiMaxCos, __float_as_int(cosv));
-      const int rot = (sg != 0.0) && (cosv > (float)tol);
-      if (rot) {
-        const float zeta = (float)((sb - sa) / (2.0 * sg));
-        const float az = fabsf(zeta);
-        const float tf = (az > 1e18f ? 0.5f / az : 1.f / (az + sqrtf(fmaf(az, az, 1.f))));
-        const double t = zeta >= 0.f ? (double)tf : -(double)tf;
-        const double x = fma(t, t, 1.0);
-        double c = (double)rsqrtf((float)x);
-        c = c * fma(-0.5 * x * c, c, 1.5);
-        c = c * fma(-0.5 * x * c, c, 1.5);
-        double rp = (double)(1.f / (float)dp), rq = (double)(1.f / (float)dq);
-        rp = rp * fma(-dp, rp, 2.0); rp = rp * fma(-dp, rp, 2.0);
-        rq = rq * fma(-dq, rq, 2.0); rq = rq * fma(-dq, rq, 2.0);
-        nrm2[p] = fma(-t, sg, sa);
-        nrm2[q] = fma(t, sg, sb);
-        dsc[p] = c * dp;
-        dsc[q] = c * dq;
-        s_al = t * (dq * rp);
-        s_be = t * (dp * rq);
-        atomicAdd(status + kStatJacobiRot, 1);
+        for (int k = 1; k < kJacThreads / 32; ++k) sg += part[l + 32 * k];
+        sg = warp_sum(sg);
+        if (l == 0) {
+          // One lane's scalar work costs whole FP64 warp instructions on this
+          // part, so only what fixes the rotation exactly is FP64: the cosine
+          // test and the angle are formed in FP32 (an angle off by 1e-7 only
+          // slows convergence by that factor), while c = (1 + t^2)^(-1/2) for
+          // the t actually applied, the norm and scale updates are FP64 (Newton
+          // steps from FP32 seeds).
+          const double dp = __ldcg(dsc + p), dq = __ldcg(dsc + q);
+          sg *= dp * dq;                                  // cross product of the true columns
+          const double sa = __ldcg(nrm2 + p), sb = __ldcg(nrm2 + q);
+          const float fa = (float)sa, fb = (float)sb;     // below float range: left as converged
+          const float cosv = (fa > 0.f && fb > 0.f) ? fabsf((float)sg) * rsqrtf(fa) * rsqrtf(fb) : 0.f;
+          atomicMax(status + kStatJacobiMaxCos, __float_as_int(cosv));
+          const int rot = (sg != 0.0) && (cosv > (float)tol);
+          if (rot) {
+            const float zeta = (float)((sb - sa) / (2.0 * sg));
+            const float az = fabsf(zeta);
+            const float tf = (az > 1e18f ? 0.5f / az : 1.f / (az + sqrtf(fmaf(az, az, 1.f))));
+            const double t = zeta >= 0.f ? (double)tf : -(double)tf;
+            const double x = fma(t, t, 1.0);
+            double c = (double)rsqrtf((float)x);
+            c = c * fma(-0.5 * x * c, c, 1.5);
+            c = c * fma(-0.5 * x * c, c, 1.5);
+            double rp = (double)(1.f / (float)dp), rq = (double)(1.f / (float)dq);
+            rp = rp * fma(-dp, rp, 2.0); rp = rp * fma(-dp, rp, 2.0);
+            rq = rq * fma(-dq, rq, 2.0); rq = rq * fma(-dq, rq, 2.0);
+            nrm2[p] = fma(-t, sg, sa);
+            nrm2[q] = fma(t, sg, sb);
+            dsc[p] = c * dp;
+            dsc[q] = c * dq;
+            s_al = t * (dq * rp);
+            s_be = t * (dp * rq);
+            atomicAdd(status + kStatJacobiRot, 1);
+          }
+          s_rot = rot;
+        }
       }
-      s_rot = rot;
+      __syncthreads();
+      if (s_rot) {
+        const double al = s_al, be = s_be;
+        for (int64_t r = threadIdx.x; r < m; r += kJacThreads) {
+          const double u = __ldcg(xp + r), v = __ldcg(xq + r);
+          xp[r] = fma(-al, v, u);
+          xq[r] = fma(be, u, v);
+        }
+      }
     }
-  }
-  __syncthreads();
-  if (!s_rot) return;
-  const double al = s_al, be = s_be;
-  for (int64_t r = threadIdx.x; r < m; r += kJacThreads) {
-    const double u = xp[r], v = xq[r];
-    xp[r] = fma(-al, v, u);
-    xq[r] = fma(be, u, v);
+    // publish: this block's stores, then the columns' round counters
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      st_release(ver + p, round + 1);
+      if (real) st_release(ver + q, round + 1);
+    }
   }
 }
 
@@ -510,15 +570,24 @@ cudaError_t transpose_lower(const double* R, int64_t ldr, double* X, int64_t ldx
   return cudaGetLastError();
 }
 
-cudaError_t jacobi_round(double* X, int64_t ldx, int64_t m, int64_t n_even, int64_t n_real,
-                         int round, double tol, int* status, double* nrm2, double* dsc,
+// One FP64 sweep: n_even - 1 rounds of n_even / 2 pairs (ProfScope: 6 flops and
+// 32 bytes per row and pair).
+cudaError_t jacobi_sweep(double* X, int64_t ldx, int64_t m, int64_t n_even, int64_t n_real,
+                         double tol, int* status, double* nrm2, double* dsc, int* ver, int* err,
                          cudaStream_t st) {
-  ProfScope ps(kProfJacobi, st, 6.0 * (double)m * (double)(n_even / 2),
-               32.0 * (double)m * (double)(n_even / 2));
-  jacobi_round_kernel<<<(unsigned)(n_even / 2), kJacThreads, 0, st>>>(X, ldx, m, (int)n_even,
-                                                                      (int)n_real, round, tol,
-                                                                      status, nrm2, dsc);
-  return cudaGetLastError();
+  int occ = 0, dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, jacobi_sweep_kernel, kJacThreads, 0) !=
+          cudaSuccess)
+    return cudaErrorUnknown;
+  const int64_t items = (n_even - 1) * (n_even / 2);
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)std::max(1, occ) * sms));
+  if (cudaMemsetAsync(ver, 0, sizeof(int) * n_even, st) != cudaSuccess) return cudaErrorUnknown;
+  ProfScope ps(kProfJacobi, st, 6.0 * (double)m * (double)items, 32.0 * (double)m * (double)items);
+  int ne = (int)n_even, nr = (int)n_real;
+  void* args[] = {&X, &ldx, &m, &ne, &nr, &tol, &status, &nrm2, &dsc, &ver, &err};
+  return cudaLaunchCooperativeKernel((const void*)jacobi_sweep_kernel, grid, kJacThreads, args, 0, st);
 }
 
 // Full driver.  Returns 0; 1 = CUDA error, 2 = no convergence, 3 = a bounded
@@ -645,15 +714,16 @@ int eig_sym_jacobi(const double* H, int64_t ldh, int64_t n, double* V, int64_t l
       fill_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(w.tmp, n, 1.0);
     }
     if (column_dots(X, n, X, n, n, n, w.lam, st) != cudaSuccess) return 1;
-    for (int round = 0; round < n_even - 1; ++round)
-      if (jacobi_round(X, n, n, n_even, n, round, tol_strict, w.status, w.lam, w.tmp, st) !=
-          cudaSuccess)
-        return 1;
-    int rs[2] = {0, 0};
-    if (cudaMemcpyAsync(rs, w.status + kStatJacobiRot, sizeof(rs), cudaMemcpyDeviceToHost, st) !=
+    if (jacobi_sweep(X, n, n, n_even, n, tol_strict, w.status, w.lam, w.tmp, w.ver, w.err, st) !=
         cudaSuccess)
       return 1;
+    int rs[2] = {0, 0}, herr = 0;
+    if (cudaMemcpyAsync(rs, w.status + kStatJacobiRot, sizeof(rs), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(&herr, w.err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+      return 1;
     if (cudaStreamSynchronize(st) != cudaSuccess) return 1;
+    if (herr) return 3;
     ++total_sweeps;
     float maxcos;
     memcpy(&maxcos, &rs[1], sizeof(float));

@@ -312,6 +312,7 @@ struct EigWork {
   double* Z;        // n x n, Z orthonormalised in FP64
   double* tmp;      // n x 64 scratch of the triangular solve
   unsigned* bar;    // grid-barrier words (2)
+  int* ver;         // n + 1 per-column round counters of the FP64 sweeps
   int* err;         // bounded-wait error flag
   // test hook of the failure path: with stall = 1, block 0 of the first FP32
   // sweep waits, for stall_ns, on a flag nothing sets, then takes the
@@ -335,8 +336,11 @@ cudaError_t gather_columns(const double* X, int64_t ldx, double* Y, int64_t ldy,
                            int64_t n, const int* perm, const double* sign, cudaStream_t st);
 cudaError_t transpose_lower(const double* R, int64_t ldr, double* X, int64_t ldx, int64_t n,
                             cudaStream_t st);
-cudaError_t jacobi_round(double* X, int64_t ldx, int64_t m, int64_t n_even, int64_t n_real, int round,
-                         double tol, int* status, double* nrm2, double* dsc, cudaStream_t st);
+// One FP64 sweep of the one-sided Jacobi rounds (a cooperative launch; ver holds
+// n_even round counters, err the bounded waits' flag).
+cudaError_t jacobi_sweep(double* X, int64_t ldx, int64_t m, int64_t n_even, int64_t n_real,
+                         double tol, int* status, double* nrm2, double* dsc, int* ver, int* err,
+                         cudaStream_t st);
 
 #endif  // __CUDACC__
 
