@@ -86,6 +86,7 @@ template <> struct Form<kFormFP8> {
 };
 template <int FORM> __host__ __device__ constexpr int form_bk() { return kRowBytes / Form<FORM>::kElem; }
 constexpr int kARing = 4;
+constexpr int kFusedSliceK = 2048;  // slicing in one launch per product up to this padded K
 constexpr int kGroupM = 8;         // tile rows per CTA group (L2 reuse of the A slices)
 constexpr int kEpiWarps = 16;      // four per TMEM lane quarter, each owning a quarter of the columns
 constexpr int kThreads = 64 + 32 * kEpiWarps;   // warp 0 TMA, warp 1 MMA, the rest epilogue
@@ -245,21 +246,15 @@ __device__ __forceinline__ void slice_values(double x, int ee, float* v) {
 // slice s (1-based) at + (s-1) * rows_pad * K_pad elements.  32 x 64 tiles
 // through shared memory: the read runs along X's contiguous dimension, and each
 // thread writes two neighbouring K entries per plane so that a warp stores whole
-// 128-byte (16-bit forms) or 64-byte (FP8) lines.
-template <int S, int FORM>
-__global__ void __launch_bounds__(256)
-slice_kernel(const double* __restrict__ X, int64_t ldx, int64_t strideX, int trans,
-             int rows, int K, const int* __restrict__ e_in,
-             uint8_t* __restrict__ out, int rows_pad, int K_pad,
-             const int* __restrict__ ek, int esign) {
+// 128-byte (16-bit forms) or 64-byte (FP8) lines.  Xb, ob and ekb are the batch
+// entry's; er(r) gives the exponent of tile row r (rows i0 + r).
+template <int S, int FORM, class ExpOf>
+__device__ __forceinline__ void slice_tile(double (*tile)[65], const double* __restrict__ Xb,
+                                           int64_t ldx, int trans, int rows, int K, ExpOf er,
+                                           uint8_t* __restrict__ ob, int rows_pad, int K_pad,
+                                           const int* __restrict__ ekb, int esign, int i0, int k0) {
   constexpr int kE = Form<FORM>::kElem;
-  __shared__ double tile[32][65];                 // [row][k]
-  const double* Xb = X + blockIdx.z * strideX;
-  const int* eb = e_in + blockIdx.z * rows_pad;
-  const int* ekb = ek ? ek + blockIdx.z * K_pad : nullptr;
   const size_t plane = (size_t)rows_pad * K_pad;  // elements
-  uint8_t* ob = out + (size_t)blockIdx.z * S * plane * kE;
-  const int i0 = blockIdx.y * 32, k0 = blockIdx.x * 64;
   const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
   if (!trans) {     // rows contiguous: tx runs along i
     const int i = i0 + tx;
@@ -285,8 +280,9 @@ slice_kernel(const double* __restrict__ X, int64_t ldx, int64_t strideX, int tra
     float va[S], vb[S];
     if (i < rows) {
       // element x 2^(esign ek[k]) against the row bound 2^(e_i - 1)
-      const int ea = ekb ? eb[i] - esign * ekb[k] : eb[i];
-      const int eb2 = ekb ? eb[i] - esign * ekb[k + 1] : eb[i];
+      const int ei = er(r);
+      const int ea = ekb ? ei - esign * ekb[k] : ei;
+      const int eb2 = ekb ? ei - esign * ekb[k + 1] : ei;
       slice_values<S, FORM>(tile[r][kl], ea, va);
       slice_values<S, FORM>(tile[r][kl + 1], eb2, vb);
     } else {
@@ -308,6 +304,102 @@ slice_kernel(const double* __restrict__ X, int64_t ldx, int64_t strideX, int tra
       for (int s = 0; s < S; ++s)
         *reinterpret_cast<__nv_bfloat162*>(o + s * plane * 2) = __floats2bfloat162_rn(va[s], vb[s]);
     }
+  }
+}
+
+// One 32 x 64 tile per block, with the row exponents row_exp_kernel wrote.
+template <int S, int FORM>
+__global__ void __launch_bounds__(256)
+slice_kernel(const double* __restrict__ X, int64_t ldx, int64_t strideX, int trans,
+             int rows, int K, const int* __restrict__ e_in,
+             uint8_t* __restrict__ out, int rows_pad, int K_pad,
+             const int* __restrict__ ek, int esign) {
+  __shared__ double tile[32][65];                 // [row][k]
+  const int* eb = e_in + blockIdx.z * rows_pad + blockIdx.y * 32;
+  const size_t plane = (size_t)rows_pad * K_pad;
+  slice_tile<S, FORM>(tile, X + blockIdx.z * strideX, ldx, trans, rows, K,
+                      [&](int r) { return eb[r]; },
+                      out + (size_t)blockIdx.z * S * plane * Form<FORM>::kElem, rows_pad, K_pad,
+                      ek ? ek + blockIdx.z * K_pad : nullptr, esign, blockIdx.y * 32,
+                      blockIdx.x * 64);
+}
+
+// One operand of a fused slicing launch.
+struct SliceOp {
+  const double* X;
+  int64_t ldx, strideX;
+  int trans, rows, rows_pad, esign;
+  int* e;                   // row exponents out (batch x rows_pad)
+  uint8_t* out;             // slice planes
+};
+
+// Row exponents and slices of both operands of a product in one launch: block
+// x < nblk_a takes 32 rows of op(A), the rest 32 rows of op(B)^T, blockIdx.z the
+// batch entry.  The block first finds its rows' exponents (the max over all K,
+// as row_exp_kernel), keeps them in shared memory, then slices its rows tile by
+// tile along K: one launch instead of four for the small products, whose K runs
+// are short (the caller uses it for K_pad <= 2048).
+template <int S, int FORM>
+__global__ void __launch_bounds__(256)
+slice_fused_kernel(const SliceOp a, const SliceOp b, int nblk_a, int K, int K_pad,
+                   const int* __restrict__ ek) {
+  __shared__ double tile[32][65];
+  __shared__ long long red[8][33];
+  __shared__ int es[32];
+  const bool on_b = (int)blockIdx.x >= nblk_a;
+  const SliceOp o = on_b ? b : a;
+  const int i0 = (on_b ? (int)blockIdx.x - nblk_a : (int)blockIdx.x) * 32;
+  const double* Xb = o.X + blockIdx.z * o.strideX;
+  const int* ekb = ek ? ek + blockIdx.z * K_pad : nullptr;
+  const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+  const unsigned long long kMag = 0x7FFFFFFFFFFFFFFFull;
+  // the row bound as row_exp_kernel forms it: the largest magnitude pattern, or
+  // with the inner-index shifts the largest shifted exponent bound
+  auto take = [&](long long& mx, double x, int k) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x) & kMag;
+    if (!ekb) {
+      mx = (long long)bits > mx ? (long long)bits : mx;
+    } else if (bits != 0) {
+      const long long e = exp_above(bits) + o.esign * ekb[k];
+      mx = e > mx ? e : mx;
+    }
+  };
+  auto finish = [&](long long v) -> int {
+    if (!ekb) return exp_above((unsigned long long)v);
+    return v == LLONG_MIN ? 0 : (int)v;
+  };
+  if (!o.trans) {   // rows contiguous: tx runs along i, k split over ty
+    const int i = i0 + tx;
+    long long mx = ekb ? LLONG_MIN : 0;
+    if (i < o.rows)
+      for (int k = ty; k < K; k += 8) take(mx, Xb[i + (int64_t)k * o.ldx], k);
+    red[ty][tx] = mx;
+    __syncthreads();
+    if (ty == 0) {
+      for (int y = 1; y < 8; ++y) mx = red[y][tx] > mx ? red[y][tx] : mx;
+      es[tx] = finish(mx);
+    }
+  } else {          // K contiguous: one warp per row, lanes along k
+    for (int r = ty; r < 32; r += 8) {
+      const int i = i0 + r;
+      long long mx = ekb ? LLONG_MIN : 0;
+      if (i < o.rows)
+        for (int k = tx; k < K; k += 32) take(mx, Xb[k + (int64_t)i * o.ldx], k);
+      for (int s = 16; s > 0; s >>= 1) {
+        const long long t = __shfl_xor_sync(0xffffffffu, mx, s);
+        mx = t > mx ? t : mx;
+      }
+      if (tx == 0) es[r] = finish(mx);
+    }
+  }
+  __syncthreads();
+  if (ty == 0 && i0 + tx < o.rows_pad) o.e[blockIdx.z * o.rows_pad + i0 + tx] = es[tx];
+  const size_t plane = (size_t)o.rows_pad * K_pad;
+  uint8_t* ob = o.out + (size_t)blockIdx.z * S * plane * Form<FORM>::kElem;
+  for (int k0 = 0; k0 < K_pad; k0 += 64) {
+    slice_tile<S, FORM>(tile, Xb, o.ldx, o.trans, o.rows, K, [&](int r) { return es[r]; }, ob,
+                        o.rows_pad, K_pad, ekb, o.esign, i0, k0);
+    __syncthreads();   // the tile is refilled
   }
 }
 
@@ -729,12 +821,23 @@ cudaError_t run_split(const GemmArgs& g, SplitWork& w, cudaStream_t st) {
         Xo, swap ? lda : ldb, swap ? sta : stb, swap ? ta : tb, swap ? M : N, K, ek, Kpad);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
-  if ((err = slice_operand<S, FORM>(Xa, lda, sta, ta, M, K, nb, ea, sa, Mpad, Kpad, ek, sign_a,
-                                    st)) != cudaSuccess)
-    return err;
-  if ((err = slice_operand<S, FORM>(Xb, ldb, stb, tb, N, K, nb, eb, sb, Npad, Kpad, ek, -sign_a,
-                                    st)) != cudaSuccess)
-    return err;
+  if (Kpad <= kFusedSliceK) {
+    // short K runs: both operands' exponents and slices in one launch
+    const SliceOp oa{Xa, lda, sta, ta, M, Mpad, sign_a, ea, sa};
+    const SliceOp ob{Xb, ldb, stb, tb, N, Npad, -sign_a, eb, sb};
+    ProfScope ps(kProfSlice, st, 0.0,
+                 (16.0 + (double)Form<FORM>::kElem * S) * nb * (double)(Mpad + Npad) * Kpad);
+    slice_fused_kernel<S, FORM><<<dim3((unsigned)((Mpad + Npad) / 32), 1, nb), dim3(32, 8), 0, st>>>(
+        oa, ob, Mpad / 32, K, Kpad, ek);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  } else {
+    if ((err = slice_operand<S, FORM>(Xa, lda, sta, ta, M, K, nb, ea, sa, Mpad, Kpad, ek, sign_a,
+                                      st)) != cudaSuccess)
+      return err;
+    if ((err = slice_operand<S, FORM>(Xb, ldb, stb, tb, N, K, nb, eb, sb, Npad, Kpad, ek, -sign_a,
+                                      st)) != cudaSuccess)
+      return err;
+  }
   CUtensorMap mA, mB;
   if (!make_map<FORM>(&mA, sa, (int64_t)nb * S * Mpad, Kpad, kTileM) ||
       !make_map<FORM>(&mB, sb, (int64_t)nb * S * Npad, Kpad, BN))
