@@ -404,15 +404,52 @@ slice_fused_kernel(const SliceOp a, const SliceOp b, int nblk_a, int K, int K_pa
 }
 
 // ----------------------------------------------------------------- GEMM
-// x 2^k, exact: an integer add on the exponent field while the result stays a
-// normal number (ldexp otherwise; zero stays zero).
-__device__ __forceinline__ double pow2_scale(double x, int k) {
-  const long long b = __double_as_longlong(x);
-  const int e = (int)((b >> 52) & 0x7FF);
-  if (e == 0) return x == 0.0 ? x : ldexp(x, k);
-  const int ne = e + k;
-  if (ne <= 0 || ne >= 0x7FF) return ldexp(x, k);
-  return __longlong_as_double(b + ((long long)k << 52));
+// The epilogue's conversions by integer operations: FP64 instructions, int64
+// and float conversions to FP64 among them, go through the FP64 units, the
+// scarce ones on this part, and the epilogue of a product with a short K does
+// as much FP64 work per output as its MMAs do tensor work.
+
+// x 2^k for an int64 x, rounded to nearest (ties to even) like (double)x, then
+// scaled exactly: the leading one found by a count of leading zeros, 53 bits
+// kept, the exponent assembled; a result outside the normal range takes the
+// FP64 route.
+__device__ __forceinline__ double i64_scaled(long long x, int k) {
+  if (x == 0) return 0.0;
+  const unsigned long long sgn = x < 0 ? 0x8000000000000000ull : 0ull;
+  const unsigned long long a = x < 0 ? 0ull - (unsigned long long)x : (unsigned long long)x;
+  int msb = 63 - __clzll((long long)a);
+  unsigned long long m;
+  if (msb <= 52) {
+    m = a << (52 - msb);
+  } else {
+    const int sh = msb - 52;
+    const unsigned long long rem = a & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    m = a >> sh;
+    if (rem > half || (rem == half && (m & 1ull))) {
+      ++m;
+      if (m >> 53) {
+        m >>= 1;
+        ++msb;
+      }
+    }
+  }
+  const int be = msb + k + 1023;
+  if (be <= 0 || be >= 2047) return ldexp((double)x, k);
+  return __longlong_as_double((long long)(sgn | ((unsigned long long)be << 52) | (m & 0xFFFFFFFFFFFFFull)));
+}
+
+// f 2^k for a float f, exact: the float's fields moved into an FP64 pattern
+// (zero keeps its sign; subnormal floats and results outside the normal range
+// take the FP64 route).
+__device__ __forceinline__ double f32_scaled(float f, int k) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned long long sgn = (unsigned long long)(u >> 31) << 63;
+  if ((u & 0x7FFFFFFFu) == 0) return __longlong_as_double((long long)sgn);
+  const int ef = (int)((u >> 23) & 0xFFu);
+  const int be = ef - 127 + k + 1023;
+  if (ef == 0 || ef == 255 || be <= 0 || be >= 2047) return ldexp((double)f, k);
+  return __longlong_as_double(
+      (long long)(sgn | ((unsigned long long)be << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29)));
 }
 
 struct SplitEpi {
@@ -683,15 +720,18 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
           const int col = n0 + half * HALF + j;
           const int ci = p.swap ? col : row, cj = p.swap ? row : col;
           if (row < (p.swap ? p.N : p.M) && col < (p.swap ? p.M : p.N)) {
-            // one conversion; the power of two 2^(e_i + f_j - 48) goes into the
-            // exponent field (FP64 arithmetic is scarce on this part)
+            // the integer part and the float part, each scaled by the power of
+            // two 2^(e_i + f_j) in its exponent field, joined by one FP64 add
+            // (the same single rounding as converting the int64 and adding the
+            // float part at its weight)
+            const int e = ei + __ldg(ebb + j);
             double v;
             if (FORM == kFormFP8)
-              v = pow2_scale(fma((double)fm[j], 0x1p-17, (double)iacc[j]), ei + __ldg(ebb + j) - 48);
+              v = i64_scaled(iacc[j], e - 48) + f32_scaled(fm[j], e - 48 - 17);
             else if (FORM == kFormFP16)
-              v = pow2_scale(fma((double)fm[j], 0x1p-7, (double)iacc[j]), ei + __ldg(ebb + j) - 49);
+              v = i64_scaled(iacc[j], e - 49) + f32_scaled(fm[j], e - 49 - 7);
             else
-              v = pow2_scale(fma((double)fm[j], 0x1p48, (double)iacc[j]), ei + __ldg(ebb + j) - 48);
+              v = i64_scaled(iacc[j], e - 48) + f32_scaled(fm[j], e);
             if (al == -1.0) v = __longlong_as_double(__double_as_longlong(v) ^ (long long)0x8000000000000000ull);
             else if (al != 1.0) v *= al;
             if (first) {
