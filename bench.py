@@ -351,9 +351,9 @@ def split_prec(zb, slices):
 # state); bench.py scales it by the bytes its own launches state.  Set to None
 # when the kernel changes.
 TRAFFIC_PER_STATED_BYTE = {
-    # qr_panel_smem_kernel, 20 launches at n = 960, r = 5: 1.336 MB read, 0
+    # qr_panel_smem_kernel, 12 launches at n = 960, r = 5: 1.313 MB read, 0
     # written, of 2.54 MB stated (profiles/traffic_batch4_split.md)
-    "qr_panel": 0.526,
+    "qr_panel": 0.517,
 }
 
 
