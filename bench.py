@@ -357,6 +357,11 @@ TRAFFIC_PER_STATED_BYTE = {
 }
 
 
+# Kernel classes whose work the Zolo-PD flop model does not count (Zolo-SVD's
+# eigensolver sweeps; its three n^3 products run in the gemm_f64 class).
+OUTSIDE_PD_MODEL = {"jacobi_round", "jacobi32_sweep"}
+
+
 def roofline(kstats, step_ms, model_flops=None, split_pairs=SPLIT_PAIRS, peak_ratio=1.0):
     """Roofline entry of the dominant kernel class (by device time in one step).
 
@@ -372,7 +377,9 @@ def roofline(kstats, step_ms, model_flops=None, split_pairs=SPLIT_PAIRS, peak_ra
                         key=lambda kv: kv[1]["ms"])
     sec = dom["ms"] / 1000.0
     bound = {"combine": "hbm", "slice": "hbm", "gemm_split": "tensor"}.get(dom_name, "alu")
-    flop_classes = {k: v for k, v in kstats.items() if v["launches"] > 0 and v["flops"] > 0}
+    # the eigensolver's sweeps are outside the Zolo-PD flop model: they take no share
+    flop_classes = {k: v for k, v in kstats.items()
+                    if v["launches"] > 0 and v["flops"] > 0 and k not in OUTSIDE_PD_MODEL}
     stated = sum(v["flops"] for v in flop_classes.values())
     if model_flops and dom_name in flop_classes and stated > 0:
         work = model_flops * dom["flops"] / stated

@@ -59,6 +59,18 @@ def test_roofline_shares_the_model_flops_between_classes():
     assert "model" in roof["work_basis"]
 
 
+def test_roofline_leaves_the_eigensolver_out_of_the_model_share():
+    # Zolo-SVD: the Jacobi sweeps state flops the Zolo-PD model does not count,
+    # so they must not dilute the share of the model's own classes
+    kstats = {"gemm_f64": {"launches": 10, "ms": 900.0, "flops": 1.2e12, "bytes": 0.0},
+              "qr_panel": {"launches": 4, "ms": 50.0, "flops": 0.3e12, "bytes": 0.0},
+              "jacobi_round": {"launches": 4, "ms": 600.0, "flops": 2.0e12, "bytes": 0.0},
+              "jacobi32_sweep": {"launches": 13, "ms": 600.0, "flops": 5.0e12, "bytes": 0.0}}
+    roof = bench.roofline(kstats, 2200.0, model_flops=1.0e12)
+    assert roof["kernel"] == "gemm_f64"
+    assert roof["achieved"] == pytest.approx(0.8e12 / 0.9 / 1e12)
+
+
 def test_oracle_sample_times_two_sizes_and_scales_by_the_model():
     w = dict(bench.WORKLOADS["pd256"], sample_n=96)
     v, spent, desc = bench.oracle_sample(w)
