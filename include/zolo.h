@@ -373,7 +373,10 @@ int zolo_tune_load(zolo_handle_t handle, const char* path);
        on an mbarrier no thread or copy arrives at;
      ZOLO_STALL_JACOBI32: block 0 of the first FP32 sweep of zolo_svd's
        eigensolver, on a flag no thread sets (the other blocks leave the grid
-       barrier when they see the error flag).
+       barrier when they see the error flag);
+     ZOLO_STALL_JACOBI64: block 0 of the first FP64 sweep, on a flag no thread
+       sets, before its first column pair (the blocks whose pairs wait for that
+       pair's columns leave when they see the error flag).
    where = 0 switches it off.  Returns 0, -1 (NULL handle), -2 (where) or -3
    (ns). */
 /* zolo_debug_guards(h, 1): a checking mode for the workspace (no counterpart in
@@ -391,6 +394,7 @@ int zolo_debug_guards(zolo_handle_t handle, int enable);
 
 #define ZOLO_STALL_SPLIT_GEMM 1
 #define ZOLO_STALL_JACOBI32 2
+#define ZOLO_STALL_JACOBI64 3
 int zolo_debug_stall(zolo_handle_t handle, int where, int64_t ns);
 
 /* Short text for a return code. */

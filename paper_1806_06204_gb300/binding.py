@@ -230,6 +230,7 @@ def autotune(handle, enable: bool) -> None:
 
 ZOLO_STALL_SPLIT_GEMM = 1
 ZOLO_STALL_JACOBI32 = 2
+ZOLO_STALL_JACOBI64 = 3
 
 
 def debug_guards(handle, enable: bool) -> None:

@@ -101,7 +101,7 @@ struct zolo_handle_s {
   // contraction kernel measured fastest per shape (zolo_autotune)
   GemmTuner tuner;
   // zolo_debug_stall: which kernel waits on a barrier nothing completes (0: none,
-  // ZOLO_STALL_SPLIT_GEMM, ZOLO_STALL_JACOBI32) and for how long
+  // ZOLO_STALL_SPLIT_GEMM, ZOLO_STALL_JACOBI32, ZOLO_STALL_JACOBI64) and for how long
   int dbg_stall = 0;
   long long dbg_ns = 0;
   cudaEvent_t ph_ev[kPhaseEvents] = {};   // phase boundaries of one call
@@ -1341,6 +1341,7 @@ int zolo_svd(zolo_handle_t h, const double* A, int64_t m, int64_t n, int64_t lda
     std::vector<double> lam(n);
     int sweeps = 0;
     b.eig.stall = h->dbg_stall == ZOLO_STALL_JACOBI32;
+    b.eig.stall64 = h->dbg_stall == ZOLO_STALL_JACOBI64;
     b.eig.stall_ns = h->dbg_ns;
     const int ee = eig_sym_jacobi(Hm, n, n, V, ldv, lam.data(), b.eig, &sweeps, st);
     info->eig_sweeps = sweeps;
@@ -1880,7 +1881,9 @@ int zolo_batch_graphs(zolo_handle_t h, int enable) {
 
 int zolo_debug_stall(zolo_handle_t h, int where, int64_t ns) {
   if (!h) return -1;
-  if (where != 0 && where != ZOLO_STALL_SPLIT_GEMM && where != ZOLO_STALL_JACOBI32) return -2;
+  if (where != 0 && where != ZOLO_STALL_SPLIT_GEMM && where != ZOLO_STALL_JACOBI32 &&
+      where != ZOLO_STALL_JACOBI64)
+    return -2;
   if (ns < 0 || ns > 1000000000) return -3;
   h->dbg_stall = where;
   h->dbg_ns = ns;

@@ -101,12 +101,32 @@ __device__ bool wait_round(const int* ver, int want, int* err) {
 // the item: the scalar work spreads over the SM's four sub-partitions.
 __global__ void __launch_bounds__(kJacThreads)
 jacobi_sweep_kernel(double* X, int64_t ldx, int64_t m, int n_even, int n_real, double tol,
-                    int* status, double* nrm2, double* dsc, int* ver, int* err) {
+                    int* status, double* nrm2, double* dsc, int* ver, int* err, int stall,
+                    long long stall_ns) {
   __shared__ double part[kJacThreads];
   __shared__ double s_al, s_be;
-  __shared__ int s_rot, s_ok;
+  __shared__ int s_rot, s_ok, never;
   const int npairs = n_even / 2;
   const int64_t items = (int64_t)(n_even - 1) * npairs;
+  if (stall && blockIdx.x == 0) {
+    // test hook of the error exit: item 0 first waits, bounded, on a flag that
+    // nothing sets; the blocks whose items need its columns leave on the flag
+    if (threadIdx.x == 0) {
+      never = 0;
+      long long t0;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+      for (;;) {
+        if (*(volatile int*)&never) break;
+        long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (t - t0 > stall_ns) break;
+        __nanosleep(256);
+      }
+      atomicExch(err, 1);
+    }
+    __syncthreads();
+    return;
+  }
   for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
     const int round = (int)(it / npairs), i = (int)(it - (int64_t)round * npairs);
     auto elem = [&](int pos) { return pos == 0 ? 0 : 1 + (pos - 1 + round) % (n_even - 1); };
@@ -114,7 +134,8 @@ jacobi_sweep_kernel(double* X, int64_t ldx, int64_t m, int n_even, int n_real, d
     if (p > q) { const int t = p; p = q; q = t; }
     const bool real = q < n_real;      // the pair with the padding column is no work
     if (threadIdx.x == 0)
-      s_ok = wait_round(ver + p, round, err) && (!real || wait_round(ver + q, round, err));
+      s_ok = !*(volatile int*)err && wait_round(ver + p, round, err) &&
+             (!real || wait_round(ver + q, round, err));
     __syncthreads();
     if (!s_ok) return;
     if (real) {
@@ -574,7 +595,7 @@ cudaError_t transpose_lower(const double* R, int64_t ldr, double* X, int64_t ldx
 // 32 bytes per row and pair).
 cudaError_t jacobi_sweep(double* X, int64_t ldx, int64_t m, int64_t n_even, int64_t n_real,
                          double tol, int* status, double* nrm2, double* dsc, int* ver, int* err,
-                         cudaStream_t st) {
+                         int stall, long long stall_ns, cudaStream_t st) {
   int occ = 0, dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
@@ -586,7 +607,7 @@ cudaError_t jacobi_sweep(double* X, int64_t ldx, int64_t m, int64_t n_even, int6
   if (cudaMemsetAsync(ver, 0, sizeof(int) * n_even, st) != cudaSuccess) return cudaErrorUnknown;
   ProfScope ps(kProfJacobi, st, 6.0 * (double)m * (double)items, 32.0 * (double)m * (double)items);
   int ne = (int)n_even, nr = (int)n_real;
-  void* args[] = {&X, &ldx, &m, &ne, &nr, &tol, &status, &nrm2, &dsc, &ver, &err};
+  void* args[] = {&X, &ldx, &m, &ne, &nr, &tol, &status, &nrm2, &dsc, &ver, &err, &stall, &stall_ns};
   return cudaLaunchCooperativeKernel((const void*)jacobi_sweep_kernel, grid, kJacThreads, args, 0, st);
 }
 
@@ -714,8 +735,8 @@ int eig_sym_jacobi(const double* H, int64_t ldh, int64_t n, double* V, int64_t l
       fill_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(w.tmp, n, 1.0);
     }
     if (column_dots(X, n, X, n, n, n, w.lam, st) != cudaSuccess) return 1;
-    if (jacobi_sweep(X, n, n, n_even, n, tol_strict, w.status, w.lam, w.tmp, w.ver, w.err, st) !=
-        cudaSuccess)
+    if (jacobi_sweep(X, n, n, n_even, n, tol_strict, w.status, w.lam, w.tmp, w.ver, w.err,
+                     sw == 0 ? w.stall64 : 0, w.stall_ns, st) != cudaSuccess)
       return 1;
     int rs[2] = {0, 0}, herr = 0;
     if (cudaMemcpyAsync(rs, w.status + kStatJacobiRot, sizeof(rs), cudaMemcpyDeviceToHost, st) !=

@@ -318,6 +318,9 @@ struct EigWork {
   // sweep waits, for stall_ns, on a flag nothing sets, then takes the
   // bounded-wait error exit (the other blocks leave the grid barrier on the flag)
   int stall = 0;
+  // the same for the first FP64 sweep: block 0 waits on a flag nothing sets, the
+  // blocks whose work items need its columns leave on the error flag
+  int stall64 = 0;
   long long stall_ns = 0;
 };
 // Y <- X R^{-1} for upper R with inverted diagonal blocks (cholesky_upper_batched output)
@@ -340,7 +343,7 @@ cudaError_t transpose_lower(const double* R, int64_t ldr, double* X, int64_t ldx
 // n_even round counters, err the bounded waits' flag).
 cudaError_t jacobi_sweep(double* X, int64_t ldx, int64_t m, int64_t n_even, int64_t n_real,
                          double tol, int* status, double* nrm2, double* dsc, int* ver, int* err,
-                         cudaStream_t st);
+                         int stall, long long stall_ns, cudaStream_t st);
 
 #endif  // __CUDACC__
 

@@ -2,7 +2,9 @@
 
 zolo_debug_stall makes a kernel's first wait one that nothing completes (an
 mbarrier no thread or copy arrives at in the split-precision product; a flag
-no thread sets in the FP32 Jacobi sweep), bounded by a few milliseconds.  The
+no thread sets in the FP32 Jacobi sweep and before the first column pair of the
+FP64 sweep, whose other blocks wait for that pair's columns), bounded by a few
+milliseconds.  The
 kernel must give up, let what it has in flight finish, release its tensor
 memory and return; the call must report ZOLO_ETIMEOUT; and the next call on the
 same handle, with the hook off, must compute the right result.  Nothing here
@@ -88,5 +90,28 @@ def test_jacobi_grid_barrier_wait_expires_then_recovers(zb):
         U, S, V, info = zb.zolo_svd(h, A, o)
         assert info.status == 0
         assert np.max(np.abs(S.cpu().numpy() - sm.sigma)) <= 1e-12 * sm.sigma[0]
+    finally:
+        h.close()
+
+
+def test_jacobi_fp64_sweep_wait_expires_then_recovers(zb):
+    # the first FP64 sweep's block 0 stalls before its first column pair: the
+    # blocks whose pairs need those columns give up on the error flag
+    from paper_1806_06204_gb300 import synth
+    sm = synth.square_geometric(300, 1e6, seed=1012)
+    A = dev(sm.A)
+    h = zb.Handle(0)
+    try:
+        o = zb.opts(beta=float(sm.sigma[-1]), alpha=1.0, r=4)
+        zb.debug_stall(h, zb.ZOLO_STALL_JACOBI64, STALL_NS)
+        for _ in range(2):
+            _, _, _, info = zb.zolo_svd(h, A, o, check=False)
+            assert info.status == ZOLO_ETIMEOUT
+        zb.debug_stall(h, 0, 0)
+        U, S, V, info = zb.zolo_svd(h, A, o)
+        assert info.status == 0
+        assert np.max(np.abs(S.cpu().numpy() - sm.sigma)) <= 1e-12 * sm.sigma[0]
+        U, V = U.cpu().numpy(), V.cpu().numpy()
+        assert zo.orthogonality(U) <= 1e-13 and zo.orthogonality(V) <= 1e-13
     finally:
         h.close()
