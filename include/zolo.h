@@ -304,9 +304,9 @@ int zolo_dgemm(zolo_handle_t handle, int transA, int transB, int64_t m, int64_t 
    (rows, cols) = (n, m) when m < 128 and n > m, else (m, n) (so
    m = n = k = 512 fits with 8 slices, 1024 x 1024 x 512 does not, and a tall
    9000 x 8 x 8 product fits).  Every size accepted here runs.  The
-   first call on a device looks up the array's device address; make it before
-   any stream capture.  All calls share the array: calls that overlap on the
-   GPU race and must be serialised by the caller.  Matrices are device
+   first call on a device looks up the array's device address.  All calls
+   share the array: calls that overlap on the GPU race and must be serialised
+   by the caller.  Matrices are device
    pointers as in zolo_dgemm; `slices` = 8 or 9 (0 = 8).  Synchronises the
    stream before returning. */
 int zolo_dgemm_noalloc(int transA, int transB, int64_t m, int64_t n, int64_t k, double alpha,

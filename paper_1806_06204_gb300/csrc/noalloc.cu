@@ -8,8 +8,8 @@
 //
 // The array is 16 MiB and every GPU that loads this library holds it until the
 // process exits.  Its device address is looked up once per device, on the
-// first call made with that device current (cudaGetSymbolAddress); make that
-// first call before any stream capture.  Every call shares the array and it
+// first call made with that device current (cudaGetSymbolAddress).  Every call
+// shares the array and it
 // keeps the previous call's contents: the error flag is cleared at the start
 // of each call, the slices and exponents are rewritten before they are read.
 // Calls whose work overlaps on the GPU (other streams, other host threads)
