@@ -357,13 +357,24 @@ TRAFFIC_PER_STATED_BYTE = {
 }
 
 
+def sm_time(kstats):
+    """Per kernel class, the SM-time of the profiled call: each launch's device
+    time times the share of the GPU's resident-block slots its blocks take (the
+    library's zolo_profile_read); with the batch's lanes in flight these shares
+    add up to about the timed step, the plain device times to several times it."""
+    return {k: round(v.get("sm_ms", 0.0), 3) for k, v in kstats.items() if v["launches"]}
+
+
 # Kernel classes whose work the Zolo-PD flop model does not count (Zolo-SVD's
 # eigensolver sweeps; its three n^3 products run in the gemm_f64 class).
 OUTSIDE_PD_MODEL = {"jacobi_round", "jacobi32_sweep"}
 
 
-def roofline(kstats, step_ms, model_flops=None, split_pairs=SPLIT_PAIRS, peak_ratio=1.0):
-    """Roofline entry of the dominant kernel class (by device time in one step).
+def roofline(kstats, step_ms, model_flops=None, split_pairs=SPLIT_PAIRS, peak_ratio=1.0,
+             by="ms"):
+    """Roofline entry of the dominant kernel class (by device time in one step,
+    or with by="sm_ms" by SM-time: device time times the share of the GPU the
+    launches' blocks take).
 
     With model_flops (the Zolo-PD flops of the step), the algorithmic work of a
     flop-carrying class is the model's, shared out between the classes in
@@ -374,7 +385,7 @@ def roofline(kstats, step_ms, model_flops=None, split_pairs=SPLIT_PAIRS, peak_ra
     state themselves (padding, T factors, the explicit Q's full rows included)
     are kept beside it as `issued_*`."""
     dom_name, dom = max(((k, v) for k, v in kstats.items() if v["launches"] > 0),
-                        key=lambda kv: kv[1]["ms"])
+                        key=lambda kv: kv[1].get(by, kv[1]["ms"]))
     sec = dom["ms"] / 1000.0
     bound = {"combine": "hbm", "slice": "hbm", "gemm_split": "tensor"}.get(dom_name, "alu")
     # the eigensolver's sweeps are outside the Zolo-PD flop model: they take no share
@@ -504,6 +515,13 @@ def batch_arm(args, w, h, mats, As, Qps, Hs, split, steps, warmup, local, dist, 
     roof["in_step_lower_bound"] = {
         "achieved": rate, "frac": rate / roof["peak"],
         "basis": "the class's work divided by the whole timed step (its lanes overlap there)"}
+    # the class that holds the most of the GPU: with 32 lanes in flight the
+    # classes' SM-times add up to about the step, so this one sets the pace
+    # (the class above has the most device time alone, on a few SMs)
+    roof_sm = roofline(kstats, prof_ms, flops, split_pairs=SPLIT_PAIRS_OF[slices],
+                       peak_ratio=SLICE_PEAK_RATIO[slices], by="sm_ms")
+    roof_sm["sm_time_share"] = (kstats[roof_sm["kernel"]].get("sm_ms", 0.0) /
+                                max(1e-9, sum(v.get("sm_ms", 0.0) for v in kstats.values())))
 
     # accuracy of every result, on the device with torch (a check, not timed)
     bwd, orth = 0.0, 0.0
@@ -517,7 +535,7 @@ def batch_arm(args, w, h, mats, As, Qps, Hs, split, steps, warmup, local, dist, 
            "bar": 1e-13, "bar_met": bool(bwd <= 1e-13 and orth <= 1e-13)}
     return {"os": os_, "ms_step": ms_step, "flops": flops, "infos": infos, "launches": launches,
             "autotune": bool(tuning),
-            "kstats": kstats, "roof": roof, "acc": acc, "clocks": clk.summary(),
+            "kstats": kstats, "roof": roof, "roof_sm": roof_sm, "acc": acc, "clocks": clk.summary(),
             "steps": steps, "warmup": warmup}
 
 
@@ -618,8 +636,10 @@ def run_batch(args, w, rank, world, dist, local):
                            "parallelism": "replicas" if world > 1 else "single"},
                 "eff_tflops": world * arm["flops"] / (arm["ms_step"] / 1000.0) / 1e12,
                 "pd_model_flops": arm["flops"], "accuracy": arm["acc"], "roofline": arm["roof"],
+                "roofline_by_sm_time": arm["roof_sm"],
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": arm["launches"],
                 "kernel_ms": {k: round(v["ms"], 3) for k, v in arm["kstats"].items() if v["launches"]},
+                "kernel_sm_ms": sm_time(arm["kstats"]),
                 "kernel_gflop": {k: round(v["flops"] / 1e9, 1) for k, v in arm["kstats"].items()
                                  if v["launches"]},
                 "clocks": arm["clocks"]}
@@ -896,6 +916,7 @@ def main():
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches,
                 "kernel_ms": {k: round(v["ms"], 3) for k, v in kstats.items() if v["launches"]},
+                "kernel_sm_ms": sm_time(kstats),
                 "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
     h.close()

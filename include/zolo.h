@@ -408,14 +408,20 @@ const char* zolo_strerror(int code);
    without a graph, so that every pair times its kernel alone.  zolo_profile(0)
    stops.  zolo_profile_read synchronises on the pending events, fills up to
    max_entries records (one per kernel class: launches, summed device time,
-   summed algorithmic flops and bytes as stated by each launch site) and
-   returns the number of classes. */
+   summed algorithmic flops and bytes as stated by each launch site, and the
+   SM-time: each launch's device time times the share of the GPU's resident-
+   block slots its blocks take, blocks / (SMs x blocks per SM at the launch's
+   occupancy), at most 1; a launch site that does not state its blocks counts
+   as taking them all) and returns the number of classes.  With many calls in
+   flight at once (the batched call's lanes) the SM-time shows which classes
+   hold the GPU; the plain device time of a kernel on a few SMs does not. */
 typedef struct {
   char name[32];
   int64_t launches;
   double ms;
   double flops;
   double bytes;
+  double sm_ms;
 } zolo_kstat_t;
 uint64_t zolo_kernel_launches(void);
 int zolo_profile(int enable);

@@ -55,7 +55,7 @@ class ZoloInfo(ctypes.Structure):
 
 class KStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("ms", ctypes.c_double),
-                ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
+                ("flops", ctypes.c_double), ("bytes", ctypes.c_double), ("sm_ms", ctypes.c_double)]
 
 
 def _load():
@@ -141,11 +141,12 @@ def profile(enable: bool) -> None:
 
 
 def profile_read() -> dict:
-    """{class name: dict(launches, ms, flops, bytes)} accumulated since profile(True)."""
+    """{class name: dict(launches, ms, flops, bytes, sm_ms)} accumulated since profile(True)."""
     buf = (KStat * 16)()
     k = LIB.zolo_profile_read(buf, 16)
     return {buf[i].name.decode(): dict(launches=buf[i].launches, ms=buf[i].ms, flops=buf[i].flops,
-                                       bytes=buf[i].bytes) for i in range(min(k, 16))}
+                                       bytes=buf[i].bytes, sm_ms=buf[i].sm_ms)
+            for i in range(min(k, 16))}
 
 
 class ZoloError(RuntimeError):

@@ -557,6 +557,7 @@ unsigned rows_grid(int64_t m) {
 cudaError_t column_norms(const double* X, int64_t ldx, int64_t m, int64_t n, double* out,
                          cudaStream_t st) {
   ProfScope ps(kProfOther, st);
+  ps.blocks((const void*)column_norms_kernel, dim3(kJacThreads), (size_t)(0), dim3((unsigned)n));
   column_norms_kernel<<<(unsigned)n, kJacThreads, 0, st>>>(X, ldx, m, out);
   return cudaGetLastError();
 }
@@ -564,6 +565,7 @@ cudaError_t column_norms(const double* X, int64_t ldx, int64_t m, int64_t n, dou
 cudaError_t column_dots(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t m,
                         int64_t n, double* out, cudaStream_t st) {
   ProfScope ps(kProfOther, st);
+  ps.blocks((const void*)column_dots_kernel, dim3(kJacThreads), (size_t)(0), dim3((unsigned)n));
   column_dots_kernel<<<(unsigned)n, kJacThreads, 0, st>>>(A, lda, B, ldb, m, out);
   return cudaGetLastError();
 }
@@ -571,6 +573,7 @@ cudaError_t column_dots(const double* A, int64_t lda, const double* B, int64_t l
 cudaError_t scale_columns(double* X, int64_t ldx, int64_t m, int64_t n, const double* s, int invert,
                           cudaStream_t st) {
   ProfScope ps(kProfOther, st);
+  ps.blocks((const void*)scale_columns_kernel, dim3(256), (size_t)(0), dim3(dim3(rows_grid(m), (unsigned)n)));
   scale_columns_kernel<<<dim3(rows_grid(m), (unsigned)n), 256, 0, st>>>(X, ldx, m, s, invert);
   return cudaGetLastError();
 }
@@ -578,6 +581,7 @@ cudaError_t scale_columns(double* X, int64_t ldx, int64_t m, int64_t n, const do
 cudaError_t gather_columns(const double* X, int64_t ldx, double* Y, int64_t ldy, int64_t m,
                            int64_t n, const int* perm, const double* sign, cudaStream_t st) {
   ProfScope ps(kProfOther, st);
+  ps.blocks((const void*)gather_columns_kernel, dim3(256), (size_t)(0), dim3(dim3(rows_grid(m), (unsigned)n)));
   gather_columns_kernel<<<dim3(rows_grid(m), (unsigned)n), 256, 0, st>>>(X, ldx, Y, ldy, m, perm,
                                                                          sign);
   return cudaGetLastError();
@@ -587,6 +591,7 @@ cudaError_t transpose_lower(const double* R, int64_t ldr, double* X, int64_t ldx
                             cudaStream_t st) {
   const int64_t b = std::min<int64_t>((n * n + 255) / 256, 4096);
   ProfScope ps(kProfOther, st);
+  ps.blocks((const void*)transpose_lower_kernel, dim3(256), (size_t)(0), dim3((unsigned)std::max<int64_t>(b, 1)));
   transpose_lower_kernel<<<(unsigned)std::max<int64_t>(b, 1), 256, 0, st>>>(R, ldr, X, ldx, n);
   return cudaGetLastError();
 }
@@ -606,6 +611,7 @@ cudaError_t jacobi_sweep(double* X, int64_t ldx, int64_t m, int64_t n_even, int6
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)std::max(1, occ) * sms));
   if (cudaMemsetAsync(ver, 0, sizeof(int) * n_even, st) != cudaSuccess) return cudaErrorUnknown;
   ProfScope ps(kProfJacobi, st, 6.0 * (double)m * (double)items, 32.0 * (double)m * (double)items);
+  ps.blocks((const void*)jacobi_sweep_kernel, dim3(kJacThreads), 0, dim3(grid));
   int ne = (int)n_even, nr = (int)n_real;
   void* args[] = {&X, &ldx, &m, &ne, &nr, &tol, &status, &nrm2, &dsc, &ver, &err, &stall, &stall_ns};
   return cudaLaunchCooperativeKernel((const void*)jacobi_sweep_kernel, grid, kJacThreads, args, 0, st);
@@ -646,10 +652,12 @@ int eig_sym_jacobi(const double* H, int64_t ldh, int64_t n, double* V, int64_t l
   if (transpose_lower(w.R, n, w.X, n, n, st) != cudaSuccess) return 1;
   {
     ProfScope ps(kProfOther, st);
+    ps.blocks((const void*)to_f32_kernel, dim3(256), (size_t)(0), dim3(eg));
     to_f32_kernel<<<eg, 256, 0, st>>>(w.X, w.X32, nn);
   }
   {
     ProfScope ps(kProfOther, st);
+    ps.blocks((const void*)identity_f32_kernel, dim3(256), (size_t)(0), dim3(eg));
     identity_f32_kernel<<<eg, 256, 0, st>>>(w.Z32, n);
   }
   if (n > 1) {
@@ -681,6 +689,7 @@ int eig_sym_jacobi(const double* H, int64_t ldh, int64_t n, double* V, int64_t l
         // Gram and two products with Q per block pair: 6 (2 kJB)^2 m flops
         ProfScope ps(kProfJacobi32, st,
                      6.0 * kJW * kJW * (double)n * (double)(nb_even / 2) * (double)(nb_even - 1));
+        ps.blocks((const void*)jacobi32_block_sweep_kernel, dim3(kJacThreads), 0, dim3(grid));
         if (cudaLaunchCooperativeKernel((const void*)jacobi32_block_sweep_kernel, grid, kJacThreads,
                                         args, 0, st) != cudaSuccess)
           return 1;
@@ -699,6 +708,7 @@ int eig_sym_jacobi(const double* H, int64_t ldh, int64_t n, double* V, int64_t l
   // ---- Z orthonormal in FP64 (Cholesky QR: Z^T Z = R_z^T R_z, Z <- Z R_z^{-1})
   {
     ProfScope ps(kProfOther, st);
+    ps.blocks((const void*)to_f64_kernel, dim3(256), (size_t)(0), dim3(eg));
     to_f64_kernel<<<eg, 256, 0, st>>>(w.Z32, w.Z, nn);
   }
   {
@@ -732,6 +742,7 @@ int eig_sym_jacobi(const double* H, int64_t ldh, int64_t n, double* V, int64_t l
     if (sw > 0 && scale_columns(X, n, n, n, w.tmp, 0, st) != cudaSuccess) return 1;
     {
       ProfScope ps(kProfOther, st);
+      ps.blocks((const void*)fill_kernel, dim3(256), (size_t)(0), dim3((unsigned)((n + 255) / 256)));
       fill_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(w.tmp, n, 1.0);
     }
     if (column_dots(X, n, X, n, n, n, w.lam, st) != cudaSuccess) return 1;

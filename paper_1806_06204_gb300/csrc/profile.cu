@@ -10,6 +10,8 @@
 #include <mutex>
 #include <set>
 #include <utility>
+#include <map>
+#include <tuple>
 #include <vector>
 
 #include "../../include/zolo.h"
@@ -24,7 +26,7 @@ const char* kClassNames[kProfClasses] = {"gemm_f64", "qr_panel", "chol_diag", "j
 struct Pending {
   int cls;
   cudaEvent_t a, b;
-  double flops, bytes;
+  double flops, bytes, share;
 };
 
 std::atomic<uint64_t> g_launches{0};
@@ -54,6 +56,7 @@ void resolve_locked() {
       s.ms += ms;
       s.flops += p.flops;
       s.bytes += p.bytes;
+      s.sm_ms += ms * p.share;
     }
     g_pool.push_back(p.a);
     g_pool.push_back(p.b);
@@ -88,8 +91,35 @@ ProfScope::~ProfScope() {
   std::lock_guard<std::mutex> lk(g_mu);
   cudaEvent_t b = take_event();
   cudaEventRecord(b, st_);
-  g_pending.push_back({cls_, static_cast<cudaEvent_t>(a_), b, flops_, bytes_});
+  g_pending.push_back({cls_, static_cast<cudaEvent_t>(a_), b, flops_, bytes_, share_});
   if (g_pending.size() > 100000) resolve_locked();
+}
+
+void ProfScope::blocks(const void* kernel, dim3 block, size_t smem, dim3 grid) {
+  if (!a_) return;
+  const int threads = (int)(block.x * block.y * block.z);
+  const double count = (double)grid.x * grid.y * grid.z;
+  // (kernel, threads, smem) -> resident blocks per SM; SM count per device
+  static std::mutex mu;
+  static std::map<std::tuple<const void*, int, size_t, int>, int> occ;
+  int dev = 0, per_sm = 1, sms = 1;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto key = std::make_tuple(kernel, threads, smem, dev);
+    auto it = occ.find(key);
+    if (it == occ.end()) {
+      int o = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kernel, threads, smem) != cudaSuccess)
+        o = 1;
+      it = occ.emplace(key, o < 1 ? 1 : o).first;
+    }
+    per_sm = it->second;
+  }
+  const double f = count / ((double)sms * per_sm);
+  share_ = f < 1.0 ? f : 1.0;
 }
 
 void add_launches(int64_t n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }

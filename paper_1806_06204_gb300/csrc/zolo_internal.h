@@ -54,11 +54,16 @@ class ProfScope {
   ~ProfScope();
   ProfScope(const ProfScope&) = delete;
   ProfScope& operator=(const ProfScope&) = delete;
+  // The launch's blocks, for its SM-time: blocks / (SMs x blocks per SM of
+  // `kernel` at this block size and dynamic shared memory), at most 1.  Only
+  // queried while profiling is on.
+  void blocks(const void* kernel, dim3 block, size_t smem, dim3 grid);
 
  private:
   int cls_;
   cudaStream_t st_;
   double flops_, bytes_;
+  double share_ = 1.0;
   void* a_ = nullptr;
 };
 

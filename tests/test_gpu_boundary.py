@@ -118,3 +118,22 @@ def test_batched_estimates(zb, handle):
         bwd = zo.backward_error_pd(sm.A, q.cpu().numpy(), h.cpu().numpy())
         assert 0 < inf.bwd_est < 1e-13 and abs(inf.bwd_est - bwd) <= 0.5 * bwd + 1e-16
         assert 0 < inf.orth_est < 1e-13
+
+
+def test_profile_reports_sm_time_within_device_time(zb, handle):
+    # zolo_profile: per kernel class the summed device time and the SM-time (each
+    # launch's time times the share of the GPU's block slots its blocks take): a
+    # share is at most 1, so 0 < sm_ms <= ms; the QR panel of a 96-column matrix
+    # runs on one CTA per shift, a small share
+    sm = synth.square_geometric(96, 1e8, seed=1070)
+    zb.profile(True)
+    try:
+        zb.zolo_pd(handle, dev(sm.A), zb.opts(beta=float(sm.sigma[-1]), r=3))
+        st = zb.profile_read()
+    finally:
+        zb.profile(False)
+    used = {k: v for k, v in st.items() if v["launches"]}
+    assert "qr_panel" in used and "gemm_f64" in used
+    for k, v in used.items():
+        assert 0.0 < v["sm_ms"] <= v["ms"] * (1 + 1e-9), (k, v)
+    assert used["qr_panel"]["sm_ms"] < 0.1 * used["qr_panel"]["ms"]
