@@ -661,12 +661,15 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     for (int c = 0; c < nchunks; ++c) {
       if (!(ok = tc::mbar_wait(tfull, c & 1, err))) break;
       tc::tc_fence_after();
+      // one TMEM load (and one wait for it) per 16 columns where the warp has 16
+      constexpr int kLd = HALF % 16 == 0 ? 16 : 8;
 #pragma unroll
       for (int a = 0; a < kAcc; ++a) {
 #pragma unroll
-        for (int g = 0; g < HALF / 8; ++g) {
-          float v[8];
-          tc::tmem_ld8(tmem + lane_off + a * BN + half * HALF + g * 8, v);
+        for (int g = 0; g < HALF / kLd; ++g) {
+          float v[kLd];
+          if constexpr (kLd == 16) tc::tmem_ld16(tmem + lane_off + a * BN + half * HALF + g * kLd, v);
+          else tc::tmem_ld8(tmem + lane_off + a * BN + half * HALF + g * kLd, v);
           if (FORM == kFormFP8) {
             // raw integer level sums (|.| <= 2^24): levels 2..9 into 2^-48 units
             // (level 2 of a 4096-chunk is below 2^20: 2^58 per chunk, so about
@@ -674,9 +677,9 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
             // (times 2^(65 - 5L), exact)
             const int L = a + 2;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              if (L <= 9) iacc[g * 8 + i] += (long long)__float2int_rn(v[i]) << (48 - 5 * L);
-              else fm[g * 8 + i] += v[i] * __int_as_float((127 + 65 - 5 * L) << 23);
+            for (int i = 0; i < kLd; ++i) {
+              if (L <= 9) iacc[g * kLd + i] += (long long)__float2int_rn(v[i]) << (48 - 5 * L);
+              else fm[g * kLd + i] += v[i] * __int_as_float((127 + 65 - 5 * L) << 23);
             }
           } else if (FORM == kFormFP16) {
             // raw integer level sums (|.| <= 2^24): levels 2..7 into 2^-49 units;
@@ -684,23 +687,23 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
             // 2^-7, exact), whose rounding lies about 2^-56 below the leading level
             const int L = a + 2;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              if (L <= 7) iacc[g * 8 + i] += (long long)__float2int_rn(v[i]) << (49 - 7 * L);
-              else if (L == 8) fm[g * 8 + i] += v[i];
-              else fm[g * 8 + i] += v[i] * 0x1p-7f;
+            for (int i = 0; i < kLd; ++i) {
+              if (L <= 7) iacc[g * kLd + i] += (long long)__float2int_rn(v[i]) << (49 - 7 * L);
+              else if (L == 8) fm[g * kLd + i] += v[i];
+              else fm[g * kLd + i] += v[i] * 0x1p-7f;
             }
           } else if (a < kAcc - 1) {
             const int L = a + 2;
             // times 2^6L: an exact integer below 2^24
             const float up = __int_as_float((127 + kBeta * L) << 23);
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
-              iacc[g * 8 + i] += (long long)__float2int_rn(v[i] * up) << (48 - kBeta * L);
+            for (int i = 0; i < kLd; ++i)
+              iacc[g * kLd + i] += (long long)__float2int_rn(v[i] * up) << (48 - kBeta * L);
           } else {
             // merged levels >= 9 stay in a float (2^-24 of a value 2^-30 below the
             // leading level: rounding them to the int64's unit would cost 2^-49)
 #pragma unroll
-            for (int i = 0; i < 8; ++i) fm[g * 8 + i] += v[i];
+            for (int i = 0; i < kLd; ++i) fm[g * kLd + i] += v[i];
           }
         }
       }
@@ -715,34 +718,53 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         const int ei = p.ea[b * p.Mpad + row];
         const int* ebb = p.eb + b * p.Npad + n0 + half * HALF;
         const double al = p.alpha[b];
+        // eight outputs at a time: their addends (beta C_in, or the running sum
+        // in reduce mode) loaded together first, then formed and stored (a load
+        // after a store to C could alias it, so a plain loop waits for each)
+        const bool use_cin = Cin && p.beta != 0.0;
 #pragma unroll
-        for (int j = 0; j < HALF; ++j) {
-          const int col = n0 + half * HALF + j;
-          const int ci = p.swap ? col : row, cj = p.swap ? row : col;
-          if (row < (p.swap ? p.N : p.M) && col < (p.swap ? p.M : p.N)) {
-            // the integer part and the float part, each scaled by the power of
-            // two 2^(e_i + f_j) in its exponent field, joined by one FP64 add
-            // (the same single rounding as converting the int64 and adding the
-            // float part at its weight)
-            const int e = ei + __ldg(ebb + j);
-            double v;
-            if (FORM == kFormFP8)
-              v = i64_scaled(iacc[j], e - 48) + f32_scaled(fm[j], e - 48 - 17);
-            else if (FORM == kFormFP16)
-              v = i64_scaled(iacc[j], e - 49) + f32_scaled(fm[j], e - 49 - 7);
-            else
-              v = i64_scaled(iacc[j], e - 48) + f32_scaled(fm[j], e);
-            if (al == -1.0) v = __longlong_as_double(__double_as_longlong(v) ^ (long long)0x8000000000000000ull);
-            else if (al != 1.0) v *= al;
-            if (first) {
-              if (Cin && p.beta != 0.0) v = fma(p.beta, Cin[ci + (int64_t)cj * p.ldcin], v);
-            } else {
-              v += C[ci + (int64_t)cj * p.ldc];
+        for (int j0 = 0; j0 < HALF; j0 += 8) {
+          double add[8];
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj) {
+            const int col = n0 + half * HALF + j0 + jj;
+            const int ci = p.swap ? col : row, cj = p.swap ? row : col;
+            add[jj] = 0.0;
+            if (row < (p.swap ? p.N : p.M) && col < (p.swap ? p.M : p.N)) {
+              if (!first) add[jj] = C[ci + (int64_t)cj * p.ldc];
+              else if (use_cin) add[jj] = Cin[ci + (int64_t)cj * p.ldcin];
             }
-            C[ci + (int64_t)cj * p.ldc] = v;
           }
-          iacc[j] = 0;
-          fm[j] = 0.f;
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj) {
+            const int j = j0 + jj;
+            const int col = n0 + half * HALF + j;
+            const int ci = p.swap ? col : row, cj = p.swap ? row : col;
+            if (row < (p.swap ? p.N : p.M) && col < (p.swap ? p.M : p.N)) {
+              // the integer part and the float part, each scaled by the power of
+              // two 2^(e_i + f_j) in its exponent field, joined by one FP64 add
+              // (the same single rounding as converting the int64 and adding the
+              // float part at its weight)
+              const int e = ei + __ldg(ebb + j);
+              double v;
+              if (FORM == kFormFP8)
+                v = i64_scaled(iacc[j], e - 48) + f32_scaled(fm[j], e - 48 - 17);
+              else if (FORM == kFormFP16)
+                v = i64_scaled(iacc[j], e - 49) + f32_scaled(fm[j], e - 49 - 7);
+              else
+                v = i64_scaled(iacc[j], e - 48) + f32_scaled(fm[j], e);
+              if (al == -1.0) v = __longlong_as_double(__double_as_longlong(v) ^ (long long)0x8000000000000000ull);
+              else if (al != 1.0) v *= al;
+              if (first) {
+                if (use_cin) v = fma(p.beta, add[jj], v);
+              } else {
+                v += add[jj];
+              }
+              C[ci + (int64_t)cj * p.ldc] = v;
+            }
+            iacc[j] = 0;
+            fm[j] = 0.f;
+          }
         }
       }
     }
