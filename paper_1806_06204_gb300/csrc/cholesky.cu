@@ -141,7 +141,8 @@ tri_inv_kernel(const double* __restrict__ R, int64_t n, double* __restrict__ Rin
 cudaError_t tri_inv_diag_blocks(const double* R, int64_t n, double* Rinv, int* status,
                                 cudaStream_t st) {
   ProfScope ps(kProfCholDiag, st);
-  ps.blocks((const void*)tri_inv_kernel<kCholNB>, dim3(kCholNB), (size_t)(0), dim3((unsigned)((n + kCholNB - 1) / kCholNB)));
+  ps.blocks((const void*)tri_inv_kernel<kCholNB>, dim3(kCholNB), 0,
+            dim3((unsigned)((n + kCholNB - 1) / kCholNB)));
   tri_inv_kernel<kCholNB><<<(unsigned)((n + kCholNB - 1) / kCholNB), kCholNB, 0, st>>>(R, n, Rinv,
                                                                                      status);
   return cudaGetLastError();
@@ -155,7 +156,7 @@ cudaError_t cholesky_upper_batched(const CholBuffers& b, int64_t n, int r, int* 
     const int nbk = (int)(n - k0 < NB ? n - k0 : NB);
     {
       ProfScope ps(kProfCholDiag, st, r * 2.0 / 3.0 * (double)nbk * nbk * nbk);
-      ps.blocks((const void*)chol_diag_kernel<NB>, dim3(kDiagThreads), (size_t)(0), dim3(r));
+      ps.blocks((const void*)chol_diag_kernel<NB>, dim3(kDiagThreads), 0, dim3(r));
       chol_diag_kernel<NB><<<r, kDiagThreads, 0, st>>>(b.Z, b.strideZ, n, k0, nbk, b.Rinv,
                                                        b.strideRinv, status);
     }
@@ -200,7 +201,7 @@ __global__ void copy_cols_kernel(const double* __restrict__ src, int64_t lds, in
 cudaError_t copy_cols(const double* src, int64_t lds, int64_t strideS, double* dst, int64_t ldd,
                       int64_t strideD, int64_t m, int w, int r, cudaStream_t st) {
   ProfScope ps(kProfOther, st, 0.0, 16.0 * m * w * r);
-  ps.blocks((const void*)copy_cols_kernel, dim3(256), (size_t)(0), dim3(dim3((unsigned)((m * w + 255) / 256), r)));
+  ps.blocks((const void*)copy_cols_kernel, dim3(256), 0, dim3((unsigned)((m * w + 255) / 256), r));
   copy_cols_kernel<<<dim3((unsigned)((m * w + 255) / 256), r), 256, 0, st>>>(src, lds, strideS, dst,
                                                                              ldd, strideD, m, w);
   return cudaGetLastError();

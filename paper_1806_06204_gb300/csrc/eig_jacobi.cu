@@ -14,8 +14,9 @@
 // X32 = R^T with the rotations accumulated in Z32, as block Jacobi on 16-column
 // blocks (one cooperative launch per sweep, rounds separated by a bounded grid
 // barrier).  Z is then made orthonormal in FP64 (Cholesky QR), X = R^T Z is
-// formed in FP64, and FP64 sweeps (one launch per round, one CTA per column
-// pair) finish from cosines ~1e-5 in a few quadratically convergent sweeps.
+// formed in FP64, and FP64 sweeps (one cooperative dataflow launch per sweep,
+// one CTA per column pair at a time) finish from cosines ~1e-4 in a few
+// quadratically convergent sweeps.
 // FP32 sweeps stop when fewer than n rotations (cosines above 8e-6) were needed
 // in a sweep (25 sweeps at most): the FP64 sweeps start from cosines of about
 // 1e-4 whatever the last FP32 sweeps do, since Z's FP32 rounding, times R^T,
@@ -557,7 +558,7 @@ unsigned rows_grid(int64_t m) {
 cudaError_t column_norms(const double* X, int64_t ldx, int64_t m, int64_t n, double* out,
                          cudaStream_t st) {
   ProfScope ps(kProfOther, st);
-  ps.blocks((const void*)column_norms_kernel, dim3(kJacThreads), (size_t)(0), dim3((unsigned)n));
+  ps.blocks((const void*)column_norms_kernel, dim3(kJacThreads), 0, dim3((unsigned)n));
   column_norms_kernel<<<(unsigned)n, kJacThreads, 0, st>>>(X, ldx, m, out);
   return cudaGetLastError();
 }
@@ -565,7 +566,7 @@ cudaError_t column_norms(const double* X, int64_t ldx, int64_t m, int64_t n, dou
 cudaError_t column_dots(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t m,
                         int64_t n, double* out, cudaStream_t st) {
   ProfScope ps(kProfOther, st);
-  ps.blocks((const void*)column_dots_kernel, dim3(kJacThreads), (size_t)(0), dim3((unsigned)n));
+  ps.blocks((const void*)column_dots_kernel, dim3(kJacThreads), 0, dim3((unsigned)n));
   column_dots_kernel<<<(unsigned)n, kJacThreads, 0, st>>>(A, lda, B, ldb, m, out);
   return cudaGetLastError();
 }
@@ -573,7 +574,7 @@ cudaError_t column_dots(const double* A, int64_t lda, const double* B, int64_t l
 cudaError_t scale_columns(double* X, int64_t ldx, int64_t m, int64_t n, const double* s, int invert,
                           cudaStream_t st) {
   ProfScope ps(kProfOther, st);
-  ps.blocks((const void*)scale_columns_kernel, dim3(256), (size_t)(0), dim3(dim3(rows_grid(m), (unsigned)n)));
+  ps.blocks((const void*)scale_columns_kernel, dim3(256), 0, dim3(rows_grid(m), (unsigned)n));
   scale_columns_kernel<<<dim3(rows_grid(m), (unsigned)n), 256, 0, st>>>(X, ldx, m, s, invert);
   return cudaGetLastError();
 }
@@ -581,7 +582,7 @@ cudaError_t scale_columns(double* X, int64_t ldx, int64_t m, int64_t n, const do
 cudaError_t gather_columns(const double* X, int64_t ldx, double* Y, int64_t ldy, int64_t m,
                            int64_t n, const int* perm, const double* sign, cudaStream_t st) {
   ProfScope ps(kProfOther, st);
-  ps.blocks((const void*)gather_columns_kernel, dim3(256), (size_t)(0), dim3(dim3(rows_grid(m), (unsigned)n)));
+  ps.blocks((const void*)gather_columns_kernel, dim3(256), 0, dim3(rows_grid(m), (unsigned)n));
   gather_columns_kernel<<<dim3(rows_grid(m), (unsigned)n), 256, 0, st>>>(X, ldx, Y, ldy, m, perm,
                                                                          sign);
   return cudaGetLastError();
@@ -591,7 +592,8 @@ cudaError_t transpose_lower(const double* R, int64_t ldr, double* X, int64_t ldx
                             cudaStream_t st) {
   const int64_t b = std::min<int64_t>((n * n + 255) / 256, 4096);
   ProfScope ps(kProfOther, st);
-  ps.blocks((const void*)transpose_lower_kernel, dim3(256), (size_t)(0), dim3((unsigned)std::max<int64_t>(b, 1)));
+  ps.blocks((const void*)transpose_lower_kernel, dim3(256), 0,
+            dim3((unsigned)std::max<int64_t>(b, 1)));
   transpose_lower_kernel<<<(unsigned)std::max<int64_t>(b, 1), 256, 0, st>>>(R, ldr, X, ldx, n);
   return cudaGetLastError();
 }
@@ -652,12 +654,12 @@ int eig_sym_jacobi(const double* H, int64_t ldh, int64_t n, double* V, int64_t l
   if (transpose_lower(w.R, n, w.X, n, n, st) != cudaSuccess) return 1;
   {
     ProfScope ps(kProfOther, st);
-    ps.blocks((const void*)to_f32_kernel, dim3(256), (size_t)(0), dim3(eg));
+    ps.blocks((const void*)to_f32_kernel, dim3(256), 0, dim3(eg));
     to_f32_kernel<<<eg, 256, 0, st>>>(w.X, w.X32, nn);
   }
   {
     ProfScope ps(kProfOther, st);
-    ps.blocks((const void*)identity_f32_kernel, dim3(256), (size_t)(0), dim3(eg));
+    ps.blocks((const void*)identity_f32_kernel, dim3(256), 0, dim3(eg));
     identity_f32_kernel<<<eg, 256, 0, st>>>(w.Z32, n);
   }
   if (n > 1) {
@@ -708,7 +710,7 @@ int eig_sym_jacobi(const double* H, int64_t ldh, int64_t n, double* V, int64_t l
   // ---- Z orthonormal in FP64 (Cholesky QR: Z^T Z = R_z^T R_z, Z <- Z R_z^{-1})
   {
     ProfScope ps(kProfOther, st);
-    ps.blocks((const void*)to_f64_kernel, dim3(256), (size_t)(0), dim3(eg));
+    ps.blocks((const void*)to_f64_kernel, dim3(256), 0, dim3(eg));
     to_f64_kernel<<<eg, 256, 0, st>>>(w.Z32, w.Z, nn);
   }
   {
@@ -742,7 +744,7 @@ int eig_sym_jacobi(const double* H, int64_t ldh, int64_t n, double* V, int64_t l
     if (sw > 0 && scale_columns(X, n, n, n, w.tmp, 0, st) != cudaSuccess) return 1;
     {
       ProfScope ps(kProfOther, st);
-      ps.blocks((const void*)fill_kernel, dim3(256), (size_t)(0), dim3((unsigned)((n + 255) / 256)));
+      ps.blocks((const void*)fill_kernel, dim3(256), 0, dim3((unsigned)((n + 255) / 256)));
       fill_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(w.tmp, n, 1.0);
     }
     if (column_dots(X, n, X, n, n, n, w.lam, st) != cudaSuccess) return 1;

@@ -288,7 +288,7 @@ Vec8 pack(const double* v, int r) {
 cudaError_t scale_copy(const double* A, int64_t lda, double* X, int64_t ldx, int64_t m, int64_t n,
                        double s, cudaStream_t st) {
   ProfScope ps(kProfOther, st);
-  ps.blocks((const void*)scale_copy_kernel, dim3(kThreads), (size_t)(0), dim3(grid_for(m * n)));
+  ps.blocks((const void*)scale_copy_kernel, dim3(kThreads), 0, dim3(grid_for(m * n)));
   scale_copy_kernel<<<grid_for(m * n), kThreads, 0, st>>>(A, lda, X, ldx, m, n, s);
   return cudaGetLastError();
 }
@@ -303,7 +303,7 @@ cudaError_t init_stacked(const double* X, int64_t ldx, double* W, int64_t stride
                          int64_t n, const double* sqrt_c, int r, cudaStream_t st) {
   dim3 grid(grid_for((m + n) * n), r);
   ProfScope ps(kProfOther, st);
-  ps.blocks((const void*)init_stacked_kernel, dim3(kThreads), (size_t)(0), dim3(grid));
+  ps.blocks((const void*)init_stacked_kernel, dim3(kThreads), 0, dim3(grid));
   init_stacked_kernel<<<grid, kThreads, 0, st>>>(X, ldx, W, strideW, m, n, pack(sqrt_c, r));
   return cudaGetLastError();
 }
@@ -312,7 +312,7 @@ cudaError_t init_q_identity(double* Q, int64_t strideQ, int64_t m, int64_t n, in
                             cudaStream_t st) {
   dim3 grid(grid_for((m + n) * n), r);
   ProfScope ps(kProfOther, st);
-  ps.blocks((const void*)init_q_identity_kernel, dim3(kThreads), (size_t)(0), dim3(grid));
+  ps.blocks((const void*)init_q_identity_kernel, dim3(kThreads), 0, dim3(grid));
   init_q_identity_kernel<<<grid, kThreads, 0, st>>>(Q, strideQ, m, n);
   return cudaGetLastError();
 }
@@ -321,7 +321,7 @@ cudaError_t init_shifted(const double* G, double* Z, int64_t strideZ, int64_t n,
                          int r, cudaStream_t st) {
   dim3 grid(grid_for(n * n), r);
   ProfScope ps(kProfOther, st);
-  ps.blocks((const void*)init_shifted_kernel, dim3(kThreads), (size_t)(0), dim3(grid));
+  ps.blocks((const void*)init_shifted_kernel, dim3(kThreads), 0, dim3(grid));
   init_shifted_kernel<<<grid, kThreads, 0, st>>>(G, Z, strideZ, n, pack(shift, r));
   return cudaGetLastError();
 }
@@ -331,13 +331,13 @@ cudaError_t combine(const double* X, int64_t ldx, double* Xn, int64_t ldxn, int6
                     int nt, double* partials, double* norms, int* status, cudaStream_t st) {
   {
     ProfScope ps(kProfCombine, st, 2.0 * (double)m * n * (nt + 2), 8.0 * (double)m * n * (nt + 2));
-    ps.blocks((const void*)combine_kernel, dim3(kThreads), (size_t)(0), dim3(kReduceBlocks));
+    ps.blocks((const void*)combine_kernel, dim3(kThreads), 0, dim3(kReduceBlocks));
     combine_kernel<<<kReduceBlocks, kThreads, 0, st>>>(X, ldx, Xn, ldxn, m, n, mhat, T, ldt,
                                                        strideT, pack(coef, nt), nt, partials,
                                                        status);
   }
   ProfScope ps(kProfOther, st);
-  ps.blocks((const void*)finish_pairs_kernel, dim3(1024), (size_t)(0), dim3(1));
+  ps.blocks((const void*)finish_pairs_kernel, dim3(1024), 0, dim3(1));
   finish_pairs_kernel<<<1, 1024, 0, st>>>(partials, kReduceBlocks, norms);
   return cudaGetLastError();
 }
@@ -345,7 +345,7 @@ cudaError_t combine(const double* X, int64_t ldx, double* Xn, int64_t ldxn, int6
 cudaError_t weighted_sum(const double* T, int64_t ldt, int64_t strideT, const double* coef, int nt,
                          double* S, int64_t lds, int64_t m, int64_t n, cudaStream_t st) {
   ProfScope ps(kProfCombine, st, 2.0 * (double)m * n * nt, 8.0 * (double)m * n * (nt + 1));
-  ps.blocks((const void*)weighted_sum_kernel, dim3(kThreads), (size_t)(0), dim3(grid_for(m * n)));
+  ps.blocks((const void*)weighted_sum_kernel, dim3(kThreads), 0, dim3(grid_for(m * n)));
   weighted_sum_kernel<<<grid_for(m * n), kThreads, 0, st>>>(T, ldt, strideT, pack(coef, nt), nt, S,
                                                              lds, m, n);
   return cudaGetLastError();
@@ -357,7 +357,8 @@ cudaError_t guard_fill(void* p, size_t bytes, cudaStream_t st) {
 
 cudaError_t guard_check(const void* p, size_t bytes, int* flag, cudaStream_t st) {
   ProfScope ps(kProfOther, st);
-  ps.blocks((const void*)guard_check_kernel, dim3(256), (size_t)(0), dim3((unsigned)((bytes + 255) / 256 < 64 ? (bytes + 255) / 256 : 64)));
+  ps.blocks((const void*)guard_check_kernel, dim3(256), 0,
+            dim3((unsigned)((bytes + 255) / 256 < 64 ? (bytes + 255) / 256 : 64)));
   guard_check_kernel<<<(unsigned)((bytes + 255) / 256 < 64 ? (bytes + 255) / 256 : 64), 256, 0, st>>>(
       static_cast<const unsigned char*>(p), bytes, flag);
   return cudaGetLastError();
@@ -365,14 +366,14 @@ cudaError_t guard_check(const void* p, size_t bytes, int* flag, cudaStream_t st)
 
 cudaError_t flag_to_double(const int* flag, double* out, cudaStream_t st) {
   ProfScope ps(kProfOther, st);
-  ps.blocks((const void*)flag_to_double_kernel, dim3(1), (size_t)(0), dim3(1));
+  ps.blocks((const void*)flag_to_double_kernel, dim3(1), 0, dim3(1));
   flag_to_double_kernel<<<1, 1, 0, st>>>(flag, out);
   return cudaGetLastError();
 }
 
 cudaError_t mirror_upper(double* W, int64_t ldw, int64_t n, cudaStream_t st) {
   ProfScope ps(kProfOther, st);
-  ps.blocks((const void*)mirror_upper_kernel, dim3(kThreads), (size_t)(0), dim3(grid_for(n * n)));
+  ps.blocks((const void*)mirror_upper_kernel, dim3(kThreads), 0, dim3(grid_for(n * n)));
   mirror_upper_kernel<<<grid_for(n * n), kThreads, 0, st>>>(W, ldw, n);
   return cudaGetLastError();
 }
@@ -380,7 +381,7 @@ cudaError_t mirror_upper(double* W, int64_t ldw, int64_t n, cudaStream_t st) {
 cudaError_t symmetrize(const double* M, int64_t ldm, double* H, int64_t ldh, int64_t n,
                        cudaStream_t st) {
   ProfScope ps(kProfOther, st);
-  ps.blocks((const void*)symmetrize_kernel, dim3(kThreads), (size_t)(0), dim3(grid_for(n * n)));
+  ps.blocks((const void*)symmetrize_kernel, dim3(kThreads), 0, dim3(grid_for(n * n)));
   symmetrize_kernel<<<grid_for(n * n), kThreads, 0, st>>>(M, ldm, H, ldh, n);
   return cudaGetLastError();
 }
@@ -388,7 +389,7 @@ cudaError_t symmetrize(const double* M, int64_t ldm, double* H, int64_t ldh, int
 cudaError_t check_finite(const double* A, int64_t lda, int64_t m, int64_t n, int* status,
                          cudaStream_t st) {
   ProfScope ps(kProfOther, st);
-  ps.blocks((const void*)check_finite_kernel, dim3(kThreads), (size_t)(0), dim3(grid_for(m * n)));
+  ps.blocks((const void*)check_finite_kernel, dim3(kThreads), 0, dim3(grid_for(m * n)));
   check_finite_kernel<<<grid_for(m * n), kThreads, 0, st>>>(A, lda, m, n, status);
   return cudaGetLastError();
 }
@@ -403,17 +404,18 @@ cudaError_t alpha_bound_sums(const double* A, int64_t lda, int64_t m, int64_t n,
   const int nchunk = (int)((n + kAbsChunk - 1) / kAbsChunk);
   {
     ProfScope ps(kProfOther, st);
-    ps.blocks((const void*)row_abs_partial_kernel, dim3(256), (size_t)(0), dim3(dim3((unsigned)((m + 255) / 256), nchunk)));
+    ps.blocks((const void*)row_abs_partial_kernel, dim3(256), 0,
+              dim3((unsigned)((m + 255) / 256), nchunk));
     row_abs_partial_kernel<<<dim3((unsigned)((m + 255) / 256), nchunk), 256, 0, st>>>(A, lda, m, n,
                                                                                       part);
   }
   {
     ProfScope ps(kProfOther, st);
-    ps.blocks((const void*)col_abs_kernel, dim3(256), (size_t)(0), dim3((unsigned)((n + 7) / 8)));
+    ps.blocks((const void*)col_abs_kernel, dim3(256), 0, dim3((unsigned)((n + 7) / 8)));
     col_abs_kernel<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(A, lda, m, n, colsum);
   }
   ProfScope ps(kProfOther, st);
-  ps.blocks((const void*)abs_norms_finish_kernel, dim3(1024), (size_t)(0), dim3(1));
+  ps.blocks((const void*)abs_norms_finish_kernel, dim3(1024), 0, dim3(1));
   abs_norms_finish_kernel<<<1, 1024, 0, st>>>(part, m, nchunk, colsum, n, out);
   return cudaGetLastError();
 }
@@ -430,11 +432,11 @@ cudaError_t gram_identity_dev2(const double* G, int64_t ldg, int64_t n, double* 
                                double* out, cudaStream_t st) {
   {
     ProfScope ps(kProfOther, st);
-    ps.blocks((const void*)gram_dev_kernel, dim3(kThreads), (size_t)(0), dim3(kReduceBlocks));
+    ps.blocks((const void*)gram_dev_kernel, dim3(kThreads), 0, dim3(kReduceBlocks));
     gram_dev_kernel<<<kReduceBlocks, kThreads, 0, st>>>(G, ldg, n, partials);
   }
   ProfScope ps(kProfOther, st);
-  ps.blocks((const void*)finish_pairs_kernel, dim3(1024), (size_t)(0), dim3(1));
+  ps.blocks((const void*)finish_pairs_kernel, dim3(1024), 0, dim3(1));
   finish_pairs_kernel<<<1, 1024, 0, st>>>(partials, kReduceBlocks, out);
   return cudaGetLastError();
 }
@@ -443,11 +445,11 @@ cudaError_t frob_norm2(const double* A, int64_t lda, int64_t m, int64_t n, doubl
                        double* out, cudaStream_t st) {
   {
     ProfScope ps(kProfOther, st);
-    ps.blocks((const void*)frob_kernel, dim3(kThreads), (size_t)(0), dim3(kReduceBlocks));
+    ps.blocks((const void*)frob_kernel, dim3(kThreads), 0, dim3(kReduceBlocks));
     frob_kernel<<<kReduceBlocks, kThreads, 0, st>>>(A, lda, m, n, partials);
   }
   ProfScope ps(kProfOther, st);
-  ps.blocks((const void*)finish_pairs_kernel, dim3(1024), (size_t)(0), dim3(1));
+  ps.blocks((const void*)finish_pairs_kernel, dim3(1024), 0, dim3(1));
   finish_pairs_kernel<<<1, 1024, 0, st>>>(partials, kReduceBlocks, out);
   return cudaGetLastError();
 }

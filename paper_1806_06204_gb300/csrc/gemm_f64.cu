@@ -162,7 +162,8 @@ cudaError_t launch(const GemmArgs& g, int ksplit, double* P, cudaStream_t st) {
                        8.0 * nz * (double)g.M * g.N * (g.beta != 0.0 ? 2 : 1);
   {
     ProfScope ps(kProfGemm, st, gemm_flops(g), bytes);
-    ps.blocks((const void*)gemm_f64_kernel<BM, BN, 16, 4, 4>, dim3((BM / 4) * (BN / 4)), (size_t)(0), dim3(grid));
+    ps.blocks((const void*)gemm_f64_kernel<BM, BN, 16, 4, 4>, dim3((BM / 4) * (BN / 4)), 0,
+              dim3(grid));
     gemm_f64_kernel<BM, BN, 16, 4, 4><<<grid, (BM / 4) * (BN / 4), 0, st>>>(g, ksplit, P);
   }
   if (ksplit > 1) {
@@ -170,7 +171,7 @@ cudaError_t launch(const GemmArgs& g, int ksplit, double* P, cudaStream_t st) {
     const int64_t mn = (int64_t)g.M * g.N;
     const unsigned bx = (unsigned)std::min<int64_t>((mn + 255) / 256, 2048);
     ProfScope ps(kProfOther, st, 0.0, 8.0 * nz * mn * (ksplit + 1));
-    ps.blocks((const void*)splitk_reduce_kernel<BM, BN>, dim3(256), (size_t)(0), dim3(dim3(bx, nz)));
+    ps.blocks((const void*)splitk_reduce_kernel<BM, BN>, dim3(256), 0, dim3(bx, nz));
     splitk_reduce_kernel<BM, BN><<<dim3(bx, nz), 256, 0, st>>>(g, ksplit, P);
   }
   return cudaGetLastError();
@@ -206,7 +207,7 @@ cudaError_t gemm_f64_variant(const GemmArgs& g, int variant, double* scratch,
     const int nz = g.reduce ? 1 : g.batch;
     dim3 grid((unsigned)((g.M * (int64_t)g.N + 255) / 256), 1, nz);
     ProfScope ps(kProfOther, st);
-    ps.blocks((const void*)gemm_beta_only, dim3(256), (size_t)(0), dim3(grid));
+    ps.blocks((const void*)gemm_beta_only, dim3(256), 0, dim3(grid));
     gemm_beta_only<<<grid, 256, 0, st>>>(g);
     return cudaGetLastError();
   }

@@ -840,7 +840,7 @@ cudaError_t slice_operand(const double* X, int64_t ldx, int64_t strideX, int tra
   ProfScope ps(kProfSlice, st, 0.0,
                (8.0 + (double)Form<FORM>::kElem * S) * batch * rows_pad * (double)K_pad);
   dim3 grid((unsigned)(K_pad / 64), (unsigned)(rows_pad / 32), batch);
-  ps.blocks((const void*)slice_kernel<S, FORM>, dim3(dim3(32, 8)), (size_t)(0), dim3(grid));
+  ps.blocks((const void*)slice_kernel<S, FORM>, dim3(32, 8), 0, dim3(grid));
   slice_kernel<S, FORM><<<grid, dim3(32, 8), 0, st>>>(X, ldx, strideX, trans, rows, K, e, out,
                                                       rows_pad, K_pad, ek, esign);
   return cudaGetLastError();
@@ -883,7 +883,7 @@ cudaError_t run_split(const GemmArgs& g, SplitWork& w, cudaStream_t st) {
   if (keq) {
     ProfScope ps(kProfSlice, st, 0.0, 8.0 * nb * (double)N * K);
     const double* Xo = swap ? Xa : Xb;
-    ps.blocks((const void*)col_exp_kernel, dim3(dim3(32, 8)), (size_t)(0), dim3(dim3((unsigned)(Kpad / 32), 1, nb)));
+    ps.blocks((const void*)col_exp_kernel, dim3(32, 8), 0, dim3((unsigned)(Kpad / 32), 1, nb));
     col_exp_kernel<<<dim3((unsigned)(Kpad / 32), 1, nb), dim3(32, 8), 0, st>>>(
         Xo, swap ? lda : ldb, swap ? sta : stb, swap ? ta : tb, swap ? M : N, K, ek, Kpad);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
@@ -894,7 +894,8 @@ cudaError_t run_split(const GemmArgs& g, SplitWork& w, cudaStream_t st) {
     const SliceOp ob{Xb, ldb, stb, tb, N, Npad, -sign_a, eb, sb};
     ProfScope ps(kProfSlice, st, 0.0,
                  (16.0 + (double)Form<FORM>::kElem * S) * nb * (double)(Mpad + Npad) * Kpad);
-    ps.blocks((const void*)slice_fused_kernel<S, FORM>, dim3(dim3(32, 8)), (size_t)(0), dim3(dim3((unsigned)((Mpad + Npad) / 32), 1, nb)));
+    ps.blocks((const void*)slice_fused_kernel<S, FORM>, dim3(32, 8), 0,
+              dim3((unsigned)((Mpad + Npad) / 32), 1, nb));
     slice_fused_kernel<S, FORM><<<dim3((unsigned)((Mpad + Npad) / 32), 1, nb), dim3(32, 8), 0, st>>>(
         oa, ob, Mpad / 32, K, Kpad, ek);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
@@ -929,7 +930,7 @@ cudaError_t run_split(const GemmArgs& g, SplitWork& w, cudaStream_t st) {
   }
   dim3 grid((unsigned)(Npad / BN), (unsigned)(Mpad / kTileM), g.reduce ? 1 : nb);
   ProfScope ps(kProfSplitGemm, st, gemm_flops(g), 0.0);
-  ps.blocks((const void*)split_gemm_kernel<BN, S, FORM>, dim3(kThreads), (size_t)(L::kAlloc), dim3(grid));
+  ps.blocks((const void*)split_gemm_kernel<BN, S, FORM>, dim3(kThreads), L::kAlloc, dim3(grid));
   split_gemm_kernel<BN, S, FORM><<<grid, kThreads, L::kAlloc, st>>>(mA, mB, p);
   err = cudaGetLastError();
   if (err != cudaSuccess && std::getenv("ZOLO_DEBUG")) {

@@ -532,14 +532,14 @@ cudaError_t ts_product(const double* A, int64_t lda, int64_t strideA, const doub
   for (int t = 0; t < tl.n; ++t) fl += 2.0 * tl.mt[t] * tl.nt[t] * (double)K * r;
   {
     ProfScope ps(kProfGemm, st, fl, 0.0);
-    ps.blocks((const void*)ts_partial_kernel, dim3(kTsThreads), (size_t)(0), dim3(dim3(nchunks, tl.n, r)));
+    ps.blocks((const void*)ts_partial_kernel, dim3(kTsThreads), 0, dim3(nchunks, tl.n, r));
     ts_partial_kernel<<<dim3(nchunks, tl.n, r), kTsThreads, 0, st>>>(A, lda, strideA, B, ldb,
                                                                      strideB, K, tl, P);
   }
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   ProfScope ps(kProfOther, st);
-  ps.blocks((const void*)ts_reduce_kernel, dim3(256), (size_t)(0), dim3(dim3(kTsMaxTile / 256, tl.n, r)));
+  ps.blocks((const void*)ts_reduce_kernel, dim3(256), 0, dim3(kTsMaxTile / 256, tl.n, r));
   ts_reduce_kernel<<<dim3(kTsMaxTile / 256, tl.n, r), 256, 0, st>>>(P, nchunks, tl, C, ldc, strideC);
   return cudaGetLastError();
 }
@@ -678,7 +678,7 @@ cudaError_t structured_qr_q(const QrBuffers& b, int64_t m, int64_t n, int r, int
     double* Tb = b.Tb + (int64_t)blk * NBb * NBb;
     {
       ProfScope ps(kProfOther, st);
-      ps.blocks((const void*)tb_init_kernel, dim3(256), (size_t)(0), dim3(dim3((nbb * nbb + 255) / 256, r)));
+      ps.blocks((const void*)tb_init_kernel, dim3(256), 0, dim3((nbb * nbb + 255) / 256, r));
       tb_init_kernel<<<dim3((nbb * nbb + 255) / 256, r), 256, 0, st>>>(b.T, b.strideT, Tb,
                                                                       b.strideTb, (int)(c0b / NB), nbb);
     }
@@ -704,7 +704,7 @@ cudaError_t structured_qr_q(const QrBuffers& b, int64_t m, int64_t n, int r, int
         const int pairs = (nbb + 2 * h - 1) / (2 * h);
         {
           ProfScope ps(kProfOther, st);
-          ps.blocks((const void*)tb_merge_kernel, dim3(NBb / 2), (size_t)(0), dim3(dim3(h, pairs, r)));
+          ps.blocks((const void*)tb_merge_kernel, dim3(NBb / 2), 0, dim3(h, pairs, r));
           tb_merge_kernel<<<dim3(h, pairs, r), NBb / 2, 0, st>>>(b.G, b.strideG, Tb, b.strideTb,
                                                                  nbb, h);
         }
