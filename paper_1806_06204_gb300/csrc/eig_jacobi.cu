@@ -200,8 +200,9 @@ jacobi_sweep_kernel(double* X, int64_t ldx, int64_t m, int n_even, int n_real, d
         }
       }
     }
-    // publish: this block's stores, then the columns' round counters
-    __threadfence();
+    // publish: the block barrier orders every thread's stores before thread 0's
+    // release of the columns' round counters (a release at GPU scope covers what
+    // happens before it in the block), which the next pair's acquire pairs with
     __syncthreads();
     if (threadIdx.x == 0) {
       st_release(ver + p, round + 1);
