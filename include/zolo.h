@@ -55,10 +55,12 @@ enum {
    factorisations, diagonal blocks and coefficients stay FP64.
    ZOLO_SPLIT_FP16: the same on the FP16 tensor cores with 8 slices of 7-bit
    integer digits and 36 slice-pair products instead of 53 (the same error
-   grade; inner dimensions up to about 60000).
+   grade).
    ZOLO_SPLIT_FP8: the same on the FP8 (E4M3) tensor cores with 11 slices of
    5-bit integer digits and 76 slice-pair products at twice the BF16 rate
-   (the same error grade; inner dimensions up to about 110000). */
+   (the same error grade).  A product whose inner dimension is longer than
+   the int64 of its exact level sums can hold at the digit bounds (114688 for
+   BF16 and FP8, 61440 for FP16) runs as consecutive products added in FP64. */
 enum { ZOLO_FP64 = 0, ZOLO_SPLIT_BF16 = 1, ZOLO_SPLIT_FP16 = 2, ZOLO_SPLIT_FP8 = 3 };
 
 typedef struct {

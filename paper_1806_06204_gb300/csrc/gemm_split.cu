@@ -638,7 +638,8 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     // ---------------- epilogue: drain chunks into integer accumulators
     // Level L (2..8) of a chunk is an integer multiple of 2^-6L below 2^24 of
     // those units, so it is added exactly to an int64 counting units of 2^-48
-    // (per chunk below 2^57.1: exact for K up to about 120000).  The merged
+    // (per chunk below 2^57.1: exact for 56 chunks, so gemm_split cuts a longer
+    // K into products of at most 56 x 2048).  The merged
     // levels >= 9 go into a float, 2^-42 below the leading level.  FP64 is used
     // only when a batch entry's result is written (two conversions, one FMA, the
     // beta term; the power-of-two scale goes into the exponent field).
@@ -951,6 +952,28 @@ cudaError_t run_split(const GemmArgs& g, SplitWork& w, cudaStream_t st) {
 cudaError_t gemm_split(const GemmArgs& g, SplitWork& w, cudaStream_t st) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
   if (g.K <= 0 || g.batch > kGemmMaxBatch) return gemm_f64(g, st);
+  // The int64 that holds an output's exact level sums has room for a bounded
+  // number of K-chunks at the digit bounds (BF16: 2^57.1 per 2048-chunk, FP16:
+  // 2^56.1 per 512-chunk, FP8: 2^58.1 per 4096-chunk); a longer K runs as
+  // consecutive products whose partial results are added in FP64.
+  const int64_t kmax = w.form == kFormFP16 ? 120 * 512 : w.form == kFormFP8 ? 28 * 4096 : 56 * 2048;
+  if (g.K > kmax) {
+    for (int64_t k0 = 0; k0 < g.K; k0 += kmax) {
+      GemmArgs h = g;
+      h.K = (int)std::min<int64_t>(kmax, g.K - k0);
+      h.A = g.A + (g.transA ? k0 : k0 * g.lda);   // op(A) columns k0..
+      h.B = g.B + (g.transB ? k0 * g.ldb : k0);   // op(B) rows k0..
+      if (k0 > 0) {
+        h.Cin = g.Cout;
+        h.ldcin = g.ldcout;
+        h.strideCin = g.reduce ? 0 : g.strideCout;
+        h.beta = 1.0;
+      }
+      const cudaError_t e = gemm_split(h, w, st);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
   // batch entries per launch that the slice workspace and the exponent array hold
   const size_t per = split_slice_elems(g.M, g.N, g.K, 1, w.slices_s, w.form);
   const size_t rows = split_exp_elems(g.M, g.N, g.K, 1, g.k_equilibrate, w.form);

@@ -81,6 +81,21 @@ def test_split_integer_products_are_exact(zb, handle, prec):
     assert np.array_equal(C.cpu().numpy(), A @ B)
 
 
+@pytest.mark.parametrize("prec", [1, 2, 3])
+def test_split_long_k_stays_exact(zb, handle, prec):
+    # every digit at its bound over K = 150000 terms: the level sums would overflow
+    # the epilogue's int64 in one product; gemm_split cuts K into pieces that fit
+    # (114688 terms for BF16 and FP8, 61440 for FP16) and adds them in FP64
+    from fractions import Fraction
+    K = 150000
+    a, b = 0.4999, -0.4999
+    A = np.full((8, K), a)
+    B = np.full((K, 8), b)
+    C = zb.zolo_dgemm(handle, dev(A), dev(B), prec=prec).cpu().numpy()
+    ref = float(Fraction(a) * Fraction(b) * K)
+    assert np.max(np.abs(C - ref)) <= 1e-14 * abs(ref)
+
+
 @pytest.mark.parametrize("m,n,kappa,r,form", [(256, 256, 1e8, 3, 1), (300, 160, 1e6, 6, 1),
                                               (384, 384, 1e12, 8, 1), (384, 384, 1e12, 8, 2),
                                               (800, 200, 1e6, 6, 0)])

@@ -300,3 +300,18 @@ def test_fp8_form_level_sums_exact_over_a_4096_chunk():
     B = np.full((8192, 1), -0.4999)
     C = split_product_fp8(A, B)
     assert abs(C[0, 0] - exact_product(A, B)[0, 0]) <= 8192 * 2.0 ** -52
+
+
+def test_long_k_pieces_keep_the_int64_exact():
+    # gemm_split cuts K into products of at most 56 x 2048 (BF16), 120 x 512
+    # (FP16) and 28 x 4096 (FP8) terms: at the digit bounds the int64 of 2^-48
+    # (FP16: 2^-49) units, summed over those chunks, stays below 2^63
+    def per_chunk(bits, chunk, top_int_level, unit, pairs_cap):
+        return sum(min(L - 1, pairs_cap) * chunk * 2 ** (2 * (bits - 1)) * 2 ** (unit - bits * L)
+                   for L in range(2, top_int_level + 1))
+    bf16 = per_chunk(6, 2048, 8, 48, 9)
+    fp16 = per_chunk(7, 512, 7, 49, 8)
+    fp8 = per_chunk(5, 4096, 9, 48, 11)
+    assert 56 * bf16 < 2 ** 63 and 120 * fp16 < 2 ** 63 and 28 * fp8 < 2 ** 63
+    # and the pieces are not needlessly short: twice as many chunks would not fit
+    assert 2 * 56 * bf16 > 2 ** 63 and 2 * 120 * fp16 > 2 ** 63 and 2 * 28 * fp8 > 2 ** 63
