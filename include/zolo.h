@@ -286,7 +286,9 @@ int zolo_svd_host(zolo_handle_t handle, const double* A, int64_t m, int64_t n, i
    run on.  prec = ZOLO_FP64 (DFMA), ZOLO_SPLIT_BF16 with `slices` = 8 or 9
    (0 = 8) six-bit slices per operand on the tensor cores, ZOLO_SPLIT_FP16
    (`slices` 0 or 8: eight seven-bit slices) or ZOLO_SPLIT_FP8 (`slices` 0 or
-   11: eleven five-bit slices).  Not in the paper as
+   11: eleven five-bit slices).  On the split path an Inf or NaN in a row of
+   op(A) or a column of op(B) makes that row or column of the product NaN.
+   Not in the paper as
    an interface; it exposes the building block for testing and reuse.
    Synchronises the stream before returning. */
 int zolo_dgemm(zolo_handle_t handle, int transA, int transB, int64_t m, int64_t n, int64_t k,

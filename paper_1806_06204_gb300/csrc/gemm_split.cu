@@ -466,6 +466,9 @@ struct SplitEpi {
   int* err;
   int stall;                // test hook: the MMA issuer first waits on a barrier nothing completes
   long long stall_ns;
+  int nan_rows;             // an exponent of 1026 marks a row or column with an Inf or NaN
+                            // (off with the inner-index equilibration, whose shifted
+                            // exponents may exceed it)
 };
 
 template <int BN, int S>
@@ -746,7 +749,7 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
               // two 2^(e_i + f_j) in its exponent field, joined by one FP64 add
               // (the same single rounding as converting the int64 and adding the
               // float part at its weight)
-              const int e = ei + __ldg(ebb + j);
+              const int ej = __ldg(ebb + j), e = ei + ej;
               double v;
               if (FORM == kFormFP8)
                 v = i64_scaled(iacc[j], e - 48) + f32_scaled(fm[j], e - 48 - 17);
@@ -754,6 +757,10 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
                 v = i64_scaled(iacc[j], e - 49) + f32_scaled(fm[j], e - 49 - 7);
               else
                 v = i64_scaled(iacc[j], e - 48) + f32_scaled(fm[j], e);
+              // an Inf or NaN in the row of op(A) or the column of op(B): the
+              // digits carry no value, so the output is NaN (as the FP64 product
+              // gives NaN or Inf there)
+              if (p.nan_rows && (ei >= 1026 || ej >= 1026)) v = __longlong_as_double(0x7FF8000000000000ll);
               if (al == -1.0) v = __longlong_as_double(__double_as_longlong(v) ^ (long long)0x8000000000000000ull);
               else if (al != 1.0) v *= al;
               if (first) {
@@ -922,6 +929,7 @@ cudaError_t run_split(const GemmArgs& g, SplitWork& w, cudaStream_t st) {
   p.err = w.err;
   p.stall = w.stall;
   p.stall_ns = w.stall_ns;
+  p.nan_rows = keq ? 0 : 1;
   using L = SmemLayout<BN, S>;
   if ((err = smem_attr_once((const void*)split_gemm_kernel<BN, S, FORM>, L::kAlloc)) != cudaSuccess) {
     if (std::getenv("ZOLO_DEBUG"))

@@ -82,6 +82,32 @@ def test_split_integer_products_are_exact(zb, handle, prec):
 
 
 @pytest.mark.parametrize("prec", [1, 2, 3])
+def test_split_nonfinite_rows_and_columns_give_nan(zb, handle, prec):
+    # an Inf or NaN leaves no digits to multiply: its row of op(A) or column of
+    # op(B) comes out NaN (FP64 gives NaN or Inf there); every other entry is the
+    # product as usual
+    rng = np.random.default_rng(17)
+    A = rng.standard_normal((64, 100))
+    B = rng.standard_normal((100, 40))
+    A[3, 17] = np.nan
+    A[10, 5] = np.inf
+    B[7, 2] = -np.inf
+    C = zb.zolo_dgemm(handle, dev(A), dev(B), prec=prec).cpu().numpy()
+    with np.errstate(invalid="ignore", over="ignore"):
+        ref = A @ B
+    bad = ~np.isfinite(ref)
+    assert np.array_equal(~np.isfinite(C), bad)
+    assert np.all(np.isnan(C[bad]))
+    ok = ~bad
+    # the bound of test_dgemm_matches_numpy (eight 6-bit BF16 slices by default)
+    bits = 48 if prec == 1 else 54
+    amax = np.where(np.isfinite(A), np.abs(A), 0.0).max(axis=1, keepdims=True)
+    bmax = np.where(np.isfinite(B), np.abs(B), 0.0).max(axis=0, keepdims=True)
+    tol = 2.0 * 100 * 2.0 ** (-bits) * amax * bmax * 4 + 1e-15 * np.abs(np.where(ok, ref, 0.0))
+    assert np.all(np.abs(C[ok] - ref[ok]) <= tol[ok])
+
+
+@pytest.mark.parametrize("prec", [1, 2, 3])
 def test_split_long_k_stays_exact(zb, handle, prec):
     # every digit at its bound over K = 150000 terms: the level sums would overflow
     # the epilogue's int64 in one product; gemm_split cuts K into pieces that fit
