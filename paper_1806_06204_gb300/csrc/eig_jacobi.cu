@@ -259,10 +259,10 @@ constexpr int kJRows = 256;            // rows per staged chunk (one per thread 
 constexpr int kJLd = kJRows + 1;       // chunk leading dimension: conflict-free column and row walks
 constexpr int kJInner = 1;             // Jacobi sweeps on G per visit
 
-__global__ void __launch_bounds__(kJacThreads)
+__global__ void __launch_bounds__(kJacThreads, 2)
 jacobi32_block_sweep_kernel(float* X, float* Z, int64_t ld, int64_t m, int nb_even, int n_real,
                             float tol, int* status, unsigned* bar, int* err, int stall,
-                            long long stall_ns) {
+                            long long stall_ns, int split, float* Gp) {
   static_assert(kJacThreads == 256 && kJW == 32 && kJRows == kJacThreads, "thread mapping below");
   __shared__ float Ct[kJW * kJLd];             // chunk, column-major: Ct[j * kJLd + r]
   __shared__ float G[kJW][kJW + 1];
@@ -292,8 +292,16 @@ jacobi32_block_sweep_kernel(float* X, float* Z, int64_t ld, int64_t m, int nb_ev
   __shared__ int s_rot;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int npairs = nb_even / 2;
+  // split = 2: two blocks per block pair, each on half of the rows, so that an
+  // SM holds two blocks (16 warps) where one left it latency-bound; their Gram
+  // partials meet through Gp after a grid barrier (the host launches exactly
+  // 2 x npairs blocks then, so every block reaches that barrier once per round)
+  const int half = split == 2 ? (int)(blockIdx.x & 1) : 0;
+  const int64_t mh = split == 2 ? ((m + 1) / 2 + kJRows - 1) / kJRows * kJRows : m;
+  const int64_t row_lo = half * mh;
+  const int64_t row_hi = row_lo + mh < m ? row_lo + mh : m;
   for (int round = 0; round < nb_even - 1; ++round) {
-    for (int pi = blockIdx.x; pi < npairs; pi += gridDim.x) {
+    for (int pi = blockIdx.x / split; pi < npairs; pi += gridDim.x / split) {
       auto elem = [&](int pos) { return pos == 0 ? 0 : 1 + (pos - 1 + round) % (nb_even - 1); };
       int P = elem(pi), Qb = elem(nb_even - 1 - pi);
       if (P > Qb) { const int t = P; P = Qb; Qb = t; }
@@ -306,7 +314,7 @@ jacobi32_block_sweep_kernel(float* X, float* Z, int64_t ld, int64_t m, int nb_ev
 #pragma unroll
         for (int j = 0; j < kJW; ++j) {
           const int c = col(j);
-          pf[j] = (c < n_real && r < m) ? M[(int64_t)c * ld + r] : 0.f;
+          pf[j] = (c < n_real && r < row_hi) ? M[(int64_t)c * ld + r] : 0.f;
         }
       };
       auto stage = [&]() {
@@ -322,11 +330,11 @@ jacobi32_block_sweep_kernel(float* X, float* Z, int64_t ld, int64_t m, int nb_ev
         for (int a = 0; a < 8; ++a)
 #pragma unroll
           for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
-        fetch(X, 0);
-        for (int64_t r0 = 0; r0 < m; r0 += kJRows) {
+        fetch(X, row_lo);
+        for (int64_t r0 = row_lo; r0 < row_hi; r0 += kJRows) {
           stage();
           __syncthreads();
-          if (r0 + kJRows < m) fetch(X, r0 + kJRows);
+          if (r0 + kJRows < row_hi) fetch(X, r0 + kJRows);
           for (int r = g; r < kJRows; r += 16) {
             float va[8], vb[8];
 #pragma unroll
@@ -360,6 +368,18 @@ jacobi32_block_sweep_kernel(float* X, float* Z, int64_t ld, int64_t m, int nb_ev
           for (int w = 0; w < kJacThreads / 32; ++w) sum += Ct[w * kJW * kJW + e];
           G[i][jj] = sum;
           Qm[i][jj] = i == jj ? 1.f : 0.f;
+          if (split == 2) Gp[((int64_t)pi * 2 + half) * kJW * kJW + e] = sum;
+        }
+      }
+      if (split == 2) {
+        // both halves' partials, summed in the same order by both blocks (read
+        // through L2: the partner wrote them on another SM)
+        if (!grid_barrier(bar, bar + 1, err)) return;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int e = tid + kJacThreads * u, i = e >> 5, jj = e & 31;
+          G[i][jj] = __ldcg(Gp + (int64_t)pi * 2 * kJW * kJW + e) +
+                     __ldcg(Gp + ((int64_t)pi * 2 + 1) * kJW * kJW + e);
         }
       }
       if (tid == 0) s_rot = 0;
@@ -412,7 +432,7 @@ jacobi32_block_sweep_kernel(float* X, float* Z, int64_t ld, int64_t m, int nb_ev
         }
       }
       const int nrot = s_rot;
-      if (tid == 0 && nrot) atomicAdd(status + kStatJacobiRot, nrot);
+      if (tid == 0 && nrot && half == 0) atomicAdd(status + kStatJacobiRot, nrot);
       // ---- 3. X and Z columns of the pair times Q (skipped when nothing rotated):
       //         thread computes rows 8 rt .. 8 rt + 7, columns 4 ct .. 4 ct + 3
       if (nrot) {
@@ -424,11 +444,11 @@ jacobi32_block_sweep_kernel(float* X, float* Z, int64_t ld, int64_t m, int nb_ev
         const int rt = tid >> 3, ct = tid & 7;
         for (int which = 0; which < 2; ++which) {
           float* M = which ? Z : X;
-          fetch(M, 0);
-          for (int64_t r0 = 0; r0 < m; r0 += kJRows) {
+          fetch(M, row_lo);
+          for (int64_t r0 = row_lo; r0 < row_hi; r0 += kJRows) {
             stage();
             __syncthreads();
-            if (r0 + kJRows < m) fetch(M, r0 + kJRows);
+            if (r0 + kJRows < row_hi) fetch(M, r0 + kJRows);
             float o[8][4];
 #pragma unroll
             for (int a = 0; a < 8; ++a)
@@ -456,7 +476,7 @@ jacobi32_block_sweep_kernel(float* X, float* Z, int64_t ld, int64_t m, int nb_ev
 #pragma unroll 8
             for (int j = 0; j < kJW; ++j) {
               const int c = col(j);
-              if (c < n_real && r < m) M[(int64_t)c * ld + r] = Ct[j * kJLd + tid];
+              if (c < n_real && r < row_hi) M[(int64_t)c * ld + r] = Ct[j * kJLd + tid];
             }
             __syncthreads();
           }
@@ -672,7 +692,13 @@ int eig_sym_jacobi(const double* H, int64_t ldh, int64_t n, double* V, int64_t l
       return 1;
     const int nb = (int)((n + kJB - 1) / kJB);
     const int nb_even = nb + (nb & 1);
-    const int grid = (int)std::min<int64_t>(nb_even / 2, (int64_t)std::max(1, occ) * sms);
+    // two blocks per block pair when they all fit at once and a half has rows
+    // to spare (n >= 512); the partial Gram matrices go to Z, unused until the
+    // FP32 phase ends
+    const int split = (int64_t)nb_even <= (int64_t)std::max(1, occ) * sms && n >= 2 * kJRows ? 2 : 1;
+    const int grid =
+        split == 2 ? nb_even : (int)std::min<int64_t>(nb_even / 2, (int64_t)std::max(1, occ) * sms);
+    float* Gp = reinterpret_cast<float*>(w.Z);
     const float tol32 = 8e-6f;
     for (int sw = 0; sw < 25; ++sw) {
       if (cudaMemsetAsync(w.status + kStatJacobiRot, 0, sizeof(int), st) != cudaSuccess) return 1;
@@ -687,7 +713,9 @@ int eig_sym_jacobi(const double* H, int64_t ldh, int64_t n, double* V, int64_t l
       int* err = w.err;
       int stall = sw == 0 ? w.stall : 0;
       long long stall_ns = w.stall_ns;
-      void* args[] = {&X32, &Z32, &ld, &mm, &ne, &nr, &tol, &status, &bar, &err, &stall, &stall_ns};
+      int sp = split;
+      void* args[] = {&X32, &Z32, &ld, &mm, &ne, &nr, &tol, &status, &bar, &err, &stall, &stall_ns,
+                      &sp, &Gp};
       {
         // Gram and two products with Q per block pair: 6 (2 kJB)^2 m flops
         ProfScope ps(kProfJacobi32, st,

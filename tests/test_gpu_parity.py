@@ -289,6 +289,27 @@ def test_svd_matches_oracle(zb, handle, m, n, kappa, r):
     assert np.allclose(np.abs(np.sum(V * Vo, axis=0))[sep], 1.0, atol=1e-9)
 
 
+@pytest.mark.parametrize("n,kappa", [(520, 1e8), (700, 1e12)])
+def test_svd_past_the_row_split_of_the_fp32_sweeps(zb, handle, n, kappa):
+    # from n = 512 the FP32 Jacobi sweeps give each block pair two blocks, one
+    # per half of the rows (520: a ragged second half of 4 rows past a 256-row
+    # chunk); checked against the singular values and vectors the matrix was
+    # built from, which hold at any size
+    sm = synth.make_matrix(n, n, synth.geometric_sigma(n, kappa), seed=1300 + n)
+    U, S, V, info = zb.zolo_svd(handle, dev(sm.A), zb.opts(beta=float(sm.sigma[-1])))
+    U, S, V = host(U), host(S), host(V)
+    assert np.max(np.abs(S - sm.sigma)) <= 1e-12 * sm.sigma[0]
+    assert zo.svd_residual(sm.A, U, S, V) <= 1e-13 * math.sqrt(n)
+    assert zo.orthogonality(U) <= 1e-13 and zo.orthogonality(V) <= 1e-13
+    # vectors of singular values separated by 1e-3 sigma_1 agree up to sign
+    So = sm.sigma
+    gap = np.minimum(np.abs(np.diff(np.r_[np.inf, So])), np.abs(np.diff(np.r_[So, -np.inf])))
+    sep = gap > 1e-3 * So[0]
+    assert sep.sum() >= 10
+    assert np.allclose(np.abs(np.sum(U * sm.U, axis=0))[sep], 1.0, atol=1e-9)
+    assert np.allclose(np.abs(np.sum(V * sm.V, axis=0))[sep], 1.0, atol=1e-9)
+
+
 def test_host_entry_points_match_device_ones(zb, handle):
     sm = synth.square_geometric(100, 1e6, seed=5)
     o = zb.opts(beta=1e-6, r=5)

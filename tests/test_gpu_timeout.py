@@ -76,9 +76,12 @@ def test_split_polar_decomposition_reports_timeout_then_matches_oracle(zb):
         h.close()
 
 
-def test_jacobi_grid_barrier_wait_expires_then_recovers(zb):
+@pytest.mark.parametrize("n", [200, 600])
+def test_jacobi_grid_barrier_wait_expires_then_recovers(zb, n):
+    # 600: two blocks per block pair, which also meet at a barrier between the
+    # Gram partials and the rotations
     from paper_1806_06204_gb300 import synth
-    sm = synth.square_geometric(200, 1e6, seed=1011)
+    sm = synth.square_geometric(n, 1e6, seed=1011)
     A = dev(sm.A)
     h = zb.Handle(0)
     try:
