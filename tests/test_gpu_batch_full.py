@@ -2,8 +2,8 @@
 to 1024, kappa log-uniform in [1e2, 1e12], r from Table 1's rule) in one
 zolo_pd_batched call, FP64 and the three split forms.  Every result meets the
 invariants the contract fixes (backward error and orthogonality <= 1e-13, H
-exactly symmetric); the members the CPU oracle decomposes in seconds (n <= 128)
-(n = 64) are compared with it entry by entry: H to 1e-13 of its norm, Qp within the
+exactly symmetric); the members the CPU oracle decomposes in seconds (n = 64)
+are compared with it entry by entry: H to 1e-13 of its norm, Qp within the
 polar factor's conditioning (its sensitivity is about 1/(sigma_{n-1}+sigma_n))."""
 import math
 
