@@ -40,7 +40,8 @@ enum {
   ZOLO_ECUDA = 4,      /* a CUDA runtime call failed                            */
   ZOLO_ENOMEM = 5,     /* workspace too small / device allocation failed        */
   ZOLO_EEIG = 6,       /* the Jacobi eigensolver did not converge               */
-  ZOLO_ETIMEOUT = 7,   /* a bounded wait inside a tensor-core kernel expired    */
+  ZOLO_ETIMEOUT = 7,   /* a bounded device wait expired (split GEMM pipeline,
+                          Jacobi grid barrier or column-pair wait)              */
   ZOLO_EIO = 8,        /* a tuning-cache file could not be written or read      */
   ZOLO_EINVAL = 9,     /* a tuning-cache file is malformed or from another GPU  */
   ZOLO_ECOMM = 10,     /* the caller's sum over ranks (zolo_pd_sharded) failed  */
@@ -166,7 +167,7 @@ int zolo_schedule(double ell0, int r, int max_iter, double* ells, int* used_qr, 
 
 /* Device memory a zolo_pd (svd = 0) or zolo_svd (svd = 1) call on an m x n
    matrix keeps in its handle (host computation, no GPU work): the workspace
-   for r shifts (r <= 0: for up to 8) plus, for ZOLO_SPLIT_BF16, the slice
+   for r shifts (r <= 0: for up to 8) plus, for a split precision, the slice
    planes and exponents, as the call allocates them (the planes are capped at
    16 GB; a smaller allocation is tried when that fails).  Not counted: the
    host entry points' staging copies of A and the results, and the tuner's
