@@ -159,12 +159,19 @@ def accuracy(w, sm, outs):
     I = torch.eye(n, dtype=torch.float64, device="cuda")
     if w["kind"] == "svd":
         U, S, V = outs
-        bwd = torch.linalg.norm(A - (U * S) @ V.T) / nA
+        res = torch.linalg.norm(A - (U * S) @ V.T)
         sig = torch.from_numpy(sm.sigma).cuda()
-        return {"bwd_err": float(bwd),
-                "orth_U": float(torch.linalg.norm(U.T @ U - I) / math.sqrt(n)),
-                "orth_V": float(torch.linalg.norm(V.T @ V - I) / math.sqrt(n)),
-                "max_sigma_err": float(torch.max(torch.abs(S - sig)) / sig[0])}
+        orth_u = float(torch.linalg.norm(U.T @ U - I))
+        orth_v = float(torch.linalg.norm(V.T @ V - I))
+        return {"bwd_err": float(res / nA),
+                "orth_U": orth_u / math.sqrt(n),
+                "orth_V": orth_v / math.sqrt(n),
+                "max_sigma_err": float(torch.max(torch.abs(S - sig)) / sig[0]),
+                # Section 4's own measures: the residual over ||A||_2 (sigma_1 of
+                # the generator) and ||I - U^T U||_F / n, ||I - V^T V||_F / n
+                "paper_Res": float(res) / float(sm.sigma[0]),
+                "paper_OrthL": orth_u / n,
+                "paper_OrthR": orth_v / n}
     Qp, H = outs
     return {"bwd_err": float(torch.linalg.norm(A - Qp @ H) / nA),
             "orth_Qp": float(torch.linalg.norm(Qp.T @ Qp - I) / math.sqrt(n)),
